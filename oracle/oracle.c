@@ -1,0 +1,491 @@
+/*
+ * oracle.c -- plain, slow FP64 CPU reference for direct volume ray casting of
+ * trivariate LR-splines (Fuchs, Barrowclough, Hjelmervik, Dahl: "Direct
+ * interactive visualization of locally refined spline volumes for scalar and
+ * vector fields").
+ *
+ * TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load this library.  It shares no code
+ * with the CUDA path.
+ *
+ * What it computes, each function following its passage of the paper:
+ *   orc_bspline      univariate B-spline by the Cox-de Boor recursion on a
+ *                    local knot vector (Sec. 3.1, Eq. 1 factors)
+ *   orc_find_element the element holding a point, by linear search over all
+ *                    element boxes (Sec. 3.2: "a linear search through all
+ *                    elements")
+ *   orc_eval         f(x) = sum_i c_i gamma_i N_i(x)  (Eq. 2), the sum running
+ *                    over the B-splines whose support contains the element of
+ *                    x, found by scanning all B-splines
+ *   orc_render       per pixel: ray setup, sampling at a fixed step or at the
+ *                    adaptive distance of Eq. 4, transfer function, and
+ *                    front-to-back compositing (Alg. 2)
+ *
+ * Readings of points the paper leaves open (each listed in the design notes):
+ *   - intervals are half open, [lo, hi); the upper domain face x = 1 belongs
+ *     to the last non-empty interval / the element with hi = 1;
+ *   - element and step decisions depend on the sample position, so sample
+ *     positions, ray parameters and the loop bounds are computed in FP32 with
+ *     the operation order stated below (the precision the kernels use); the
+ *     field, the transfer function and the compositing are FP64;
+ *   - Eq. 4 uses d = max(p1,p2,p3) and the element's sides in parameter units;
+ *     the step is rounded once to FP32;
+ *   - the segment of Alg. 2 belonging to sample k is the forward segment to
+ *     the next sample, the last one clipped at the exit parameter;
+ *   - the TF is linear interpolation over 256 entries spanning [vmin, vmax],
+ *     colour not premultiplied (Alg. 2 multiplies by (1-T)(1-alpha_dst));
+ *   - early termination when alpha_dst >= alpha_stop; background transparent.
+ */
+#include <math.h>
+#include <pthread.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_MAXP 4
+#define ORC_NONE 0xFFFFFFFFu
+
+typedef struct {
+  int p[3];
+  int nc;
+  int64_t n_elem;
+  double *box; /* n_elem x 6: lo xyz, hi xyz */
+  int64_t n_basis;
+  int kw;          /* knots per B-spline: p0+p1+p2+6 */
+  double *knots;   /* n_basis x kw, x then y then z */
+  double *coef;    /* n_basis x nc */
+  double *weight;  /* n_basis: gamma */
+} orc_vol;
+
+/* ------------------------------------------------------------------------ */
+/* Eq. 1 factor: one univariate B-spline of degree p on knots xi[0..p+1].    */
+/* ------------------------------------------------------------------------ */
+double orc_bspline(const double *xi, int p, double x) {
+  double N[ORC_MAXP + 2];
+  if (x < xi[0] || x > xi[p + 1]) return 0.0;
+  for (int j = 0; j <= p; ++j) N[j] = (xi[j] <= x && x < xi[j + 1]) ? 1.0 : 0.0;
+  if (x == xi[p + 1] && x == 1.0) {
+    /* upper domain face: belongs to the last non-empty interval */
+    for (int j = p; j >= 0; --j)
+      if (xi[j] < xi[j + 1]) {
+        N[j] = 1.0;
+        break;
+      }
+  }
+  for (int r = 1; r <= p; ++r) {
+    for (int j = 0; j + r <= p; ++j) {
+      double left = 0.0, right = 0.0;
+      if (xi[j + r] != xi[j]) left = (x - xi[j]) / (xi[j + r] - xi[j]) * N[j];
+      if (xi[j + r + 1] != xi[j + 1]) right = (xi[j + r + 1] - x) / (xi[j + r + 1] - xi[j + 1]) * N[j + 1];
+      N[j] = left + right;
+    }
+  }
+  return N[0];
+}
+
+orc_vol *orc_create(const int *deg, int nc, int64_t n_elem, const double *box, int64_t n_basis,
+                    const double *knots, const double *coef, const double *weight) {
+  for (int a = 0; a < 3; ++a)
+    if (deg[a] < 0 || deg[a] > ORC_MAXP) return NULL;
+  if (nc < 1 || nc > 3 || n_elem < 1 || n_basis < 1) return NULL;
+  orc_vol *v = (orc_vol *)calloc(1, sizeof(orc_vol));
+  for (int a = 0; a < 3; ++a) v->p[a] = deg[a];
+  v->nc = nc;
+  v->n_elem = n_elem;
+  v->n_basis = n_basis;
+  v->kw = deg[0] + deg[1] + deg[2] + 6;
+  v->box = (double *)malloc(sizeof(double) * 6 * n_elem);
+  v->knots = (double *)malloc(sizeof(double) * v->kw * n_basis);
+  v->coef = (double *)malloc(sizeof(double) * nc * n_basis);
+  v->weight = (double *)malloc(sizeof(double) * n_basis);
+  memcpy(v->box, box, sizeof(double) * 6 * n_elem);
+  memcpy(v->knots, knots, sizeof(double) * v->kw * n_basis);
+  memcpy(v->coef, coef, sizeof(double) * nc * n_basis);
+  memcpy(v->weight, weight, sizeof(double) * n_basis);
+  return v;
+}
+
+void orc_destroy(orc_vol *v) {
+  if (!v) return;
+  free(v->box);
+  free(v->knots);
+  free(v->coef);
+  free(v->weight);
+  free(v);
+}
+
+static const double *knots_of(const orc_vol *v, int64_t i, int a) {
+  const double *k = v->knots + i * v->kw;
+  if (a >= 1) k += v->p[0] + 2;
+  if (a >= 2) k += v->p[1] + 2;
+  return k;
+}
+
+/* x in element e: lo <= x < hi per axis, with x == hi allowed when hi == 1. */
+static int in_element(const orc_vol *v, int64_t e, const double *x) {
+  const double *b = v->box + 6 * e;
+  for (int a = 0; a < 3; ++a) {
+    double lo = b[a], hi = b[3 + a];
+    if (!(lo <= x[a] && (x[a] < hi || (x[a] == hi && hi == 1.0)))) return 0;
+  }
+  return 1;
+}
+
+/* The element holding x, by linear search over all elements; ORC_NONE outside [0,1]^3. */
+uint32_t orc_find_element(const orc_vol *v, const double *x) {
+  for (int a = 0; a < 3; ++a)
+    if (!(x[a] >= 0.0 && x[a] <= 1.0)) return ORC_NONE;
+  for (int64_t e = 0; e < v->n_elem; ++e)
+    if (in_element(v, e, x)) return (uint32_t)e;
+  return ORC_NONE;
+}
+
+/* B-splines whose support contains element e, by scanning all B-splines.
+ * out must hold n_basis entries; returns the count. */
+int64_t orc_incidence(const orc_vol *v, int64_t e, int64_t *out) {
+  const double *b = v->box + 6 * e;
+  int64_t n = 0;
+  for (int64_t i = 0; i < v->n_basis; ++i) {
+    int ok = 1;
+    for (int a = 0; a < 3 && ok; ++a) {
+      const double *k = knots_of(v, i, a);
+      ok = (k[0] <= b[a]) && (b[3 + a] <= k[v->p[a] + 1]);
+    }
+    if (ok) out[n++] = i;
+  }
+  return n;
+}
+
+/* Eq. 2 at x, given the incidence list of the element holding x. */
+static void eval_with(const orc_vol *v, const int64_t *inc, int64_t ninc, const double *x, double *out) {
+  for (int c = 0; c < v->nc; ++c) out[c] = 0.0;
+  for (int64_t q = 0; q < ninc; ++q) {
+    int64_t i = inc[q];
+    double N = v->weight[i];
+    for (int a = 0; a < 3; ++a) N *= orc_bspline(knots_of(v, i, a), v->p[a], x[a]);
+    for (int c = 0; c < v->nc; ++c) out[c] += v->coef[i * v->nc + c] * N;
+  }
+}
+
+/* f(x) (Eq. 2).  Returns the element id, ORC_NONE (and zeros) outside the domain. */
+uint32_t orc_eval(const orc_vol *v, const double *x, double *out) {
+  uint32_t e = orc_find_element(v, x);
+  if (e == ORC_NONE) {
+    for (int c = 0; c < v->nc; ++c) out[c] = 0.0;
+    return e;
+  }
+  int64_t *inc = (int64_t *)malloc(sizeof(int64_t) * v->n_basis);
+  int64_t n = orc_incidence(v, e, inc);
+  eval_with(v, inc, n, x, out);
+  free(inc);
+  return e;
+}
+
+/* ------------------------------------------------------------------------ */
+/* threaded batches                                                         */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  const orc_vol *v;
+  const float *pts_f;
+  const double *pts_d;
+  int64_t n;
+  int tid, nth;
+  uint32_t *elem;
+  double *val;
+} batch_job;
+
+static void *batch_worker(void *arg) {
+  batch_job *j = (batch_job *)arg;
+  const orc_vol *v = j->v;
+  int64_t *inc = j->val ? (int64_t *)malloc(sizeof(int64_t) * v->n_basis) : NULL;
+  uint32_t cur = ORC_NONE;
+  int64_t ninc = 0;
+  for (int64_t q = j->tid; q < j->n; q += j->nth) {
+    double x[3];
+    for (int a = 0; a < 3; ++a) x[a] = j->pts_f ? (double)j->pts_f[3 * q + a] : j->pts_d[3 * q + a];
+    uint32_t e = orc_find_element(v, x);
+    if (j->elem) j->elem[q] = e;
+    if (j->val) {
+      if (e == ORC_NONE) {
+        for (int c = 0; c < v->nc; ++c) j->val[q * v->nc + c] = 0.0;
+        continue;
+      }
+      if (e != cur) {
+        ninc = orc_incidence(v, e, inc);
+        cur = e;
+      }
+      eval_with(v, inc, ninc, x, j->val + q * v->nc);
+    }
+  }
+  free(inc);
+  return NULL;
+}
+
+static void run_batch(batch_job *proto, int nth) {
+  if (nth < 1) nth = 1;
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nth);
+  batch_job *jobs = (batch_job *)malloc(sizeof(batch_job) * nth);
+  for (int t = 0; t < nth; ++t) {
+    jobs[t] = *proto;
+    jobs[t].tid = t;
+    jobs[t].nth = nth;
+    pthread_create(&th[t], NULL, batch_worker, &jobs[t]);
+  }
+  for (int t = 0; t < nth; ++t) pthread_join(th[t], NULL);
+  free(th);
+  free(jobs);
+}
+
+/* Element ids of n FP32 points (n x 3). */
+void orc_lookup_batch(const orc_vol *v, const float *pts, int64_t n, uint32_t *elem, int nth) {
+  batch_job j = {v, pts, NULL, n, 0, 1, elem, NULL};
+  run_batch(&j, nth);
+}
+
+/* f at n FP32 points (val: n x nc) and their element ids (may be NULL). */
+void orc_eval_batch_f32(const orc_vol *v, const float *pts, int64_t n, double *val, uint32_t *elem, int nth) {
+  batch_job j = {v, pts, NULL, n, 0, 1, elem, val};
+  run_batch(&j, nth);
+}
+
+/* f at n FP64 points. */
+void orc_eval_batch_f64(const orc_vol *v, const double *pts, int64_t n, double *val, uint32_t *elem, int nth) {
+  batch_job j = {v, NULL, pts, n, 0, 1, elem, val};
+  run_batch(&j, nth);
+}
+
+/* ------------------------------------------------------------------------ */
+/* rendering (Sec. 4)                                                       */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t projection; /* 0 ortho, 1 persp */
+  int32_t width, height;
+  double eye[3], target[3], up[3];
+  double fovy;   /* persp: full vertical field of view (radians) */
+  double extent; /* ortho: full height of the view window */
+} orc_camera;
+
+typedef struct {
+  const double *table; /* 256 x 4 RGBA */
+  double vmin, vmax;
+} orc_tf;
+
+typedef struct {
+  int32_t mode;  /* 0 fixed, 1 heuristic (Eq. 4) */
+  int32_t field; /* 0 scalar, 1 magnitude, 2 component */
+  int32_t component;
+  double h, xi, alpha_stop;
+} orc_step;
+
+typedef struct {
+  /* FP32 ray-generation constants, from FP64 camera algebra rounded once */
+  float E[3], F[3], R[3], U[3];
+  float sxs, sxo, sys, syo;
+  int persp;
+} ray_consts;
+
+static void camera_consts(const orc_camera *c, ray_consts *k) {
+  double F[3], R[3], U[3], n;
+  for (int a = 0; a < 3; ++a) F[a] = c->target[a] - c->eye[a];
+  n = sqrt(F[0] * F[0] + F[1] * F[1] + F[2] * F[2]);
+  for (int a = 0; a < 3; ++a) F[a] = F[a] / n;
+  R[0] = F[1] * c->up[2] - F[2] * c->up[1];
+  R[1] = F[2] * c->up[0] - F[0] * c->up[2];
+  R[2] = F[0] * c->up[1] - F[1] * c->up[0];
+  n = sqrt(R[0] * R[0] + R[1] * R[1] + R[2] * R[2]);
+  for (int a = 0; a < 3; ++a) R[a] = R[a] / n;
+  U[0] = R[1] * F[2] - R[2] * F[1];
+  U[1] = R[2] * F[0] - R[0] * F[2];
+  U[2] = R[0] * F[1] - R[1] * F[0];
+  double ty = c->projection == 1 ? tan(0.5 * c->fovy) : 0.5 * c->extent;
+  double tx = ty * (double)c->width / (double)c->height;
+  for (int a = 0; a < 3; ++a) {
+    k->E[a] = (float)c->eye[a];
+    k->F[a] = (float)F[a];
+    k->R[a] = (float)R[a];
+    k->U[a] = (float)U[a];
+  }
+  k->sxs = (float)(2.0 * tx / (double)c->width);
+  k->sxo = (float)(-tx);
+  k->sys = (float)(-2.0 * ty / (double)c->height);
+  k->syo = (float)ty;
+  k->persp = c->projection == 1;
+}
+
+/* FP32 ray of pixel (i, j) (j = 0 is the top row) and its parameter interval
+ * in the unit cube.  Returns 0 when the ray misses the cube. */
+static int ray_setup(const ray_consts *k, int i, int j, float o[3], float d[3], float *tin, float *tout) {
+  float a = fmaf((float)i + 0.5f, k->sxs, k->sxo);
+  float b = fmaf((float)j + 0.5f, k->sys, k->syo);
+  if (k->persp) {
+    for (int c = 0; c < 3; ++c) {
+      d[c] = fmaf(a, k->R[c], fmaf(b, k->U[c], k->F[c]));
+      o[c] = k->E[c];
+    }
+    float n2 = fmaf(d[0], d[0], fmaf(d[1], d[1], d[2] * d[2]));
+    float n = sqrtf(n2);
+    for (int c = 0; c < 3; ++c) d[c] = d[c] / n;
+  } else {
+    for (int c = 0; c < 3; ++c) {
+      o[c] = fmaf(a, k->R[c], fmaf(b, k->U[c], k->E[c]));
+      d[c] = k->F[c];
+    }
+  }
+  float t0 = 0.0f, t1 = INFINITY;
+  for (int c = 0; c < 3; ++c) {
+    if (d[c] == 0.0f) {
+      if (o[c] < 0.0f || o[c] > 1.0f) return 0;
+      continue;
+    }
+    float inv = 1.0f / d[c];
+    float ta = (0.0f - o[c]) * inv;
+    float tb = (1.0f - o[c]) * inv;
+    t0 = fmaxf(t0, fminf(ta, tb));
+    t1 = fminf(t1, fmaxf(ta, tb));
+  }
+  *tin = t0;
+  *tout = t1;
+  return t0 < t1;
+}
+
+/* Eq. 4: 2^-d times the shortest side of element e, d = max degree, rounded once to FP32. */
+float orc_heuristic_step(const orc_vol *v, uint32_t e) {
+  const double *b = v->box + 6 * (int64_t)e;
+  int d = v->p[0];
+  if (v->p[1] > d) d = v->p[1];
+  if (v->p[2] > d) d = v->p[2];
+  double m = b[3] - b[0];
+  if (b[4] - b[1] < m) m = b[4] - b[1];
+  if (b[5] - b[2] < m) m = b[5] - b[2];
+  return (float)ldexp(m, -d);
+}
+
+/* Transfer function: linear interpolation over 256 entries spanning [vmin, vmax]. */
+static void tf_lookup(const orc_tf *tf, double v, double rgba[4]) {
+  double x = (v - tf->vmin) / (tf->vmax - tf->vmin);
+  if (!(x > 0.0)) x = 0.0;
+  if (x > 1.0) x = 1.0;
+  x *= 255.0;
+  int i0 = (int)floor(x);
+  if (i0 > 254) i0 = 254;
+  double f = x - (double)i0;
+  for (int c = 0; c < 4; ++c) rgba[c] = (1.0 - f) * tf->table[4 * i0 + c] + f * tf->table[4 * (i0 + 1) + c];
+}
+
+typedef struct {
+  int64_t samples;
+  int64_t lookups;
+  int64_t rays_hit;
+} orc_stats;
+
+typedef struct {
+  const orc_vol *v;
+  const orc_camera *cam;
+  const orc_tf *tf;
+  const orc_step *st;
+  const int32_t *pix; /* npix x 2 (i, j) or NULL for the full image */
+  int64_t npix;
+  double *rgba; /* npix x 4 */
+  int tid, nth;
+  orc_stats stats;
+} render_job;
+
+static void *render_worker(void *arg) {
+  render_job *J = (render_job *)arg;
+  const orc_vol *v = J->v;
+  ray_consts K;
+  camera_consts(J->cam, &K);
+  int64_t *inc = (int64_t *)malloc(sizeof(int64_t) * v->n_basis);
+  double val[3];
+  for (int64_t q = J->tid; q < J->npix; q += J->nth) {
+    int i = J->pix ? J->pix[2 * q] : (int)(q % J->cam->width);
+    int j = J->pix ? J->pix[2 * q + 1] : (int)(q / J->cam->width);
+    double *out = J->rgba + 4 * q;
+    out[0] = out[1] = out[2] = out[3] = 0.0;
+    float o[3], d[3], tin, tout;
+    if (!ray_setup(&K, i, j, o, d, &tin, &tout)) continue;
+    J->stats.rays_hit++;
+    double C[3] = {0, 0, 0}, A = 0.0;
+    uint32_t cur = ORC_NONE;
+    int64_t ninc = 0;
+    float t = tin;
+    int64_t k = 0;
+    while (t < tout) {
+      float pf[3];
+      double x[3];
+      for (int c = 0; c < 3; ++c) {
+        pf[c] = fminf(fmaxf(fmaf(t, d[c], o[c]), 0.0f), 1.0f);
+        x[c] = (double)pf[c];
+      }
+      if (cur == ORC_NONE || !in_element(v, cur, x)) {
+        cur = orc_find_element(v, x);
+        ninc = orc_incidence(v, cur, inc);
+        J->stats.lookups++;
+      }
+      float tn;
+      if (J->st->mode == 1) {
+        tn = t + orc_heuristic_step(v, cur);
+      } else {
+        tn = fmaf((float)(k + 1), (float)J->st->h, tin);
+      }
+      if (!(tn > t)) tn = nextafterf(t, INFINITY);
+      double seg = (double)fminf(tn, tout) - (double)t;
+      eval_with(v, inc, ninc, x, val);
+      double s;
+      if (J->st->field == 1)
+        s = sqrt(val[0] * val[0] + val[1] * val[1] + val[2] * val[2]);
+      else if (J->st->field == 2)
+        s = val[J->st->component];
+      else
+        s = val[0];
+      double src[4];
+      tf_lookup(J->tf, s, src);
+      /* Alg. 2 */
+      double T = pow(1.0 - src[3], seg / J->st->xi);
+      double w = (1.0 - T) * (1.0 - A);
+      for (int c = 0; c < 3; ++c) C[c] += w * src[c];
+      A += w;
+      J->stats.samples++;
+      ++k;
+      t = tn;
+      if (A >= J->st->alpha_stop) break;
+    }
+    out[0] = C[0];
+    out[1] = C[1];
+    out[2] = C[2];
+    out[3] = A;
+  }
+  free(inc);
+  return NULL;
+}
+
+/* Render npix pixels (pix = NULL: the whole width x height image, row major). */
+void orc_render(const orc_vol *v, const orc_camera *cam, const orc_tf *tf, const orc_step *st,
+                const int32_t *pix, int64_t npix, double *rgba, int nth, orc_stats *stats) {
+  if (nth < 1) nth = 1;
+  if (!pix) npix = (int64_t)cam->width * cam->height;
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nth);
+  render_job *jobs = (render_job *)calloc(nth, sizeof(render_job));
+  for (int t = 0; t < nth; ++t) {
+    render_job J = {v, cam, tf, st, pix, npix, rgba, t, nth, {0, 0, 0}};
+    jobs[t] = J;
+    pthread_create(&th[t], NULL, render_worker, &jobs[t]);
+  }
+  orc_stats s = {0, 0, 0};
+  for (int t = 0; t < nth; ++t) {
+    pthread_join(th[t], NULL);
+    s.samples += jobs[t].stats.samples;
+    s.lookups += jobs[t].stats.lookups;
+    s.rays_hit += jobs[t].stats.rays_hit;
+  }
+  if (stats) *stats = s;
+  free(th);
+  free(jobs);
+}
+
+/* The FP32 ray of one pixel (for tests of the ray setup). */
+int orc_ray(const orc_camera *cam, int i, int j, float *o, float *d, float *tin, float *tout) {
+  ray_consts K;
+  camera_consts(cam, &K);
+  return ray_setup(&K, i, j, o, d, tin, tout);
+}

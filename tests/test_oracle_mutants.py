@@ -1,0 +1,103 @@
+"""Planted mistakes: every plausible slip in the oracle must trip a pin.
+
+Each case edits one line of oracle.c (a dropped term, a wrong index or sign,
+a transposed axis, an off-by-one), builds the edited copy on the CPU into a
+temporary directory, points the oracle module at it, and runs the pins of
+test_oracle_pins; at least one must fail.  The default build is restored
+afterwards.  No GPU is involved.
+"""
+import os
+import pytest
+
+import oracle.oracle as orc
+
+import test_oracle_pins as P
+
+SRC = os.path.join(os.path.dirname(orc.__file__), "oracle.c")
+
+MUTANTS = [
+    ("Cox-de Boor drops the right term", "N[j] = left + right;", "N[j] = left;"),
+    ("Cox-de Boor right term uses a wrong knot",
+     "right = (xi[j + r + 1] - x) / (xi[j + r + 1] - xi[j + 1]) * N[j + 1];",
+     "right = (xi[j + r] - x) / (xi[j + r + 1] - xi[j + 1]) * N[j + 1];"),
+    ("Cox-de Boor starts from closed intervals", "N[j] = (xi[j] <= x && x < xi[j + 1]) ? 1.0 : 0.0;",
+     "N[j] = (xi[j] <= x && x <= xi[j + 1]) ? 1.0 : 0.0;"),
+    ("Eq. 2 without the scale factors gamma", "double N = v->weight[i];", "double N = 1.0;"),
+    ("Eq. 2 evaluates every factor on the x knots",
+     "for (int a = 0; a < 3; ++a) N *= orc_bspline(knots_of(v, i, a), v->p[a], x[a]);",
+     "for (int a = 0; a < 3; ++a) N *= orc_bspline(knots_of(v, i, 0), v->p[a], x[a]);"),
+    ("Eq. 2 evaluates a factor at the wrong coordinate",
+     "for (int a = 0; a < 3; ++a) N *= orc_bspline(knots_of(v, i, a), v->p[a], x[a]);",
+     "for (int a = 0; a < 3; ++a) N *= orc_bspline(knots_of(v, i, a), v->p[a], x[(a + 1) % 3]);"),
+    ("incidence misses supports that start at the element",
+     "ok = (k[0] <= b[a]) && (b[3 + a] <= k[v->p[a] + 1]);",
+     "ok = (k[0] < b[a]) && (b[3 + a] <= k[v->p[a] + 1]);"),
+    ("element boxes closed at the top", "if (!(lo <= x[a] && (x[a] < hi || (x[a] == hi && hi == 1.0)))) return 0;",
+     "if (!(lo <= x[a] && (x[a] <= hi))) return 0;"),
+    ("Alg. 2 drops the (1 - alpha_dst) factor", "double w = (1.0 - T) * (1.0 - A);", "double w = (1.0 - T);"),
+    ("Alg. 2 ignores the segment length", "double T = pow(1.0 - src[3], seg / J->st->xi);",
+     "double T = 1.0 - src[3];"),
+    ("segment not clipped at the exit", "double seg = (double)fminf(tn, tout) - (double)t;",
+     "double seg = (double)tn - (double)t;"),
+    ("Eq. 4 with 2^-(d-1)", "return (float)ldexp(m, -d);", "return (float)ldexp(m, -d + 1);"),
+    ("Eq. 4 with the longest side", "if (b[4] - b[1] < m) m = b[4] - b[1];", "if (b[4] - b[1] > m) m = b[4] - b[1];"),
+    ("TF weights swapped",
+     "rgba[c] = (1.0 - f) * tf->table[4 * i0 + c] + f * tf->table[4 * (i0 + 1) + c];",
+     "rgba[c] = f * tf->table[4 * i0 + c] + (1.0 - f) * tf->table[4 * (i0 + 1) + c];"),
+    ("image rows flipped", "k->sys = (float)(-2.0 * ty / (double)c->height);",
+     "k->sys = (float)(2.0 * ty / (double)c->height);"),
+    ("camera right vector sign", "R[0] = F[1] * c->up[2] - F[2] * c->up[1];",
+     "R[0] = F[2] * c->up[1] - F[1] * c->up[2];"),
+    ("slab test uses the wrong face", "float tb = (1.0f - o[c]) * inv;", "float tb = (0.5f - o[c]) * inv;"),
+    ("fixed step doubled", "tn = fmaf((float)(k + 1), (float)J->st->h, tin);",
+     "tn = fmaf((float)(k + 1), 2.0f * (float)J->st->h, tin);"),
+]
+
+
+def _pins(cfg1):
+    """The pins of test_oracle_pins, run against whatever library is loaded."""
+    O = orc.Oracle(cfg1)
+    yield lambda: P.test_bspline_golden_closed_forms()
+    yield lambda: P.test_bspline_half_open_support()
+    yield lambda: P.test_partition_of_unity((2, 2, 2), (3, 3, 3), (0.4, 0.2), (0.3, 0.6, 0.45))
+    yield lambda: P.test_polynomial_reproduction((2, 2, 2), ([0.1, -1.0, 2.0], [0.2, 0.5, -0.3], [1.0, 0.0, 1.0]),
+                                                 "carried")
+    yield lambda: P.test_tensor_product_special_case()
+    yield lambda: P.test_lookup_tiny_partition()
+    yield lambda: P.test_bezier_blocks_equal_bspline_evaluation(cfg1, O)
+    for which in ("ortho_z", "oblique", "persp"):
+        yield lambda which=which: P.test_ray_setup_matches_double(which)
+    yield lambda: P.test_ray_ortho_z_exact()
+    for mode in ("fixed", "heuristic"):
+        for which in ("ortho_z", "persp"):
+            yield lambda mode=mode, which=which: P.test_closed_form_opacity(cfg1, mode, which)
+    yield lambda: P.test_tf_linear_interpolation(cfg1)
+    yield lambda: P.heuristic_count_pin(cfg1, O)
+    yield lambda: P.test_heuristic_step_counts_anisotropic()
+    yield lambda: P.test_early_termination_and_miss(O)
+
+
+def test_unmutated_source_passes_the_same_pins(cfg1):
+    for pin in _pins(cfg1):
+        pin()
+
+
+@pytest.mark.parametrize("name,old,new", MUTANTS, ids=[m[0] for m in MUTANTS])
+def test_planted_mistake_is_caught(name, old, new, tmp_path, cfg1):
+    src = open(SRC).read()
+    assert src.count(old) == 1, f"mutation site not unique: {old}"
+    msrc = tmp_path / "oracle_mutant.c"
+    msrc.write_text(src.replace(old, new))
+    lib = orc.build(force=True, src=str(msrc), lib=str(tmp_path / "liboracle_mutant.so"))
+    prev = orc.use_library(lib)
+    caught = None
+    try:
+        for pin in _pins(cfg1):
+            try:
+                pin()
+            except (AssertionError, StopIteration, ValueError, IndexError) as exc:
+                caught = exc
+                break
+    finally:
+        orc.use_library(prev)
+    assert caught is not None, f"no pin caught: {name}"
