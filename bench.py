@@ -1,0 +1,275 @@
+"""Benchmark: direct volume ray casting of an LR-spline on one GB300.
+
+One step = one frame of the whole per-frame path (ray setup, forest look-up,
+element reuse, Bezier evaluation, Eq. 4 steps, transfer function, Alg. 2
+compositing) at 1920x1080 on the MR-like scalar tricubic volume (~174k
+elements, perspective camera at distance 1.8, fovy 40 deg, alpha_stop 0.99).
+The once-per-volume change of basis and forest build are timed separately
+(`setup`).  Metric: Gsamples/s (a sample = one field evaluation that is
+composited); ms/frame beside it.
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun each rank renders its own frame (replicas; weak scaling) and
+rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+WIDTH, HEIGHT = 1920, 1080
+BLOCKS = (64, 64, 64)
+METRIC = "Gsamples/s (1080p frame, MR-like tricubic LR-spline, Eq. 4 steps)"
+L2_FLUSH_BYTES = 512 << 20
+
+# Algorithmic FP32 flops per composited sample of the tricubic scalar path
+# (an FMA counts 2): sample position 3 FMA + 6 clamps = 12; local coordinates
+# 3 x 3 = 9; Bernstein basis 3 x 9 = 27; tensor contraction 64+16+4 FMA = 168;
+# transfer function 13; Alg. 2 compositing 15 (log2/exp2 counted as 1 each).
+FLOP_PER_SAMPLE_P3_SCALAR = 12 + 9 + 27 + 168 + 13 + 15
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def _workload():
+    from paper_1707_01170_gb300.synth import volumes as V
+    vol = V.load_config(2)
+    tf, cam = V.config2_render(WIDTH, HEIGHT)
+    tf.table = np.asarray(tf.table, dtype=np.float32).astype(np.float64)
+    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
+    return vol, tf, cam, step
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        self.lines = []
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.lines = [ln for ln in out.splitlines() if ln.strip()]
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(vol, tf, cam, step, pixels: int = 384, seed: int = 11):
+    """The FP64 oracle, as it stands, on a seeded pixel subset of the same frame."""
+    from oracle.oracle import Oracle
+    rng = np.random.default_rng(seed)
+    pix = np.stack([rng.integers(0, cam.width, pixels), rng.integers(0, cam.height, pixels)], axis=1).astype(np.int32)
+    orc = Oracle(vol)
+    t0 = time.perf_counter()
+    _, st = orc.render(cam, tf, step, pixels=pix)
+    dt = time.perf_counter() - t0
+    return {"value": st["samples"] / dt / 1e9, "unit": "Gsamples/s", "cores": orc.threads, "kind": "oracle",
+            "sample": f"{pixels} seeded pixels of the same 1920x1080 frame ({st['samples']} samples, {dt:.1f} s)"}
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    vol, tf, cam, step = _workload()
+    from oracle.oracle import Oracle
+    orc = Oracle(vol)
+    rng = np.random.default_rng(5)
+    times, samples = [], 0
+    for k in range(args.warmup + args.steps):
+        pix = np.stack([rng.integers(0, cam.width, 96), rng.integers(0, cam.height, 96)], axis=1).astype(np.int32)
+        t0 = time.perf_counter()
+        _, st = orc.render(cam, tf, step, pixels=pix)
+        dt = time.perf_counter() - t0
+        if k >= args.warmup:
+            times.append(dt)
+            samples += st["samples"]
+    tot = sum(times)
+    val = samples / tot / 1e9
+    line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "cfg2 MR-like tricubic LR-spline, 1920x1080 persp, Eq. 4 steps; "
+                                   "each step = 96 seeded pixels of the frame"},
+            "cpu_baseline": {"value": val, "unit": "Gsamples/s", "cores": orc.threads, "kind": "oracle",
+                             "sample": "96 seeded pixels per step"},
+            "e2e": {"value": val, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def run_ours(args):
+    import torch
+    ws, rank, local = _dist()
+    torch.cuda.set_device(local)
+    dist = None
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    from paper_1707_01170_gb300 import lrvol as lv
+
+    vol, tf, cam, step = _workload()
+    stream = torch.cuda.current_stream()
+    # ---- setup (once per volume) ----
+    t0 = time.perf_counter()
+    gv = lv.Volume(vol)
+    t1 = time.perf_counter()
+    gv.build_accel(BLOCKS, stream=stream)
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    gv.to_bezier(stream=stream)
+    torch.cuda.synchronize()
+    t3 = time.perf_counter()
+    ccam, ctf, cstep = lv.make_camera(cam), lv.make_tf(tf), lv.make_step(step)
+    out = torch.zeros((HEIGHT, WIDTH, 4), dtype=torch.float32, device="cuda")
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    for _ in range(args.warmup):
+        gv.render(ccam, ctf, cstep, out=out, stream=stream)
+    torch.cuda.synchronize()
+    st = gv.stats()
+    samples_per_frame = st["samples"]
+
+    # ---- timed region: K frames, L2 flushed between frames (flush not timed) ----
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(torch.cuda.current_device()) as clk:
+        w0 = time.perf_counter()
+        for k in range(args.steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            gv.render(ccam, ctf, cstep, out=out, stream=stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        wall = time.perf_counter() - w0
+    if dist:
+        dist.barrier()
+    per = [a.elapsed_time(b) for a, b in evs]
+    dev_ms = float(sum(per))
+    if dist:
+        t = torch.tensor([dev_ms, wall], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms, wall = float(t[0]), float(t[1])
+    total_samples = samples_per_frame * args.steps * ws
+    value = total_samples / (dev_ms / 1e3) / 1e9
+    ms_per_step = dev_ms / args.steps
+
+    # ---- end to end through the C ABI with host buffers ----
+    host = torch.empty((HEIGHT, WIDTH, 4), dtype=torch.float32, pin_memory=True)
+    e2e_steps = max(3, min(args.steps, 10))
+    torch.cuda.synchronize()
+    e0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        gv.render(ccam, ctf, cstep, out=out, stream=stream)   # camera/TF/step travel as kernel parameters
+        host.copy_(out, non_blocking=True)
+        stream.synchronize()
+    e2e_s = (time.perf_counter() - e0) / e2e_steps
+    import ctypes
+    h2d = ctypes.sizeof(lv.Camera) + ctypes.sizeof(lv.TF) + ctypes.sizeof(lv.Step)
+    e2e = {"value": samples_per_frame * ws / e2e_s / 1e9, "unit": "Gsamples/s", "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": HEIGHT * WIDTH * 16, "ms_per_step": 1e3 * e2e_s}
+
+    if rank != 0:
+        gv.close()
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    flop = FLOP_PER_SAMPLE_P3_SCALAR * samples_per_frame
+    achieved = flop / (ms_per_step / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "kernel": "k_render<3,0>", "flop_per_sample": FLOP_PER_SAMPLE_P3_SCALAR,
+            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no FP32 figure measured)"}
+    line = {"metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": "cfg2: MR-like scalar tricubic LR-spline, 174000 elements, 1920x1080 persp "
+                                   "fovy 40 at distance 1.8, Eq. 4 heuristic steps, xi 1/256, alpha_stop 0.99, "
+                                   f"forest {BLOCKS[0]}^3",
+                       "l2": "flushed between frames (512 MB write, outside the timed events)",
+                       "samples_per_frame": samples_per_frame, "rays_hit": st["rays_hit"],
+                       "lookups_per_frame": st["lookups"], "parallelism": f"replicas x{ws}"},
+            "wall_s": wall, "gpu_launches": args.steps,
+            "roofline": roof, "e2e": e2e, "clocks": clk.summary(),
+            "setup": {"create_s": t1 - t0, "build_accel_s": t2 - t1, "to_bezier_s": t3 - t2,
+                      "forest_depth": [st["depth_min"], st["depth_max"], st["depth_mean"], st["depth_var"]],
+                      "n_nodes": st["n_nodes"], "incidence_entries": st["incidence_entries"]}}
+    if not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(vol, tf, cam, step)
+    print(json.dumps(line))
+    gv.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up frames
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,177 @@
+/*
+ * lrvol.h -- C ABI of liblrvol: direct volume ray casting of trivariate
+ * LR-splines on one GPU (sm_103a).
+ *
+ * Method: Fuchs, Barrowclough, Hjelmervik, Dahl, "Direct interactive
+ * visualization of locally refined spline volumes for scalar and vector
+ * fields".  An LR-spline f = sum_i c_i gamma_i N_i (Eq. 2) is converted once
+ * to one Bezier block per element (Sec. 3.2.3), elements are found through a
+ * k-d forest (Sec. 3.2.1, Alg. 1), and each pixel ray is sampled at a fixed
+ * step or at the adaptive distance of Eq. 4, mapped through a 1D transfer
+ * function and composited front to back (Alg. 2).
+ *
+ * Conventions for every function:
+ *   - returns an lrvol_status (0 = LRVOL_OK); no C++ exception and no exit()
+ *     crosses this boundary; lrvol_last_error() describes the last failure
+ *     of the calling thread;
+ *   - pointers named *_dev are device pointers on the handle's device, owned
+ *     by the caller; host pointers are read during the call only;
+ *   - `stream` is a cudaStream_t (NULL = the legacy default stream); calls
+ *     that take one are asynchronous on it, except where stated;
+ *   - one handle may be used by one stream at a time;
+ *   - element ids are positions in the caller's element array (0-based);
+ *     0xFFFFFFFF marks "no element" (a point outside [0,1]^3).
+ *
+ * Boxes are half open, [lo, hi); the upper domain face x = 1 belongs to the
+ * element whose hi is 1.  Ties at a split plane go to the ">=" side, as in
+ * Alg. 1.
+ */
+#ifndef LRVOL_H
+#define LRVOL_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lrvol_s *lrvol_t; /* opaque; owns all device copies of one volume */
+
+typedef enum {
+  LRVOL_OK = 0,
+  LRVOL_ERR_ARG = -1,         /* invalid argument (null pointer, bad size, bad enum) */
+  LRVOL_ERR_OOM = -2,         /* device or host allocation failed */
+  LRVOL_ERR_CUDA = -3,        /* a CUDA runtime call failed */
+  LRVOL_ERR_STATE = -4,       /* call out of order (e.g. render before to_bezier/build_accel) */
+  LRVOL_ERR_BOUNDS = -5,      /* a kernel's bounds check tripped (index outside its buffer) */
+  LRVOL_ERR_TIMEOUT = -6,     /* a bounded device-side wait gave up */
+  LRVOL_ERR_UNSUPPORTED = -7  /* valid but not supported by this build (e.g. degree > 3 in render) */
+} lrvol_status;
+
+enum { LRVOL_ORTHO = 0, LRVOL_PERSP = 1 };
+enum { LRVOL_STEP_FIXED = 0, LRVOL_STEP_HEURISTIC = 1 };
+enum { LRVOL_FIELD_SCALAR = 0, LRVOL_FIELD_MAGNITUDE = 1, LRVOL_FIELD_COMPONENT = 2 };
+enum { LRVOL_STORE_F32 = 0, LRVOL_STORE_F16 = 1, LRVOL_STORE_BF16 = 2 };
+
+/* Camera.  Ray of pixel (i, j), row j = 0 at the top, in FP32 with this exact
+ * order of operations (fmaf = fused multiply-add, all other ops IEEE-rounded):
+ *   FP64, once: F = normalize(target - eye), R = normalize(cross(F, up)),
+ *     U = cross(R, F); ty = tan(fovy/2) (persp) or extent/2 (ortho);
+ *     tx = ty*width/height; sxs = (float)(2*tx/width), sxo = (float)(-tx),
+ *     sys = (float)(-2*ty/height), syo = (float)ty; E,F,R,U rounded to float.
+ *   a = fmaf(i + 0.5f, sxs, sxo); b = fmaf(j + 0.5f, sys, syo)
+ *   persp: d_c = fmaf(a, R_c, fmaf(b, U_c, F_c)); n = sqrtf(fmaf(dx,dx, fmaf(dy,dy, dz*dz)));
+ *          d_c = d_c / n; o = E
+ *   ortho: o_c = fmaf(a, R_c, fmaf(b, U_c, E_c)); d = F
+ *   slab test against [0,1]^3 from t = 0 gives [t_in, t_out); a miss writes 0.
+ * Rows [row_begin, row_end) are rendered (both 0: all rows); other rows of
+ * the output are left untouched.  This is the screen-space sharding hook. */
+typedef struct {
+  int32_t projection; /* LRVOL_ORTHO | LRVOL_PERSP */
+  int32_t width, height;
+  double eye[3], target[3], up[3];
+  double fovy;   /* persp: full vertical field of view, radians */
+  double extent; /* ortho: full height of the view window, world units */
+  int32_t row_begin, row_end;
+} lrvol_camera;
+
+/* Transfer function: 256 RGBA entries spanning [vmin, vmax]; value v maps to
+ * x = clamp((v - vmin)/(vmax - vmin), 0, 1) * 255 and the entries floor(x)
+ * and floor(x)+1 are linearly interpolated (colour not premultiplied).
+ * Copied during the call. */
+typedef struct {
+  float rgba[256][4];
+  double vmin, vmax;
+} lrvol_tf;
+
+/* Sampling and compositing (Sec. 4.2, Alg. 2, Eq. 4).
+ *   FIXED:     t_k = fmaf((float)k, h, t_in)
+ *   HEURISTIC: t_{k+1} = t_k + ds(e_k), ds(e) = (float)(2^-d * min side of e),
+ *              d = max(p1,p2,p3), e_k the element holding sample k (Eq. 4)
+ * Sample k sits at p_k = clamp(fmaf(t_k, d, o), 0, 1); its segment is
+ * min(t_{k+1}, t_out) - t_k; T = (1 - alpha_src)^(segment/xi);
+ * C += (1-T)(1-alpha) C_src; alpha += (1-T)(1-alpha); the ray stops at
+ * t_out or once alpha >= alpha_stop.  Output is premultiplied RGBA. */
+typedef struct {
+  int32_t mode;      /* LRVOL_STEP_FIXED | LRVOL_STEP_HEURISTIC */
+  int32_t field;     /* LRVOL_FIELD_SCALAR | _MAGNITUDE (|v| of a 3-vector) | _COMPONENT */
+  int32_t component; /* for LRVOL_FIELD_COMPONENT */
+  double h;          /* fixed step (FIXED only) */
+  double xi;         /* standard length of Alg. 2 */
+  double alpha_stop; /* early ray termination threshold; 1.0 = only when fully opaque */
+} lrvol_step;
+
+/* Diagnostics; the depth rows match the paper's tables (Sec. 4.3). */
+typedef struct {
+  int64_t n_elem, n_basis, n_nodes;
+  int32_t blocks[3];
+  int32_t depth_min, depth_max; /* tree depth per forest block (0: the head names the element) */
+  double depth_mean, depth_var;
+  int64_t incidence_entries;    /* element-to-B-spline pairs used by the change of basis */
+  int64_t bytes_device;         /* device memory held by the handle */
+  int64_t samples, lookups, rays_hit; /* counters of the last render call */
+} lrvol_stats_t;
+
+/* Create a volume from an LR-spline (Eq. 2).  Synchronous.
+ * deg[3]     tri-degree p, each in 1..4 (render needs all equal, 1..3)
+ * ncomp      1 (scalar) or 3 (vector field)
+ * elem_box   n_elem x 6 doubles: lo x,y,z then hi x,y,z; a box partition of [0,1]^3
+ * knots      n_basis x (p1+2 + p2+2 + p3+2) doubles: each LR B-spline's local
+ *            knot vectors, x then y then z, non-decreasing
+ * coef       n_basis x ncomp doubles (c_i); weight: n_basis doubles (gamma_i)
+ * The inputs are copied to the current device; the caller keeps ownership.
+ * Errors: LRVOL_ERR_ARG for null pointers, sizes < 1, degrees out of range,
+ * boxes outside [0,1] or empty, decreasing knots; LRVOL_ERR_OOM; LRVOL_ERR_CUDA. */
+int lrvol_create(const int32_t deg[3], int32_t ncomp, int64_t n_elem, const double *elem_box,
+                 int64_t n_basis, const double *knots, const double *coef, const double *weight,
+                 lrvol_t *out);
+
+/* Build the k-d forest (Sec. 3.2.1): blocks[0] x blocks[1] x blocks[2]
+ * regular blocks (each a power of two, at most 1024), one depth-balanced k-d
+ * tree per block over the elements meeting it; split planes are element
+ * faces rounded up to FP32 so that FP32 queries decide exactly as in FP64.
+ * The tree is built on the host and uploaded on `stream`.
+ * Errors: LRVOL_ERR_ARG (blocks not powers of two), LRVOL_ERR_OOM, LRVOL_ERR_CUDA. */
+int lrvol_build_accel(lrvol_t vol, const int32_t blocks[3], void *stream);
+
+/* Change of basis to Bezier blocks (Sec. 3.2.3), FP64 on the GPU by blossoming
+ * each incident B-spline's univariate factors over the element (exact up to
+ * rounding); blocks are stored as `storage` (LRVOL_STORE_F32 in this build)
+ * for rendering and kept in FP64 for lrvol_get_bezier.
+ * Errors: LRVOL_ERR_ARG, LRVOL_ERR_UNSUPPORTED (F16/BF16 not built), LRVOL_ERR_OOM, LRVOL_ERR_CUDA. */
+int lrvol_to_bezier(lrvol_t vol, int32_t storage, void *stream);
+
+/* Render one image into rgba_dev (height x width x 4 floats, row major,
+ * premultiplied RGBA, caller-owned device buffer).  Needs build_accel and
+ * to_bezier first (else LRVOL_ERR_STATE).  Asynchronous on `stream`.
+ * Errors: LRVOL_ERR_ARG (bad camera/step, null), LRVOL_ERR_STATE,
+ * LRVOL_ERR_UNSUPPORTED (non-isotropic degree or degree > 3), LRVOL_ERR_CUDA. */
+int lrvol_render(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                 float *rgba_dev, void *stream);
+
+/* Element look-up through the forest (Alg. 1) for n FP32 points (n x 3,
+ * device) into elem_dev (n uint32, device).  Needs build_accel. */
+int lrvol_lookup(lrvol_t vol, const float *pts_dev, int64_t n, uint32_t *elem_dev, void *stream);
+
+/* Field values (Eq. 2 through the Bezier blocks, FP32) at n FP32 points into
+ * val_dev (n x ncomp floats, device).  Needs build_accel and to_bezier. */
+int lrvol_eval(lrvol_t vol, const float *pts_dev, int64_t n, float *val_dev, void *stream);
+
+/* Copy the FP64 Bezier blocks to host_out: n_elem x ncomp x (p3+1) x (p2+1)
+ * x (p1+1) doubles, x index fastest.  Synchronous. */
+int lrvol_get_bezier(lrvol_t vol, double *host_out);
+
+/* Statistics of the forest and of the last render.  Synchronous; also
+ * reports a pending device-side status (LRVOL_ERR_BOUNDS / _TIMEOUT). */
+int lrvol_stats(lrvol_t vol, lrvol_stats_t *out);
+
+const char *lrvol_status_string(int status);
+const char *lrvol_last_error(void);
+
+/* Release all device memory of the handle (synchronises the device first). */
+void lrvol_destroy(lrvol_t vol);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LRVOL_H */

@@ -1,0 +1,128 @@
+// Internal declarations of liblrvol (host code and kernels).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "lrvol.h"
+
+namespace lrvol {
+
+constexpr uint32_t kLeaf = 0x80000000u;   // forest reference: bit 31 set = element id in bits 0..30
+constexpr uint32_t kNone = 0xFFFFFFFFu;   // "no element"
+constexpr int kMaxDepth = 96;             // traversal bound: a deeper tree is reported as LRVOL_ERR_BOUNDS
+constexpr int kMaxDeg = 4;
+constexpr int kMaxSamplesPerRay = 1 << 24;  // a longer ray stops with LRVOL_ERR_TIMEOUT
+
+// Device status word values (first error wins).
+enum : uint32_t { kStatusOk = 0, kStatusBounds = 1, kStatusTimeout = 2 };
+
+// Counters written by render (one slot each).
+enum { kCntSamples = 0, kCntLookups = 1, kCntRays = 2, kCntTiles = 3, kNumCounters = 8 };
+
+// Element record, 4 x float4 = 64 bytes:
+//   a = {lo_ru.x, lo_ru.y, lo_ru.z, ds}   lower corner rounded up to FP32 (membership), Eq. 4 step
+//   b = {hi_ru.x, hi_ru.y, hi_ru.z, 0}    upper corner rounded up (+inf where hi = 1)
+//   c = {dlo.x, dlo.y, dlo.z, 0}          (float)(lo_ru - lo) >= 0, for accurate local coordinates
+//   d = {iw.x, iw.y, iw.z, 0}             (float)(1 / (hi - lo))
+// Local coordinate u = ((p - lo_ru) + dlo) * iw.
+struct ElemRec {
+  float4 a, b, c, d;
+};
+
+// Forest node, 16 bytes: split value (FP32, rounded up), axis, child refs for
+// p[axis] < split and p[axis] >= split.  A ref with kLeaf set names an element.
+struct Node {
+  uint32_t split_bits;
+  uint32_t axis;
+  uint32_t child[2];
+};
+
+struct ForestView {
+  const uint32_t *head;  // blocks[2] x blocks[1] x blocks[0], x fastest
+  const uint4 *nodes;
+  int64_t n_nodes;
+  int bx, by, bz;        // block counts (powers of two)
+  float fbx, fby, fbz;
+};
+
+struct RayConsts {
+  float E[3], F[3], R[3], U[3];
+  float sxs, sxo, sys, syo;
+  int persp;
+};
+
+struct RenderParams {
+  const ElemRec *elem;
+  int64_t n_elem;
+  const float *bez;       // FP32 Bezier blocks
+  int elem_stride;        // floats per element
+  int comp_stride;        // floats per component (multiple of 4)
+  int comp;               // component evaluated (FIELD_COMPONENT / SCALAR)
+  ForestView forest;
+  float *out;
+  int width, height, row_begin, row_end;
+  RayConsts ray;
+  int mode;               // LRVOL_STEP_*
+  float h, inv_xi, alpha_stop;
+  float tf_off, tf_scale; // x = (v - tf_off) * tf_scale in [0, 255]
+  unsigned long long *counters;
+  uint32_t *status;
+  float4 tf[256];
+};
+
+struct Volume;
+
+}  // namespace lrvol
+
+struct lrvol_s {
+  int device = 0;
+  int p[3] = {0, 0, 0};
+  int nc = 1;
+  int64_t n_elem = 0, n_basis = 0;
+  int kw = 0;  // knots per B-spline
+  std::vector<double> box, knots, coef, weight;
+
+  // device copies of the spline
+  double *d_box = nullptr, *d_knots = nullptr, *d_coef = nullptr, *d_weight = nullptr;
+  // change of basis
+  int64_t *d_inc_ptr = nullptr;
+  int32_t *d_inc_idx = nullptr;
+  int64_t inc_entries = 0;
+  double *d_bez64 = nullptr;
+  float *d_bez32 = nullptr;
+  int storage = -1;
+  int comp_stride = 0, elem_stride = 0;
+  lrvol::ElemRec *d_elem = nullptr;
+  bool have_bezier = false;
+  // forest
+  uint32_t *d_head = nullptr;
+  uint4 *d_nodes = nullptr;
+  int64_t n_nodes = 0;
+  int blocks[3] = {0, 0, 0};
+  int depth_min = 0, depth_max = 0;
+  double depth_mean = 0, depth_var = 0;
+  bool have_accel = false;
+  // scratch
+  unsigned long long *d_counters = nullptr;
+  uint32_t *d_status = nullptr;
+  int64_t bytes_device = 0;
+};
+
+namespace lrvol {
+
+// kernels.cu
+cudaError_t launch_to_bezier(const lrvol_s *v, cudaStream_t s);
+cudaError_t launch_elem_records(const lrvol_s *v, cudaStream_t s);
+cudaError_t launch_lookup(const lrvol_s *v, const float *pts, int64_t n, uint32_t *out, cudaStream_t s);
+cudaError_t launch_eval(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s);
+cudaError_t launch_render(const RenderParams &prm, int degree, int field, cudaStream_t s);
+
+// host.cpp
+void camera_consts(const lrvol_camera *c, RayConsts *k);
+ForestView forest_view(const lrvol_s *v);
+
+}  // namespace lrvol

@@ -1,0 +1,238 @@
+"""Python binding of liblrvol (include/lrvol.h): argument marshalling only.
+
+Device buffers and streams come from PyTorch; every step of the path runs in
+the library's CUDA kernels.  There is no CPU fallback: if liblrvol.so is
+missing or no GPU is present, the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblrvol.so")
+
+OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_BOUNDS, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
+ORTHO, PERSP = 0, 1
+STEP_FIXED, STEP_HEURISTIC = 0, 1
+FIELD_SCALAR, FIELD_MAGNITUDE, FIELD_COMPONENT = 0, 1, 2
+STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
+NONE = 0xFFFFFFFF
+
+EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
+            "lrvol_eval", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
+            "lrvol_destroy"]
+
+
+class LrvolError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        super().__init__(f"{what}: status {status} ({_lib_str(status)}): {last_error()}")
+        self.status = status
+
+
+class Camera(ctypes.Structure):
+    _fields_ = [("projection", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
+                ("eye", ctypes.c_double * 3), ("target", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
+                ("fovy", ctypes.c_double), ("extent", ctypes.c_double),
+                ("row_begin", ctypes.c_int32), ("row_end", ctypes.c_int32)]
+
+
+class TF(ctypes.Structure):
+    _fields_ = [("rgba", (ctypes.c_float * 4) * 256), ("vmin", ctypes.c_double), ("vmax", ctypes.c_double)]
+
+
+class Step(ctypes.Structure):
+    _fields_ = [("mode", ctypes.c_int32), ("field", ctypes.c_int32), ("component", ctypes.c_int32),
+                ("h", ctypes.c_double), ("xi", ctypes.c_double), ("alpha_stop", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("n_elem", ctypes.c_int64), ("n_basis", ctypes.c_int64), ("n_nodes", ctypes.c_int64),
+                ("blocks", ctypes.c_int32 * 3), ("depth_min", ctypes.c_int32), ("depth_max", ctypes.c_int32),
+                ("depth_mean", ctypes.c_double), ("depth_var", ctypes.c_double),
+                ("incidence_entries", ctypes.c_int64), ("bytes_device", ctypes.c_int64),
+                ("samples", ctypes.c_int64), ("lookups", ctypes.c_int64), ("rays_hit", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        d = {k: getattr(self, k) for k, _ in self._fields_}
+        d["blocks"] = list(self.blocks)
+        return d
+
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load liblrvol.so (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise RuntimeError(f"liblrvol.so not built at {path}: run __graft_entry__.build()")
+        L = ctypes.CDLL(path)
+        vp, i32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+        L.lrvol_create.restype = ctypes.c_int
+        L.lrvol_create.argtypes = [vp, i32, i64, vp, i64, vp, vp, vp, ctypes.POINTER(vp)]
+        L.lrvol_build_accel.restype = ctypes.c_int
+        L.lrvol_build_accel.argtypes = [vp, vp, vp]
+        L.lrvol_to_bezier.restype = ctypes.c_int
+        L.lrvol_to_bezier.argtypes = [vp, i32, vp]
+        L.lrvol_render.restype = ctypes.c_int
+        L.lrvol_render.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step), vp, vp]
+        L.lrvol_lookup.restype = ctypes.c_int
+        L.lrvol_lookup.argtypes = [vp, vp, i64, vp, vp]
+        L.lrvol_eval.restype = ctypes.c_int
+        L.lrvol_eval.argtypes = [vp, vp, i64, vp, vp]
+        L.lrvol_get_bezier.restype = ctypes.c_int
+        L.lrvol_get_bezier.argtypes = [vp, vp]
+        L.lrvol_stats.restype = ctypes.c_int
+        L.lrvol_stats.argtypes = [vp, ctypes.POINTER(Stats)]
+        L.lrvol_status_string.restype = ctypes.c_char_p
+        L.lrvol_status_string.argtypes = [ctypes.c_int]
+        L.lrvol_last_error.restype = ctypes.c_char_p
+        L.lrvol_last_error.argtypes = []
+        L.lrvol_destroy.restype = None
+        L.lrvol_destroy.argtypes = [vp]
+        _lib = L
+    return _lib
+
+
+def _lib_str(status: int) -> str:
+    try:
+        return load().lrvol_status_string(status).decode()
+    except Exception:  # library not loadable
+        return "?"
+
+
+def last_error() -> str:
+    try:
+        return load().lrvol_last_error().decode()
+    except Exception:
+        return ""
+
+
+def _check(status: int, what: str) -> None:
+    if status != OK:
+        raise LrvolError(status, what)
+
+
+def _stream_ptr(stream) -> int | None:
+    if stream is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    return getattr(stream, "cuda_stream", stream)
+
+
+def make_camera(cam, row_begin: int = 0, row_end: int = 0) -> Camera:
+    """From any object with projection ('ortho'|'persp'), width, height, eye, target, up, fovy, extent."""
+    c = Camera()
+    c.projection = PERSP if cam.projection == "persp" else ORTHO
+    c.width, c.height = int(cam.width), int(cam.height)
+    c.eye = (ctypes.c_double * 3)(*[float(v) for v in cam.eye])
+    c.target = (ctypes.c_double * 3)(*[float(v) for v in cam.target])
+    c.up = (ctypes.c_double * 3)(*[float(v) for v in cam.up])
+    c.fovy, c.extent = float(cam.fovy), float(cam.extent)
+    c.row_begin, c.row_end = int(row_begin), int(row_end)
+    return c
+
+
+def make_tf(tf) -> TF:
+    """From any object with table (256 x 4), vmin, vmax; the table is rounded to FP32."""
+    t = TF()
+    tab = np.ascontiguousarray(np.asarray(tf.table, dtype=np.float32).reshape(256, 4))
+    ctypes.memmove(ctypes.addressof(t.rgba), tab.ctypes.data, tab.nbytes)
+    t.vmin, t.vmax = float(tf.vmin), float(tf.vmax)
+    return t
+
+
+def make_step(step) -> Step:
+    s = Step()
+    s.mode = STEP_HEURISTIC if step.mode == "heuristic" else STEP_FIXED
+    s.field = {"scalar": FIELD_SCALAR, "magnitude": FIELD_MAGNITUDE, "component": FIELD_COMPONENT}[step.field]
+    s.component = int(step.component)
+    s.h, s.xi, s.alpha_stop = float(step.h), float(step.xi), float(step.alpha_stop)
+    return s
+
+
+class Volume:
+    """One LR-spline volume resident on the current CUDA device (lrvol_t)."""
+
+    def __init__(self, vol):
+        L = load()
+        deg = np.ascontiguousarray([int(v) for v in vol.deg], dtype=np.int32)
+        self._arrays = [np.ascontiguousarray(a, dtype=np.float64) for a in
+                        (vol.elem_box, vol.knots, vol.coef, vol.weight)]
+        box, knots, coef, weight = self._arrays
+        self.ncomp = int(coef.shape[1])
+        self.n_elem = int(box.shape[0])
+        self.deg = [int(v) for v in deg]
+        h = ctypes.c_void_p()
+        _check(L.lrvol_create(deg.ctypes.data, self.ncomp, self.n_elem, box.ctypes.data, int(knots.shape[0]),
+                              knots.ctypes.data, coef.ctypes.data, weight.ctypes.data, ctypes.byref(h)),
+               "lrvol_create")
+        self._h = h
+        self._arrays = None
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lrvol_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+    @property
+    def handle(self):
+        return self._h
+
+    def build_accel(self, blocks=(64, 64, 64), stream=None):
+        b = np.ascontiguousarray(blocks, dtype=np.int32)
+        _check(load().lrvol_build_accel(self._h, b.ctypes.data, _stream_ptr(stream)), "lrvol_build_accel")
+        return self
+
+    def to_bezier(self, storage: int = STORE_F32, stream=None):
+        _check(load().lrvol_to_bezier(self._h, int(storage), _stream_ptr(stream)), "lrvol_to_bezier")
+        return self
+
+    def render(self, cam, tf, step, out=None, stream=None, row_begin: int = 0, row_end: int = 0):
+        """Render into a (H, W, 4) float32 CUDA tensor (allocated if out is None)."""
+        import torch
+        c = cam if isinstance(cam, Camera) else make_camera(cam, row_begin, row_end)
+        t = tf if isinstance(tf, TF) else make_tf(tf)
+        s = step if isinstance(step, Step) else make_step(step)
+        if out is None:
+            out = torch.zeros((c.height, c.width, 4), dtype=torch.float32, device="cuda")
+        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
+        assert out.numel() == c.height * c.width * 4
+        _check(load().lrvol_render(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), out.data_ptr(),
+                                   _stream_ptr(stream)), "lrvol_render")
+        return out
+
+    def lookup(self, pts, out=None, stream=None):
+        import torch
+        assert pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous() and pts.shape[-1] == 3
+        n = pts.numel() // 3
+        if out is None:
+            out = torch.empty(n, dtype=torch.int32, device=pts.device)
+        _check(load().lrvol_lookup(self._h, pts.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)), "lrvol_lookup")
+        return out
+
+    def eval(self, pts, out=None, stream=None):
+        import torch
+        assert pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous() and pts.shape[-1] == 3
+        n = pts.numel() // 3
+        if out is None:
+            out = torch.empty((n, self.ncomp), dtype=torch.float32, device=pts.device)
+        _check(load().lrvol_eval(self._h, pts.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)), "lrvol_eval")
+        return out
+
+    def get_bezier(self) -> np.ndarray:
+        p = self.deg
+        out = np.empty((self.n_elem, self.ncomp, p[2] + 1, p[1] + 1, p[0] + 1), dtype=np.float64)
+        _check(load().lrvol_get_bezier(self._h, out.ctypes.data), "lrvol_get_bezier")
+        return out
+
+    def stats(self) -> dict:
+        s = Stats()
+        _check(load().lrvol_stats(self._h, ctypes.byref(s)), "lrvol_stats")
+        return s.as_dict()

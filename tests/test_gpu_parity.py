@@ -1,0 +1,300 @@
+"""GPU parity: the CUDA path (through the C ABI) against the FP64 CPU oracle.
+
+Bars (from the arithmetic of each step):
+  element ids        bit-exact (FP32 queries, split planes rounded up: the
+                     FP32 comparison equals the FP64 one);
+  per-sample values  |v_gpu - v_orc| <= 1e-5 * max(|v_orc|, max|c|);
+  Bezier blocks      GPU FP64 blossoming vs oracle interpolation within
+                     1e-12 * max|c| (both exact up to rounding);
+  images             RMSE <= 1e-4 in [0,1] RGBA (sample positions, element
+                     choices and step lengths are identical FP32 decisions on
+                     both sides, so only FP32 vs FP64 arithmetic differs).
+"""
+import zlib
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from oracle.oracle import NONE, Oracle
+from paper_1707_01170_gb300 import lrvol as lv
+from paper_1707_01170_gb300.synth import volumes as V
+from paper_1707_01170_gb300.synth.lrgen import LRVolume
+
+pytestmark = pytest.mark.gpu
+
+RMSE_TOL = 1e-4
+VAL_TOL = 1e-5
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    lv.load()
+
+
+def _f32_tf(tf):
+    tf.table = np.asarray(tf.table, dtype=np.float32).astype(np.float64)
+    return tf
+
+
+def _with_coef(vol, coef):
+    return LRVolume(deg=vol.deg, elem_box=vol.elem_box, knots=vol.knots,
+                    coef=np.asarray(coef, dtype=np.float64).reshape(vol.n_basis, -1), weight=vol.weight, grid=vol.grid)
+
+
+def _rmse(a, b):
+    return float(np.sqrt(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2)))
+
+
+def _probe_points(vol, n, seed, blocks=(64, 64, 64)):
+    """Uniform points plus points on element faces, forest block faces, 0 and 1."""
+    rng = np.random.default_rng(seed)
+    X = rng.random((n, 3)).astype(np.float32)
+    faces = np.unique(vol.elem_box.astype(np.float32))
+    m = rng.random((n, 3)) < 0.3
+    X[m] = rng.choice(faces, size=int(m.sum()))
+    bf = np.unique(np.concatenate([np.arange(b + 1) / b for b in blocks])).astype(np.float32)
+    m = rng.random((n, 3)) < 0.1
+    X[m] = rng.choice(bf, size=int(m.sum()))
+    edges = np.array([[0, 0, 0], [1, 1, 1], [1, 0, 0], [0, 1, 0], [0, 0, 1], [1, 1, 0.5], [0.5, 0.5, 1]], np.float32)
+    out = np.array([[1.0000001, 0.5, 0.5], [-1e-7, 0.5, 0.5], [0.5, 2.0, 0.5]], np.float32)
+    return np.concatenate([X, edges, out])
+
+
+def _nondyadic():
+    return V.refined_ball((2, 2, 2), (3, 3, 3), centres=((0.3, 0.6, 0.45),), radii=(0.4, 0.2), ncomp=3, seed=4)
+
+
+VOLS = {
+    "cfg1": lambda: V.load_config(1),
+    "nondyadic_p2_vec": _nondyadic,
+    "tp_p1": lambda: V.tensor_product((1, 1, 1), (5, 3, 4), seed=2),
+}
+
+
+@pytest.fixture(scope="module")
+def vols():
+    return {k: f() for k, f in VOLS.items()}
+
+
+@pytest.fixture(scope="module")
+def oracles(vols):
+    return {k: Oracle(v) for k, v in vols.items()}
+
+
+# ----------------------------------------------------------------------------
+# look-up (Alg. 1)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(VOLS))
+@pytest.mark.parametrize("blocks", [(1, 1, 1), (2, 2, 2), (64, 64, 64), (8, 4, 16)])
+def test_lookup_bit_exact(vols, oracles, name, blocks):
+    vol = vols[name]
+    gv = lv.Volume(vol).build_accel(blocks)
+    n = 200_000 if blocks == (64, 64, 64) and name == "cfg1" else 40_000
+    X = _probe_points(vol, n, seed=zlib.crc32(f"{name}{blocks}".encode()) % 1000, blocks=blocks)
+    got = gv.lookup(torch.from_numpy(X).cuda()).cpu().numpy().view(np.uint32)
+    want = oracles[name].lookup(X)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, f"{bad.size} mismatches, e.g. {X[bad[:3]]} gpu {got[bad[:3]]} orc {want[bad[:3]]}"
+    assert np.sum(want == NONE) == 3
+    st = gv.stats()
+    assert st["depth_max"] >= st["depth_min"] >= 0
+    gv.close()
+
+
+def test_lookup_million_points_cfg1(vols, oracles):
+    vol = vols["cfg1"]
+    gv = lv.Volume(vol).build_accel((64, 64, 64))
+    X = _probe_points(vol, 1_000_000, seed=17)
+    got = gv.lookup(torch.from_numpy(X).cuda()).cpu().numpy().view(np.uint32)
+    np.testing.assert_array_equal(got, oracles["cfg1"].lookup(X))
+
+
+def test_lookup_empty_and_state(vols):
+    gv = lv.Volume(vols["tp_p1"])
+    with pytest.raises(lv.LrvolError) as ei:
+        gv.lookup(torch.zeros((4, 3), device="cuda"))
+    assert ei.value.status == lv.ERR_STATE
+    gv.build_accel((4, 4, 4))
+    out = gv.lookup(torch.zeros((0, 3), device="cuda"))
+    assert out.numel() == 0
+    with pytest.raises(lv.LrvolError) as ei:
+        gv.build_accel((3, 4, 4))
+    assert ei.value.status == lv.ERR_ARG
+
+
+# ----------------------------------------------------------------------------
+# change of basis and evaluation (Sec. 3.2.3)
+# ----------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name", list(VOLS))
+def test_bezier_blocks_match_interpolation(vols, oracles, name):
+    vol = vols[name]
+    gv = lv.Volume(vol).to_bezier()
+    B = gv.get_bezier()
+    rng = np.random.default_rng(1)
+    el = rng.choice(vol.n_elem, min(vol.n_elem, 400), replace=False)
+    ref = oracles[name].bezier_blocks(el)
+    scale = np.abs(vol.coef).max()
+    np.testing.assert_allclose(B[el], ref, atol=1e-12 * scale, rtol=0)
+    gv.close()
+
+
+@pytest.mark.parametrize("name", list(VOLS))
+def test_eval_values(vols, oracles, name):
+    vol = vols[name]
+    gv = lv.Volume(vol).build_accel((16, 16, 16)).to_bezier()
+    X = _probe_points(vol, 100_000, seed=5)
+    got = gv.eval(torch.from_numpy(X).cuda()).cpu().numpy().astype(np.float64)
+    want = oracles[name].eval(X)
+    tol = VAL_TOL * np.maximum(np.abs(want), np.abs(vol.coef).max())
+    err = np.abs(got - want)
+    assert np.all(err <= tol), f"max err {err.max()} at {np.argmax(err.max(axis=1))}"
+    gv.close()
+
+
+def test_eval_anisotropic_degree():
+    vol = V.refined_ball((1, 2, 3), (4, 3, 5), centres=((0.5, 0.5, 0.5),), radii=(0.35,), seed=8)
+    gv = lv.Volume(vol).build_accel((8, 8, 8)).to_bezier()
+    X = _probe_points(vol, 20_000, seed=6)
+    got = gv.eval(torch.from_numpy(X).cuda()).cpu().numpy()
+    want = Oracle(vol).eval(X)
+    assert np.abs(got - want).max() <= VAL_TOL * max(1.0, np.abs(vol.coef).max())
+
+
+# ----------------------------------------------------------------------------
+# rendering (Sec. 4)
+# ----------------------------------------------------------------------------
+
+def _render_pair(vol, orc, cam, tf, step, blocks=(64, 64, 64), pixels=None):
+    gv = lv.Volume(vol).build_accel(blocks).to_bezier()
+    img = gv.render(cam, tf, step).cpu().numpy()
+    st = gv.stats()
+    gv.close()
+    if pixels is None:
+        ref, ost = orc.render(cam, tf, step)
+        return img, ref, st, ost
+    ref, ost = orc.render(cam, tf, step, pixels=pixels)
+    return img[pixels[:, 1], pixels[:, 0]], ref, st, ost
+
+
+@pytest.mark.parametrize("mode", ["fixed", "heuristic"])
+@pytest.mark.parametrize("view", [0, 1])
+def test_render_cfg1(vols, oracles, mode, view):
+    tf, cams = V.config1_render()
+    tf = _f32_tf(tf)
+    step = V.StepParams(mode=mode, h=1 / 256, xi=1 / 256, alpha_stop=1.0)
+    img, ref, st, ost = _render_pair(vols["cfg1"], oracles["cfg1"], cams[view], tf, step)
+    assert _rmse(img, ref) <= RMSE_TOL
+    assert np.abs(img - ref).max() <= 2e-3
+    assert st["rays_hit"] == ost["rays_hit"]
+    # identical FP32 decisions: same samples, except where FP32 alpha saturates to 1 before FP64
+    assert abs(st["samples"] - ost["samples"]) <= 0.001 * ost["samples"]
+
+
+@pytest.mark.parametrize("mode", ["fixed", "heuristic"])
+def test_render_ragged_persp(vols, oracles, mode):
+    """A size that leaves partial tiles in both directions, perspective, early termination on."""
+    tf, _ = V.config1_render()
+    tf = _f32_tf(tf)
+    cam = V.orbit_camera(V.Stream(77), 100, 70)
+    step = V.StepParams(mode=mode, h=1 / 300, xi=1 / 256, alpha_stop=0.95)
+    img, ref, st, ost = _render_pair(vols["cfg1"], oracles["cfg1"], cam, tf, step, blocks=(32, 32, 32))
+    assert _rmse(img, ref) <= RMSE_TOL
+
+
+@pytest.mark.parametrize("field,comp", [("magnitude", 0), ("component", 0), ("component", 2)])
+def test_render_vector(vols, oracles, field, comp):
+    vol = vols["nondyadic_p2_vec"]
+    tf = _f32_tf(V.seeded_tf(V.Stream(31), alpha_max=0.05))
+    tf.vmin, tf.vmax = (0.0, 1.6) if field == "magnitude" else (0.0, 1.0)
+    cam = V.orbit_camera(V.Stream(32), 64, 48)
+    step = V.StepParams(mode="heuristic", xi=1 / 128, field=field, component=comp)
+    img, ref, st, ost = _render_pair(vol, oracles["nondyadic_p2_vec"], cam, tf, step, blocks=(16, 16, 16))
+    assert _rmse(img, ref) <= RMSE_TOL
+    assert st["samples"] == ost["samples"]
+
+
+@pytest.mark.parametrize("mode", ["fixed", "heuristic"])
+def test_render_closed_form_constant_field(vols, mode):
+    vol = _with_coef(vols["cfg1"], np.full(vols["cfg1"].n_basis, 0.37))
+    a_src, rgb = 0.02, np.array([0.9, 0.4, 0.1], np.float32)
+    tf = V.TransferFunction(table=np.tile(np.array([*rgb, a_src], np.float32), (256, 1)).astype(np.float64))
+    cam = V.orbit_camera(V.Stream(5), 48, 32)
+    step = V.StepParams(mode=mode, h=1 / 200, xi=1 / 128)
+    gv = lv.Volume(vol).build_accel((16, 16, 16)).to_bezier()
+    img = gv.render(cam, tf, step).cpu().numpy()
+    from oracle.oracle import ray
+    for j in range(cam.height):
+        for i in range(cam.width):
+            r = ray(cam, i, j)
+            if r is None:
+                assert np.all(img[j, i] == 0)
+                continue
+            alpha = 1 - (1 - float(np.float32(a_src))) ** ((r[3] - r[2]) / step.xi)
+            assert abs(img[j, i, 3] - alpha) <= 2e-5
+            np.testing.assert_allclose(img[j, i, :3], rgb.astype(np.float64) * alpha, atol=2e-5)
+
+
+def test_render_deterministic_and_rows(vols):
+    tf, cams = V.config1_render()
+    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
+    gv = lv.Volume(vols["cfg1"]).build_accel((32, 32, 32)).to_bezier()
+    a = gv.render(cams[1], tf, step)
+    b = gv.render(cams[1], tf, step)
+    assert torch.equal(a, b)
+    # row ranges (screen-space shards) reproduce the full image exactly
+    out = torch.full_like(a, -1.0)
+    for r0, r1 in [(0, 50), (50, 51), (51, 128)]:
+        gv.render(cams[1], tf, step, out=out, row_begin=r0, row_end=r1)
+    assert torch.equal(out, a)
+    gv.close()
+
+
+def test_render_errors(vols):
+    tf, cams = V.config1_render()
+    step = V.StepParams()
+    gv = lv.Volume(vols["cfg1"])
+    with pytest.raises(lv.LrvolError) as ei:
+        gv.render(cams[0], tf, step)
+    assert ei.value.status == lv.ERR_STATE
+    gv.build_accel((8, 8, 8)).to_bezier()
+    with pytest.raises(lv.LrvolError) as ei:
+        gv.render(cams[0], tf, V.StepParams(field="magnitude"))
+    assert ei.value.status == lv.ERR_ARG
+    with pytest.raises(lv.LrvolError) as ei:
+        gv.render(cams[0], tf, V.StepParams(h=0.0))
+    assert ei.value.status == lv.ERR_ARG
+    one = V.ortho_z(1, 1)
+    img = gv.render(one, tf, step).cpu().numpy()
+    ref, _ = Oracle(vols["cfg1"]).render(one, _f32_tf(tf), step)
+    assert _rmse(img, ref) <= RMSE_TOL
+    gv.close()
+    aniso = V.refined_ball((1, 2, 3), (4, 3, 5), radii=(0.3,))
+    ga = lv.Volume(aniso).build_accel((8, 8, 8)).to_bezier()
+    with pytest.raises(lv.LrvolError) as ei:
+        ga.render(cams[0], tf, step)
+    assert ei.value.status == lv.ERR_UNSUPPORTED
+
+
+def _sample_pixels(cam, n, seed):
+    rng = np.random.default_rng(seed)
+    return np.stack([rng.integers(0, cam.width, n), rng.integers(0, cam.height, n)], axis=1).astype(np.int32)
+
+
+@pytest.mark.slow
+def test_render_cfg2_full_size_sampled():
+    """The benchmark configuration (1920x1080, Eq. 4, alpha_stop 0.99, 64^3 forest)
+    on sampled pixels, each recomputed by the oracle."""
+    vol = V.load_config(2)
+    tf, cam = V.config2_render()
+    tf = _f32_tf(tf)
+    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
+    pix = _sample_pixels(cam, 48, 3)
+    img, ref, st, ost = _render_pair(vol, Oracle(vol), cam, tf, step, blocks=(64, 64, 64), pixels=pix)
+    assert _rmse(img, ref) <= RMSE_TOL
+    assert st["samples"] > 0 and st["rays_hit"] > 0
