@@ -51,7 +51,7 @@ def _dist():
 def _workload():
     from paper_1707_01170_gb300.synth import volumes as V
     vol = V.load_config(2)
-    tf, cam = V.config2_render(WIDTH, HEIGHT)
+    tf, cam = V.config2_render(WIDTH, HEIGHT, vol)
     tf.table = np.asarray(tf.table, dtype=np.float32).astype(np.float64)
     step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
     return vol, tf, cam, step
@@ -107,17 +107,42 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(vol, tf, cam, step, pixels: int = 384, seed: int = 11):
-    """The FP64 oracle, as it stands, on a seeded pixel subset of the same frame."""
+def cpu_baseline(vol, tf, cam, step, target_s: float = 12.0, seed: int = 11):
+    """The FP64 oracle, as it stands, on a seeded pixel subset of the same
+    frame, sized to about target_s seconds of work on all host cores."""
     from oracle.oracle import Oracle
     rng = np.random.default_rng(seed)
-    pix = np.stack([rng.integers(0, cam.width, pixels), rng.integers(0, cam.height, pixels)], axis=1).astype(np.int32)
     orc = Oracle(vol)
-    t0 = time.perf_counter()
-    _, st = orc.render(cam, tf, step, pixels=pix)
-    dt = time.perf_counter() - t0
-    return {"value": st["samples"] / dt / 1e9, "unit": "Gsamples/s", "cores": orc.threads, "kind": "oracle",
-            "sample": f"{pixels} seeded pixels of the same 1920x1080 frame ({st['samples']} samples, {dt:.1f} s)"}
+
+    def run(n):
+        pix = np.stack([rng.integers(0, cam.width, n), rng.integers(0, cam.height, n)], axis=1).astype(np.int32)
+        t0 = time.perf_counter()
+        _, st = orc.render(cam, tf, step, pixels=pix)
+        return st["samples"], time.perf_counter() - t0
+
+    s0, d0 = run(256)
+    n = int(min(40000, max(256, 256 * (target_s - d0) / max(d0, 1e-3))))
+    s1, d1 = run(n)
+    samples, dt = s0 + s1, d0 + d1
+    return {"value": samples / dt / 1e9, "unit": "Gsamples/s", "cores": orc.threads, "kind": "oracle",
+            "sample": f"{256 + n} seeded pixels of the same 1920x1080 frame ({samples} samples, {dt:.1f} s)"}
+
+
+def profiled_traffic():
+    """DRAM bytes per k_render launch from the committed ncu summary, if the
+    kernel source is unchanged since that capture; else None."""
+    import hashlib
+    try:
+        prof = open(os.path.join(ROOT, "profiles", "k_render_cfg2_1080p.md")).read()
+        src = open(os.path.join(ROOT, "paper_1707_01170_gb300", "csrc", "kernels.cu"), "rb").read()
+    except OSError:
+        return None
+    sha = hashlib.sha256(src).hexdigest()[:16]
+    fields = dict(ln.strip().split(": ", 1) for ln in prof.splitlines() if ln.strip().startswith(
+        ("kernels_cu_sha256_16:", "traffic_bytes_per_launch:")))
+    if fields.get("kernels_cu_sha256_16") != sha:
+        return None
+    return int(fields["traffic_bytes_per_launch"])
 
 
 def run_reference(args):
@@ -231,7 +256,7 @@ def run_ours(args):
     flop = FLOP_PER_SAMPLE_P3_SCALAR * samples_per_frame
     achieved = flop / (ms_per_step / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": None,
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(),
             "kernel": "k_render<3,0>", "flop_per_sample": FLOP_PER_SAMPLE_P3_SCALAR,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no FP32 figure measured)"}
     line = {"metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": ws, "steps": args.steps,
@@ -260,7 +285,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -118,14 +118,17 @@ class LRVolume:
         return [slice(o[a], o[a] + p[a] + 2) for a in range(3)]
 
     def save(self, path: str) -> None:
+        import json
         np.savez(path, deg=self.deg, elem_box=self.elem_box, knots=self.knots, coef=self.coef,
-                 weight=self.weight, grid=self.grid, name=np.array(self.name))
+                 weight=self.weight, grid=self.grid, name=np.array(self.name), meta=np.array(json.dumps(self.meta)))
 
     @staticmethod
     def load(path: str) -> "LRVolume":
+        import json
         z = np.load(path)
+        meta = json.loads(str(z["meta"])) if "meta" in z else {}
         return LRVolume(deg=z["deg"], elem_box=z["elem_box"], knots=z["knots"], coef=z["coef"],
-                        weight=z["weight"], grid=z["grid"], name=str(z["name"]))
+                        weight=z["weight"], grid=z["grid"], name=str(z["name"]), meta=meta)
 
 
 class Refiner:

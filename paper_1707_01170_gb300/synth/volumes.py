@@ -284,19 +284,24 @@ def config2() -> LRVolume:
     g = greville(R.knots(), R.deg)
     coef = fld.trilinear(g).astype(np.float32).astype(np.float64)
     vol = R.volume(coef=coef[:, None], name="cfg2")
-    vol.meta["shell_values"] = [float(a) for a in fld.amp]
+    # normalised field value on each shell (peak of its Gaussian profile)
+    vol.meta["shell_values"] = [float((a - fld.lo) / (fld.hi - fld.lo)) for a in fld.amp]
     return vol
 
 
-def config2_render(width: int = 1920, height: int = 1080):
+def config2_render(width: int = 1920, height: int = 1080, vol: LRVolume | None = None):
     """Perspective 1920x1080 camera at distance 1.8, fovy 40 deg, and the TF:
-    the config-1 recipe plus 3 opacity bands on the shell values."""
+    the config-1 recipe (peak opacity 0.02) plus 3 opacity bands, half width
+    0.04, centred on the normalised shell values (seeded peak opacity
+    U[0.05,0.3], seeded colour)."""
+    if vol is None:
+        vol = load_config(2)
     st = Stream(SEED_BASE + 2 + 1000)
     cam = orbit_camera(st, width, height)
-    centres = st.uniform(0.45, 0.9, 3)
+    centres = vol.meta["shell_values"]
     bands = []
     for k in range(3):
-        a = st.uniform(0.3, 0.6, 1)[0]
+        a = st.uniform(0.05, 0.3, 1)[0]
         rgb = st.take(3)
         bands.append((float(centres[k]), 0.04, a, *rgb))
     tf = seeded_tf(st, alpha_max=0.02, bands=bands)
@@ -389,7 +394,7 @@ def load_config(k: int, cache: bool = True) -> LRVolume:
     if not cache:
         return _BUILDERS[k]()
     os.makedirs(_CACHE, exist_ok=True)
-    path = os.path.join(_CACHE, f"cfg{k}_v1.npz")
+    path = os.path.join(_CACHE, f"cfg{k}_v2.npz")
     if os.path.exists(path):
         return LRVolume.load(path)
     vol = _BUILDERS[k]()
