@@ -50,6 +50,12 @@ __device__ void bernstein_of_bspline(const double *xi, int p, double a, double b
   }
 }
 
+__device__ __forceinline__ double binomial(int n, int k) {
+  double b = 1.0;
+  for (int i = 1; i <= k; ++i) b = b * (double)(n - k + i) / (double)i;
+  return b;
+}
+
 constexpr int kBezWarps = 4;
 constexpr int kChunk = 32;
 
@@ -99,13 +105,18 @@ __global__ void __launch_bounds__(32 * kBezWarps) k_to_bezier(
     }
     __syncwarp();
   }
+  // FP32 render copy with the binomials folded in: c_ijk C(p0,i) C(p1,j) C(p2,k),
+  // so that evaluation multiplies by plain monomials u^i (1-u)^(p-i).
   for (int r = 0; r < 4; ++r) {
     const int q = lane + 32 * r;
-    if (q < nb)
+    if (q < nb) {
+      const int ix = q % n0, iy = (q / n0) % n1, iz = q / (n0 * n1);
+      const double binom = binomial(p0, ix) * binomial(p1, iy) * binomial(p2, iz);
       for (int c = 0; c < nc; ++c) {
         out64[(e * nc + c) * nb + q] = acc[r][c];
-        out32[e * elem_stride + c * comp_stride + q] = (float)acc[r][c];
+        out32[e * elem_stride + c * comp_stride + q] = (float)(acc[r][c] * binom);
       }
+    }
   }
 }
 
@@ -169,25 +180,27 @@ __global__ void k_lookup(ForestView f, int64_t n_elem, const float *__restrict__
 }
 
 // ----------------------------------------------------------------------------
-// Bezier evaluation
+// Bezier evaluation.  Render blocks hold binomially scaled coefficients, so a
+// block is evaluated as sum c'_ijk m_i(u) m_j(v) m_k(w) with monomials
+// m_i(u) = u^i (1-u)^(p-i).
 // ----------------------------------------------------------------------------
 
 template <int P>
-__device__ __forceinline__ void bernstein(float u, float *b) {
+__device__ __forceinline__ void monomials(float u, float *m) {
   const float v = 1.f - u;
   if constexpr (P == 1) {
-    b[0] = v;
-    b[1] = u;
+    m[0] = v;
+    m[1] = u;
   } else if constexpr (P == 2) {
-    b[0] = v * v;
-    b[1] = 2.f * u * v;
-    b[2] = u * u;
+    m[0] = v * v;
+    m[1] = u * v;
+    m[2] = u * u;
   } else {
     const float u2 = u * u, v2 = v * v;
-    b[0] = v2 * v;
-    b[1] = 3.f * u * v2;
-    b[2] = 3.f * u2 * v;
-    b[3] = u2 * u;
+    m[0] = v2 * v;
+    m[1] = u * v2;
+    m[2] = u2 * v;
+    m[3] = u2 * u;
   }
 }
 
@@ -220,12 +233,11 @@ __device__ float eval_generic(const float *c, const int *deg, float ux, float uy
   for (int a = 0; a < 3; ++a) {
     const int p = deg[a];
     const float v = 1.f - u[a];
-    // Bernstein values by the triangular recurrence B^r_j = v B^{r-1}_j + u B^{r-1}_{j-1}
-    b[a][0] = 1.f;
-    for (int r = 1; r <= p; ++r) {
-      b[a][r] = u[a] * b[a][r - 1];
-      for (int j = r - 1; j >= 1; --j) b[a][j] = v * b[a][j] + u[a] * b[a][j - 1];
-      b[a][0] = v * b[a][0];
+    for (int i = 0; i <= p; ++i) {
+      float m = 1.f;
+      for (int q = 0; q < i; ++q) m *= u[a];
+      for (int q = i; q < p; ++q) m *= v;
+      b[a][i] = m;
     }
   }
   const int n0 = deg[0] + 1, n1 = deg[1] + 1, n2 = deg[2] + 1;
@@ -272,74 +284,143 @@ __global__ void k_eval(ForestView f, const ElemRec *__restrict__ elem, int64_t n
 // render (Sec. 4, Alg. 2, Eq. 4)
 // ----------------------------------------------------------------------------
 
-// FIELD: 0 = one component (scalar or chosen), 1 = magnitude of 3 components
+__device__ __forceinline__ float ex2_approx(float x) {
+  float y;
+  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+__device__ __forceinline__ float lg2_approx(float x) {
+  float y;
+  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+
+// 8x4-pixel warp tiles, numbered so that 4 consecutive tiles form a 16x8 patch
+// and consecutive patches run along rows (spatial locality between the warps
+// that fetch neighbouring tile numbers).
+__device__ __forceinline__ void tile_origin(int tile, int tiles_x, int *i0, int *j0) {
+  const int patch = tile >> 2, sub = tile & 3;
+  const int patches_x = (tiles_x + 1) >> 1;
+  const int px = patch % patches_x, py = patch / patches_x;
+  *i0 = (px * 2 + (sub & 1)) * 8;
+  *j0 = (py * 2 + (sub >> 1)) * 4;
+}
+
+struct Ray {
+  float o[3], d[3], tin, tout;
+};
+
+// FP32 ray of pixel (i, j) and its interval in the unit cube (order of
+// operations as stated in lrvol.h).  Returns false on a miss.
+__device__ __forceinline__ bool make_ray(const RayConsts &K, int i, int j, Ray &r) {
+  const float a = __fmaf_rn(__fadd_rn((float)i, 0.5f), K.sxs, K.sxo);
+  const float b = __fmaf_rn(__fadd_rn((float)j, 0.5f), K.sys, K.syo);
+  if (K.persp) {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      r.d[c] = __fmaf_rn(a, K.R[c], __fmaf_rn(b, K.U[c], K.F[c]));
+      r.o[c] = K.E[c];
+    }
+    const float n = __fsqrt_rn(__fmaf_rn(r.d[0], r.d[0], __fmaf_rn(r.d[1], r.d[1], __fmul_rn(r.d[2], r.d[2]))));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) r.d[c] = __fdiv_rn(r.d[c], n);
+  } else {
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      r.o[c] = __fmaf_rn(a, K.R[c], __fmaf_rn(b, K.U[c], K.E[c]));
+      r.d[c] = K.F[c];
+    }
+  }
+  float tin = 0.f, tout = __int_as_float(0x7f800000);
+  bool hit = true;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    if (r.d[c] == 0.f) {
+      if (r.o[c] < 0.f || r.o[c] > 1.f) hit = false;
+    } else {
+      const float inv = __fdiv_rn(1.f, r.d[c]);
+      const float ta = __fmul_rn(__fsub_rn(0.f, r.o[c]), inv);
+      const float tb = __fmul_rn(__fsub_rn(1.f, r.o[c]), inv);
+      tin = fmaxf(tin, fminf(ta, tb));
+      tout = fminf(tout, fmaxf(ta, tb));
+    }
+  }
+  r.tin = tin;
+  r.tout = tout;
+  return hit && tin < tout;
+}
+
+// FIELD: 0 = one component (scalar or chosen), 1 = magnitude of 3 components.
+// Persistent warps: each warp takes 8x4-pixel tiles from a counter until the
+// image is done; one lane traces one ray.  In the sample loop the Alg. 2 update
+// of sample k is issued together with the evaluation of sample k+1 (they are
+// independent), so the scheduler can overlap their latencies; a ray that
+// terminates after sample k discards the already evaluated sample k+1.
 template <int P, int FIELD>
-__global__ void __launch_bounds__(128) k_render(const __grid_constant__ RenderParams prm) {
+__global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ RenderParams prm) {
   constexpr int N = P + 1;
   constexpr int NB = N * N * N;
   constexpr int CS = (NB + 3) & ~3;
   constexpr int NCE = FIELD == 1 ? 3 : 1;
-  __shared__ float4 tf[256];
-  for (int q = threadIdx.x; q < 256; q += blockDim.x) tf[q] = prm.tf[q];
+  __shared__ float4 tfb[256], tfd[256];
+  for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+    const float4 e0 = prm.tf[q], e1 = prm.tf[q < 255 ? q + 1 : 255];
+    tfb[q] = e0;
+    tfd[q] = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
+  }
   __syncthreads();
 
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-  const int j = prm.row_begin + blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-  const bool active = i < prm.width && j < prm.row_end;
+  const int lane = threadIdx.x & 31;
+  const int tiles_x = (prm.width + 7) >> 3;
+  const int tiles_y = (prm.row_end - prm.row_begin + 3) >> 2;
+  const int n_tiles = ((tiles_x + 1) >> 1) * 2 * (((tiles_y + 1) >> 1) * 2);
   unsigned long long nsamp = 0, nlook = 0, nhit = 0;
-  float4 out = make_float4(0.f, 0.f, 0.f, 0.f);
 
-  if (active) {
-    const RayConsts &K = prm.ray;
-    const float a = __fmaf_rn(__fadd_rn((float)i, 0.5f), K.sxs, K.sxo);
-    const float b = __fmaf_rn(__fadd_rn((float)j, 0.5f), K.sys, K.syo);
-    float o[3], d[3];
-    if (K.persp) {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        d[c] = __fmaf_rn(a, K.R[c], __fmaf_rn(b, K.U[c], K.F[c]));
-        o[c] = K.E[c];
-      }
-      const float n = __fsqrt_rn(__fmaf_rn(d[0], d[0], __fmaf_rn(d[1], d[1], __fmul_rn(d[2], d[2]))));
-#pragma unroll
-      for (int c = 0; c < 3; ++c) d[c] = __fdiv_rn(d[c], n);
-    } else {
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        o[c] = __fmaf_rn(a, K.R[c], __fmaf_rn(b, K.U[c], K.E[c]));
-        d[c] = K.F[c];
-      }
-    }
-    float tin = 0.f, tout = __int_as_float(0x7f800000);
-    bool hit = true;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      if (d[c] == 0.f) {
-        if (o[c] < 0.f || o[c] > 1.f) hit = false;
-      } else {
-        const float inv = __fdiv_rn(1.f, d[c]);
-        const float ta = __fmul_rn(__fsub_rn(0.f, o[c]), inv);
-        const float tb = __fmul_rn(__fsub_rn(1.f, o[c]), inv);
-        tin = fmaxf(tin, fminf(ta, tb));
-        tout = fminf(tout, fmaxf(ta, tb));
-      }
-    }
-    hit = hit && tin < tout;
-    if (hit) {
-      nhit = 1;
-      float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+  for (;;) {
+    int tile = 0;
+    if (lane == 0) tile = (int)atomicAdd(prm.counters + kCntTiles, 1ull);
+    tile = __shfl_sync(0xffffffffu, tile, 0);
+    if (tile >= n_tiles) break;
+    int i0, j0;
+    tile_origin(tile, tiles_x, &i0, &j0);
+    const int i = i0 + (lane & 7);
+    const int j = prm.row_begin + j0 + (lane >> 3);
+    if (i >= prm.width || j >= prm.row_end) continue;
+
+    Ray ray;
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+    if (make_ray(prm.ray, i, j, ray)) {
+      ++nhit;
       uint32_t cur = kNone;
-      float4 ra = make_float4(0, 0, 0, 0), rb = ra, rc = ra, rd = ra;
+      float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
       float cf[NCE][CS];
-      float t = tin;
+      float t = ray.tin;
       int k = 0;
-      while (t < tout) {
-        const float px = fminf(fmaxf(__fmaf_rn(t, d[0], o[0]), 0.f), 1.f);
-        const float py = fminf(fmaxf(__fmaf_rn(t, d[1], o[1]), 0.f), 1.f);
-        const float pz = fminf(fmaxf(__fmaf_rn(t, d[2], o[2]), 0.f), 1.f);
-        const bool inside = cur != kNone && px >= ra.x && py >= ra.y && pz >= ra.z && px < rb.x && py < rb.y &&
-                            pz < rb.z;
+      bool pend = false;     // a sample evaluated but not yet composited
+      float pv = 0.f, pseg = 0.f;
+      for (;;) {
+        if (!(t < ray.tout)) {
+          if (pend) {
+            const float x = fminf(fmaxf((pv - prm.tf_off) * prm.tf_scale, 0.f), 255.f);
+            const int q = min((int)x, 254);
+            const float fr = x - (float)q;
+            const float4 e0 = tfb[q], de = tfd[q];
+            const float sa = fmaf(fr, de.w, e0.w);
+            const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (pseg * prm.inv_xi));
+            const float wgt = (1.f - T) * (1.f - A);
+            C0 = fmaf(wgt, fmaf(fr, de.x, e0.x), C0);
+            C1 = fmaf(wgt, fmaf(fr, de.y, e0.y), C1);
+            C2 = fmaf(wgt, fmaf(fr, de.z, e0.z), C2);
+            A += wgt;
+            ++nsamp;
+          }
+          break;
+        }
+        const float px = fminf(fmaxf(__fmaf_rn(t, ray.d[0], ray.o[0]), 0.f), 1.f);
+        const float py = fminf(fmaxf(__fmaf_rn(t, ray.d[1], ray.o[1]), 0.f), 1.f);
+        const float pz = fminf(fmaxf(__fmaf_rn(t, ray.d[2], ray.o[2]), 0.f), 1.f);
+        const bool inside = px >= ra.x && py >= ra.y && pz >= ra.z && px < rb.x && py < rb.y && pz < rb.z;
         if (!inside) {
           cur = forest_lookup(prm.forest, px, py, pz, prm.status);
           if (cur == kNone || (int64_t)cur >= prm.n_elem) {
@@ -365,13 +446,14 @@ __global__ void __launch_bounds__(128) k_render(const __grid_constant__ RenderPa
               cf[c][4 * q + 3] = v.w;
             }
         }
-        float tn = prm.mode == LRVOL_STEP_HEURISTIC ? __fadd_rn(t, ra.w) : __fmaf_rn((float)(k + 1), prm.h, tin);
+        float tn = prm.mode == LRVOL_STEP_HEURISTIC ? __fadd_rn(t, ra.w) : __fmaf_rn((float)(k + 1), prm.h, ray.tin);
         if (!(tn > t)) tn = nextafterf(t, __int_as_float(0x7f800000));
-        const float seg = __fsub_rn(fminf(tn, tout), t);
+        const float seg = __fsub_rn(fminf(tn, ray.tout), t);
+        // evaluate sample k ...
         float bx[N], by[N], bz[N];
-        bernstein<P>(local_u(px, ra.x, rc.x, rd.x), bx);
-        bernstein<P>(local_u(py, ra.y, rc.y, rd.y), by);
-        bernstein<P>(local_u(pz, ra.z, rc.z, rd.z), bz);
+        monomials<P>(local_u(px, ra.x, rc.x, rd.x), bx);
+        monomials<P>(local_u(py, ra.y, rc.y, rd.y), by);
+        monomials<P>(local_u(pz, ra.z, rc.z, rd.z), bz);
         float v;
         if constexpr (FIELD == 1) {
           const float v0 = contract<P>(cf[0], bx, by, bz);
@@ -381,34 +463,33 @@ __global__ void __launch_bounds__(128) k_render(const __grid_constant__ RenderPa
         } else {
           v = contract<P>(cf[0], bx, by, bz);
         }
-        // transfer function
-        const float x = fminf(fmaxf((v - prm.tf_off) * prm.tf_scale, 0.f), 255.f);
-        const int i0 = min((int)x, 254);
-        const float fr = x - (float)i0;
-        const float4 e0 = tf[i0], e1 = tf[i0 + 1];
-        const float sr = fmaf(fr, e1.x - e0.x, e0.x);
-        const float sg = fmaf(fr, e1.y - e0.y, e0.y);
-        const float sb = fmaf(fr, e1.z - e0.z, e0.z);
-        const float sa = fmaf(fr, e1.w - e0.w, e0.w);
-        // Alg. 2
-        const float T = exp2f(__log2f(fmaxf(1.f - sa, 0.f)) * (seg * prm.inv_xi));
-        const float wgt = (1.f - T) * (1.f - A);
-        C0 = fmaf(wgt, sr, C0);
-        C1 = fmaf(wgt, sg, C1);
-        C2 = fmaf(wgt, sb, C2);
-        A += wgt;
-        ++nsamp;
-        ++k;
+        // ... while compositing sample k-1 (transfer function + Alg. 2)
+        if (pend) {
+          const float x = fminf(fmaxf((pv - prm.tf_off) * prm.tf_scale, 0.f), 255.f);
+          const int q = min((int)x, 254);
+          const float fr = x - (float)q;
+          const float4 e0 = tfb[q], de = tfd[q];
+          const float sa = fmaf(fr, de.w, e0.w);
+          const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (pseg * prm.inv_xi));
+          const float wgt = (1.f - T) * (1.f - A);
+          C0 = fmaf(wgt, fmaf(fr, de.x, e0.x), C0);
+          C1 = fmaf(wgt, fmaf(fr, de.y, e0.y), C1);
+          C2 = fmaf(wgt, fmaf(fr, de.z, e0.z), C2);
+          A += wgt;
+          ++nsamp;
+          if (A >= prm.alpha_stop) break;
+        }
+        pend = true;
+        pv = v;
+        pseg = seg;
         t = tn;
-        if (A >= prm.alpha_stop) break;
-        if (k >= kMaxSamplesPerRay) {
+        if (++k >= kMaxSamplesPerRay) {
           set_status(prm.status, kStatusTimeout);
           break;
         }
       }
-      out = make_float4(C0, C1, C2, A);
     }
-    reinterpret_cast<float4 *>(prm.out)[(int64_t)j * prm.width + i] = out;
+    reinterpret_cast<float4 *>(prm.out)[(int64_t)j * prm.width + i] = make_float4(C0, C1, C2, A);
   }
   // per-warp counters
 #pragma unroll
@@ -455,20 +536,31 @@ cudaError_t launch_eval(const lrvol_s *v, const float *pts, int64_t n, float *ou
   return cudaGetLastError();
 }
 
+template <int P, int FIELD>
+cudaError_t launch_render_t(const RenderParams &prm, cudaStream_t s) {
+  static int grid = 0;  // per-instantiation: SMs x resident CTAs (the device does not change in a process)
+  if (grid == 0) {
+    int dev = 0, sms = 0, per_sm = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render<P, FIELD>, 128, 0);
+    grid = sms * (per_sm > 0 ? per_sm : 1);
+  }
+  k_render<P, FIELD><<<grid, 128, 0, s>>>(prm);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_render(const RenderParams &prm, int degree, int field, cudaStream_t s) {
-  dim3 block(128);
-  dim3 grid((unsigned)((prm.width + 15) / 16), (unsigned)((prm.row_end - prm.row_begin + 7) / 8));
   const bool mag = field == LRVOL_FIELD_MAGNITUDE;
   switch (degree * 2 + (mag ? 1 : 0)) {
-    case 2: k_render<1, 0><<<grid, block, 0, s>>>(prm); break;
-    case 3: k_render<1, 1><<<grid, block, 0, s>>>(prm); break;
-    case 4: k_render<2, 0><<<grid, block, 0, s>>>(prm); break;
-    case 5: k_render<2, 1><<<grid, block, 0, s>>>(prm); break;
-    case 6: k_render<3, 0><<<grid, block, 0, s>>>(prm); break;
-    case 7: k_render<3, 1><<<grid, block, 0, s>>>(prm); break;
+    case 2: return launch_render_t<1, 0>(prm, s);
+    case 3: return launch_render_t<1, 1>(prm, s);
+    case 4: return launch_render_t<2, 0>(prm, s);
+    case 5: return launch_render_t<2, 1>(prm, s);
+    case 6: return launch_render_t<3, 0>(prm, s);
+    case 7: return launch_render_t<3, 1>(prm, s);
     default: return cudaErrorInvalidValue;
   }
-  return cudaGetLastError();
 }
 
 }  // namespace lrvol
