@@ -32,11 +32,6 @@ BLOCKS = (64, 64, 64)
 METRIC = "Gsamples/s (1080p frame, MR-like tricubic LR-spline, Eq. 4 steps)"
 L2_FLUSH_BYTES = 512 << 20
 
-# Algorithmic FP32 flops per composited sample of the tricubic scalar path
-# (an FMA counts 2): sample position 3 FMA + 6 clamps = 12; local coordinates
-# 3 x 3 = 9; Bernstein basis 3 x 9 = 27; tensor contraction 64+16+4 FMA = 168;
-# transfer function 13; Alg. 2 compositing 15 (log2/exp2 counted as 1 each).
-FLOP_PER_SAMPLE_P3_SCALAR = 12 + 9 + 27 + 168 + 13 + 15
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s
 
@@ -48,12 +43,43 @@ def _dist():
     return ws, rank, local
 
 
-def _workload():
+WORKLOADS = {
+    "cfg2": "cfg2: MR-like scalar tricubic LR-spline, 174000 elements, 1920x1080 persp fovy 40 at distance 1.8, "
+            "Eq. 4 heuristic steps, xi 1/256, alpha_stop 0.99",
+    "cfg3mag": "cfg3: wind-flow 3-vector triquadratic LR-spline, 388016 elements, |v|, 1920x1080 persp, "
+               "Eq. 4 heuristic steps, xi 1/256, alpha_stop 0.99",
+    "cfg3x": "cfg3: wind-flow 3-vector triquadratic LR-spline, 388016 elements, v_x, 1920x1080 persp, "
+             "Eq. 4 heuristic steps, xi 1/256, alpha_stop 0.99",
+}
+
+
+def flop_per_sample(p: int, field: str) -> int:
+    """Algorithmic FP32 flops per composited sample (an FMA counts 2): sample
+    position 12, local coordinates 9, monomial basis 3*(2p+1) (p=3: 21),
+    contraction 2*((p+1)^3 + (p+1)^2 + (p+1)) per component, |v| 6, transfer
+    function 13, Alg. 2 compositing 15."""
+    n = p + 1
+    contraction = 2 * (n ** 3 + n ** 2 + n)
+    comps = 3 if field == "magnitude" else 1
+    return 12 + 9 + 3 * (2 * p + 1) + comps * contraction + (6 if field == "magnitude" else 0) + 13 + 15
+
+
+def _workload(name: str = "cfg2"):
     from paper_1707_01170_gb300.synth import volumes as V
-    vol = V.load_config(2)
-    tf, cam = V.config2_render(WIDTH, HEIGHT, vol)
+    if name == "cfg2":
+        vol = V.load_config(2)
+        tf, cam = V.config2_render(WIDTH, HEIGHT, vol)
+        step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
+    else:
+        vol = V.load_config(3)
+        tf, cam = V.config3_render(WIDTH, HEIGHT)
+        if name == "cfg3mag":
+            tf.vmin, tf.vmax = 0.0, 1.5
+            step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, field="magnitude")
+        else:
+            tf.vmin, tf.vmax = -0.5, 1.5
+            step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, field="component", component=0)
     tf.table = np.asarray(tf.table, dtype=np.float32).astype(np.float64)
-    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
     return vol, tf, cam, step
 
 
@@ -149,7 +175,7 @@ def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
         return 0
-    vol, tf, cam, step = _workload()
+    vol, tf, cam, step = _workload(args.workload)
     from oracle.oracle import Oracle
     orc = Oracle(vol)
     rng = np.random.default_rng(5)
@@ -167,8 +193,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "cfg2 MR-like tricubic LR-spline, 1920x1080 persp, Eq. 4 steps; "
-                                   "each step = 96 seeded pixels of the frame"},
+            "config": {"workload": WORKLOADS[args.workload] + "; each step = 96 seeded pixels of the frame"},
             "cpu_baseline": {"value": val, "unit": "Gsamples/s", "cores": orc.threads, "kind": "oracle",
                              "sample": "96 seeded pixels per step"},
             "e2e": {"value": val, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -186,7 +211,7 @@ def run_ours(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     from paper_1707_01170_gb300 import lrvol as lv
 
-    vol, tf, cam, step = _workload()
+    vol, tf, cam, step = _workload(args.workload)
     stream = torch.cuda.current_stream()
     # ---- setup (once per volume) ----
     t0 = time.perf_counter()
@@ -253,18 +278,17 @@ def run_ours(args):
         if dist:
             dist.destroy_process_group()
         return 0
-    flop = FLOP_PER_SAMPLE_P3_SCALAR * samples_per_frame
+    fps = flop_per_sample(int(vol.deg[0]), step.field)
+    flop = fps * samples_per_frame
     achieved = flop / (ms_per_step / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic(),
-            "kernel": "k_render<3,0>", "flop_per_sample": FLOP_PER_SAMPLE_P3_SCALAR,
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic() if args.workload == "cfg2" else None,
+            "kernel": f"k_render<{int(vol.deg[0])},{1 if step.field == 'magnitude' else 0}>", "flop_per_sample": fps,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no FP32 figure measured)"}
     line = {"metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": "cfg2: MR-like scalar tricubic LR-spline, 174000 elements, 1920x1080 persp "
-                                   "fovy 40 at distance 1.8, Eq. 4 heuristic steps, xi 1/256, alpha_stop 0.99, "
-                                   f"forest {BLOCKS[0]}^3",
+            "config": {"workload": WORKLOADS[args.workload] + f", forest {BLOCKS[0]}^3",
                        "l2": "flushed between frames (512 MB write, outside the timed events)",
                        "samples_per_frame": samples_per_frame, "rays_hit": st["rays_hit"],
                        "lookups_per_frame": st["lookups"], "parallelism": f"replicas x{ws}"},
@@ -289,6 +313,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up frames
     if args.impl == "reference":
