@@ -149,6 +149,32 @@ int lrvol_to_bezier(lrvol_t vol, int32_t storage, void *stream);
 int lrvol_render(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
                  float *rgba_dev, void *stream);
 
+/* lrvol_render for callers that may not allocate device memory.  Some
+ * callers cannot call cudaMalloc: a host application that owns every byte of
+ * device memory through its own pool and forbids libraries to allocate, or a
+ * long-running service whose device footprint must not change once it has
+ * started.  This call allocates nothing (no cudaMalloc, no cudaFree, no
+ * allocating library routine) and does not touch the handle's scratch: the
+ * kernel's scratch (tile counter, sample/look-up/ray counters, status word)
+ * is a file-scope static device array of 256 bytes, which every GPU that
+ * loads the library holds until the process exits.  The paper has no
+ * counterpart; it is an integration variant of lrvol_render.
+ *
+ * The caller passes the inputs (a handle whose build_accel and to_bezier are
+ * done, camera, TF, step) and the outputs: rgba_dev as for lrvol_render, and
+ * optionally counters_dev (4 uint64 on the device, or NULL) receiving samples,
+ * look-ups, rays hit and the device status word (0 ok, 1 bounds, 2 timeout).
+ * The first call on each device looks up the array's device address with
+ * that device current (make that first call before any stream capture).
+ * Each call clears the counters on `stream` first; all calls share the one
+ * array and it keeps the last call's contents, so calls that overlap on the
+ * GPU (other streams, other threads) race on it.
+ * Sizes: one call needs 40 of the 256 bytes, whatever the image size; the
+ * maximum image is 32768 x 32768 (as for lrvol_render), larger ones are
+ * rejected with LRVOL_ERR_ARG.  Other errors: as lrvol_render. */
+int lrvol_render_noalloc(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                         float *rgba_dev, uint64_t *counters_dev, void *stream);
+
 /* Element look-up through the forest (Alg. 1) for n FP32 points (n x 3,
  * device) into elem_dev (n uint32, device).  Needs build_accel. */
 int lrvol_lookup(lrvol_t vol, const float *pts_dev, int64_t n, uint32_t *elem_dev, void *stream);

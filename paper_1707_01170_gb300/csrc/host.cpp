@@ -513,6 +513,58 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   return LRVOL_OK;
 }
 
+// The allocation-free render: same checks and kernel as lrvol_render, but the
+// kernel's scratch (tile counter, statistics, status word) is the library's
+// static device array instead of memory of the handle, and nothing is allocated.
+int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                         float *rgba_dev, uint64_t *counters_dev, void *stream) {
+  if (!v || !cam || !tf || !step || !rgba_dev) return fail(LRVOL_ERR_ARG, "null pointer");
+  if (!v->have_bezier || !v->have_accel) return fail(LRVOL_ERR_STATE, "render needs to_bezier and build_accel");
+  if (cam->width < 1 || cam->height < 1 || cam->width > kMaxImageSide || cam->height > kMaxImageSide)
+    return fail(LRVOL_ERR_ARG, "image size outside 1..32768 x 1..32768, the maximum of lrvol_render_noalloc");
+  if (cam->projection != LRVOL_ORTHO && cam->projection != LRVOL_PERSP) return fail(LRVOL_ERR_ARG, "bad projection");
+  int r0 = cam->row_begin, r1 = cam->row_end;
+  if (r0 == 0 && r1 == 0) r1 = cam->height;
+  if (r0 < 0 || r1 > cam->height || r0 > r1) return fail(LRVOL_ERR_ARG, "bad row range");
+  if (step->mode != LRVOL_STEP_FIXED && step->mode != LRVOL_STEP_HEURISTIC) return fail(LRVOL_ERR_ARG, "bad step mode");
+  if (step->mode == LRVOL_STEP_FIXED && !(step->h > 0)) return fail(LRVOL_ERR_ARG, "fixed step must be > 0");
+  if (!(step->xi > 0) || !(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "xi and vmax - vmin must be > 0");
+  const int field = step->field;
+  if (field < 0 || field > 2) return fail(LRVOL_ERR_ARG, "bad field");
+  if (field == LRVOL_FIELD_SCALAR && v->nc != 1) return fail(LRVOL_ERR_ARG, "scalar field needs ncomp = 1");
+  if (field == LRVOL_FIELD_MAGNITUDE && v->nc != 3) return fail(LRVOL_ERR_ARG, "magnitude needs ncomp = 3");
+  if (field == LRVOL_FIELD_COMPONENT && (step->component < 0 || step->component >= v->nc))
+    return fail(LRVOL_ERR_ARG, "bad component");
+  if (v->p[0] != v->p[1] || v->p[0] != v->p[2] || v->p[0] > 3)
+    return fail(LRVOL_ERR_UNSUPPORTED, "render needs equal degrees 1..3");
+  RenderParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.elem = v->d_elem;
+  prm.n_elem = v->n_elem;
+  prm.bez = v->d_bez32;
+  prm.elem_stride = v->elem_stride;
+  prm.comp_stride = v->comp_stride;
+  prm.comp = field == LRVOL_FIELD_COMPONENT ? step->component : 0;
+  prm.forest = forest_view(v);
+  prm.out = rgba_dev;
+  prm.width = cam->width;
+  prm.height = cam->height;
+  prm.row_begin = r0;
+  prm.row_end = r1;
+  camera_consts(cam, &prm.ray);
+  prm.mode = step->mode;
+  prm.h = (float)step->h;
+  prm.inv_xi = (float)(1.0 / step->xi);
+  prm.alpha_stop = (float)step->alpha_stop;
+  prm.tf_off = (float)tf->vmin;
+  prm.tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
+  for (int q = 0; q < 256; ++q) prm.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
+  cudaError_t e = launch_render_static(prm, v->p[0], field, (cudaStream_t)stream,
+                                       reinterpret_cast<unsigned long long *>(counters_dev));
+  if (e != cudaSuccess) return cuda_fail(e, "render_noalloc");
+  return LRVOL_OK;
+}
+
 int lrvol_lookup(lrvol_t v, const float *pts, int64_t n, uint32_t *elem, void *stream) {
   if (!v || (n > 0 && (!pts || !elem)) || n < 0) return fail(LRVOL_ERR_ARG, "bad arguments");
   if (!v->have_accel) return fail(LRVOL_ERR_STATE, "lookup needs build_accel");

@@ -11,6 +11,7 @@
 #include <cuda_runtime.h>
 
 #include <cstdint>
+#include <mutex>
 
 #include "lrvol_internal.h"
 
@@ -561,6 +562,70 @@ cudaError_t launch_render(const RenderParams &prm, int degree, int field, cudaSt
     case 7: return launch_render_t<3, 1>(prm, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ----------------------------------------------------------------------------
+// Scratch for lrvol_render_noalloc.  The render kernel needs a little global
+// memory beyond its inputs and outputs: the tile counter that hands out work,
+// three statistics counters and a status word.  lrvol_render takes them from
+// the handle; lrvol_render_noalloc takes them from this file-scope array, so
+// that the call itself allocates nothing.  Every GPU that loads the library
+// holds these bytes until the process exits.  Host code must not pass the
+// symbol itself to a kernel (on the host it names a stand-in, not device
+// memory): its device address is looked up once per device below.
+// ----------------------------------------------------------------------------
+}  // namespace lrvol
+
+static __device__ __align__(256) unsigned long long g_render_scratch[lrvol::kStaticScratchWords];
+
+namespace lrvol {
+
+namespace {
+constexpr int kMaxDevices = 256;
+std::mutex g_scratch_mutex;
+unsigned long long *g_scratch_ptr[kMaxDevices] = {};
+}  // namespace
+
+// Device address of g_render_scratch on the current device; resolved on the
+// first call for that device, with that device current.
+cudaError_t static_scratch(unsigned long long **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_scratch_mutex);
+  if (!g_scratch_ptr[dev]) {
+    void *ptr = nullptr;
+    e = cudaGetSymbolAddress(&ptr, g_render_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = static_cast<unsigned long long *>(ptr);
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+// Same kernel as launch_render, with the counters and the status word in the
+// static scratch (cleared on the stream before the launch).
+cudaError_t launch_render_static(RenderParams prm, int degree, int field, cudaStream_t s,
+                                 unsigned long long *counters_out) {
+  unsigned long long *scratch = nullptr;
+  cudaError_t e = static_scratch(&scratch);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * kStaticScratchWords, s);
+  if (e != cudaSuccess) return e;
+  prm.counters = scratch;
+  prm.status = reinterpret_cast<uint32_t *>(scratch + kNumCounters);
+  e = launch_render(prm, degree, field, s);
+  if (e != cudaSuccess) return e;
+  if (counters_out) {
+    // samples, lookups, rays hit, then the status word widened to 64 bits
+    e = cudaMemcpyAsync(counters_out, scratch + kCntSamples, sizeof(unsigned long long) * 3,
+                        cudaMemcpyDeviceToDevice, s);
+    if (e != cudaSuccess) return e;
+    e = cudaMemcpyAsync(counters_out + 3, scratch + kNumCounters, sizeof(unsigned long long),
+                        cudaMemcpyDeviceToDevice, s);
+  }
+  return e;
 }
 
 }  // namespace lrvol

@@ -23,6 +23,13 @@ enum : uint32_t { kStatusOk = 0, kStatusBounds = 1, kStatusTimeout = 2 };
 // Counters written by render (one slot each).
 enum { kCntSamples = 0, kCntLookups = 1, kCntRays = 2, kCntTiles = 3, kNumCounters = 8 };
 
+// Static scratch of lrvol_render_noalloc: kNumCounters counters, then the
+// status word (in a 64-bit slot); 32 words = 256 bytes per device.  One call
+// needs kNumCounters + 1 words, whatever the image size.
+constexpr int kStaticScratchWords = 32;
+static_assert(kNumCounters + 1 <= kStaticScratchWords, "static scratch too small for one render");
+constexpr int kMaxImageSide = 32768;  // largest width or height a render accepts
+
 // Element record, 4 x float4 = 64 bytes:
 //   a = {lo_ru.x, lo_ru.y, lo_ru.z, ds}   lower corner rounded up to FP32 (membership), Eq. 4 step
 //   b = {hi_ru.x, hi_ru.y, hi_ru.z, 0}    upper corner rounded up (+inf where hi = 1)
@@ -120,6 +127,8 @@ cudaError_t launch_elem_records(const lrvol_s *v, cudaStream_t s);
 cudaError_t launch_lookup(const lrvol_s *v, const float *pts, int64_t n, uint32_t *out, cudaStream_t s);
 cudaError_t launch_eval(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s);
 cudaError_t launch_render(const RenderParams &prm, int degree, int field, cudaStream_t s);
+cudaError_t launch_render_static(RenderParams prm, int degree, int field, cudaStream_t s,
+                                 unsigned long long *counters_out);
 
 // host.cpp
 void camera_consts(const lrvol_camera *c, RayConsts *k);

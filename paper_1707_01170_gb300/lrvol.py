@@ -23,7 +23,7 @@ NONE = 0xFFFFFFFF
 
 EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
             "lrvol_eval", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
-            "lrvol_destroy"]
+            "lrvol_destroy", "lrvol_render_noalloc"]
 
 
 class LrvolError(RuntimeError):
@@ -80,6 +80,9 @@ def load(path: str = LIB_PATH):
         L.lrvol_to_bezier.argtypes = [vp, i32, vp]
         L.lrvol_render.restype = ctypes.c_int
         L.lrvol_render.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step), vp, vp]
+        L.lrvol_render_noalloc.restype = ctypes.c_int
+        L.lrvol_render_noalloc.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
+                                           vp, vp, vp]
         L.lrvol_lookup.restype = ctypes.c_int
         L.lrvol_lookup.argtypes = [vp, vp, i64, vp, vp]
         L.lrvol_eval.restype = ctypes.c_int
