@@ -97,7 +97,7 @@ typedef struct {
   int32_t field;     /* LRVOL_FIELD_SCALAR | _MAGNITUDE (|v| of a 3-vector) | _COMPONENT */
   int32_t component; /* for LRVOL_FIELD_COMPONENT */
   double h;          /* fixed step (FIXED only) */
-  double xi;         /* standard length of Alg. 2 */
+  double xi;         /* reference length xi of Alg. 2 (T = (1 - alpha)^(segment / xi)) */
   double alpha_stop; /* early ray termination threshold; 1.0 = only when fully opaque */
 } lrvol_step;
 

@@ -11,9 +11,9 @@
  * What it computes, each function following its passage of the paper:
  *   orc_bspline      univariate B-spline by the Cox-de Boor recursion on a
  *                    local knot vector (Sec. 3.1, Eq. 1 factors)
- *   orc_find_element the element holding a point, by linear search over all
- *                    element boxes (Sec. 3.2: "a linear search through all
- *                    elements")
+ *   orc_find_element the element holding a point, by scanning every element
+ *                    box in turn (the O(N) search Sec. 3.2 sets against the
+ *                    acceleration structures)
  *   orc_eval         f(x) = sum_i c_i gamma_i N_i(x)  (Eq. 2), the sum running
  *                    over the B-splines whose support contains the element of
  *                    x, found by scanning all B-splines

@@ -11,9 +11,9 @@ field, component, h, xi, alpha_stop`` (the dataclasses of the seeded input
 generator fit).
 
 Bezier blocks (Sec. 3.2.3): on each element the LR-spline is one polynomial
-of tri-degree p; the paper obtains its Bernstein coefficients "by computing
-the coefficients of an interpolating polynomial".  ``bezier_blocks`` does
-exactly that: it evaluates Eq. 2 at the (p+1)^3 tensor points
+of tri-degree p, and the paper gets its Bernstein coefficients by
+interpolation.  ``bezier_blocks`` does exactly that: it evaluates Eq. 2 at the
+(p+1)^3 tensor points
 u_m = (m + 1/2)/(p+1) inside the element and solves the tensor Bernstein
 interpolation problem one axis at a time (numpy's dense solver is the
 library step).

@@ -114,8 +114,8 @@ int build_incidence(lrvol_s *v, std::vector<int64_t> &ptr, std::vector<int32_t> 
 }
 
 // ----------------------------------------------------------------------------
-// k-d forest (Sec. 3.2.1).  Split rule (the paper counts active elements on
-// both sides of the mean split value per direction): candidates are the
+// k-d forest (Sec. 3.2.1).  Split rule (the paper balances depth by counting,
+// per direction, the elements on either side of a mean split plane): candidates are the
 // element faces strictly inside the node region; per axis the candidate
 // nearest to the mean of the candidates; score = max(#left, #right) with
 // straddling elements counted on both sides; lowest score wins, ties x<y<z.

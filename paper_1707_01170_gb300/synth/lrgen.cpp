@@ -7,9 +7,10 @@
 // B-splines, each a product of three univariate B-splines on local knot
 // vectors, with scale factors gamma that keep a partition of unity (Eq. 2).
 //
-// LR B-splines arise by refining a tensor-product mesh and "recursively
-// splitting every LR B-spline on the mesh until all LR B-splines are minimal
-// support" (Sec. 3.1).  The refinement strategy used here is the structured
+// LR B-splines come from local refinements of a tensor-product mesh: each
+// B-spline that a new mesh plane cuts clean through is split, and this is
+// repeated until no mesh plane cuts through any support (Sec. 3.1).  The
+// refinement strategy used here is the structured
 // mesh one: every B-spline whose support meets a marked element gets its
 // support halved in every knot interval, in all three directions, by mesh
 // rectangles spanning the support; then every B-spline whose support is

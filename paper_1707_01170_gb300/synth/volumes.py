@@ -54,7 +54,7 @@ class TransferFunction:
 class StepParams:
     mode: str = "fixed"      # "fixed" | "heuristic"
     h: float = 1.0 / 256     # fixed step
-    xi: float = 1.0 / 256    # standard length of Alg. 2
+    xi: float = 1.0 / 256    # reference length xi of Alg. 2
     alpha_stop: float = 1.0  # early termination threshold (1 = off)
     field: str = "scalar"    # "scalar" | "magnitude" | "component"
     component: int = 0
