@@ -298,3 +298,19 @@ def test_render_cfg2_full_size_sampled():
     img, ref, st, ost = _render_pair(vol, Oracle(vol), cam, tf, step, blocks=(64, 64, 64), pixels=pix)
     assert _rmse(img, ref) <= RMSE_TOL
     assert st["samples"] > 0 and st["rays_hit"] > 0
+
+
+def test_render_shards_reassemble(vols):
+    """Screen-space shards (row ranges of 3 ranks, rendered here in turn) give
+    the full frame bitwise."""
+    from paper_1707_01170_gb300.shard import render_shard
+    tf, cams = V.config1_render()
+    cam = V.orbit_camera(V.Stream(9), 70, 53)
+    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
+    gv = lv.Volume(vols["cfg1"]).build_accel((16, 16, 16)).to_bezier()
+    full = gv.render(cam, tf, step)
+    out = torch.full_like(full, -1.0)
+    for r in range(3):
+        render_shard(gv, cam, tf, step, out, world=3, rank=r)
+    assert torch.equal(out, full)
+    gv.close()
