@@ -155,7 +155,7 @@ int lrvol_render(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const
  * long-running service whose device footprint must not change once it has
  * started.  This call allocates nothing (no cudaMalloc, no cudaFree, no
  * allocating library routine) and does not touch the handle's scratch: the
- * kernel's scratch (tile counter, sample/look-up/ray counters, status word)
+ * kernel's scratch (sample/look-up/ray counters and the status word)
  * is a file-scope static device array of 256 bytes, which every GPU that
  * loads the library holds until the process exits.  The paper has no
  * counterpart; it is an integration variant of lrvol_render.

@@ -440,12 +440,13 @@ int lrvol_to_bezier(lrvol_t v, int32_t storage, void *stream) {
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int nb = (v->p[0] + 1) * (v->p[1] + 1) * (v->p[2] + 1);
-  v->comp_stride = (nb + 3) & ~3;
-  v->elem_stride = v->comp_stride * v->nc;
+  v->elem_stride = render_stride(v->nc, v->p[0] + 1, v->p[1] + 1, v->p[2] + 1);
+  v->elemc_stride = v->nc == 3 ? 3 * roundup8(nb) : 0;
   if ((rc = dev_alloc(v, &v->d_inc_ptr, ptr.size(), "alloc incidence ptr")) ||
       (rc = dev_alloc(v, &v->d_inc_idx, idx.size(), "alloc incidence")) ||
       (rc = dev_alloc(v, &v->d_bez64, (size_t)v->n_elem * v->nc * nb, "alloc bezier64")) ||
       (rc = dev_alloc(v, &v->d_bez32, (size_t)v->n_elem * v->elem_stride, "alloc bezier32")) ||
+      (v->nc == 3 && (rc = dev_alloc(v, &v->d_bezc, (size_t)v->n_elem * v->elemc_stride, "alloc bezier plain"))) ||
       (rc = dev_alloc(v, &v->d_elem, (size_t)v->n_elem, "alloc element records")))
     return rc;
   CU(cudaMemcpyAsync(v->d_inc_ptr, ptr.data(), sizeof(int64_t) * ptr.size(), cudaMemcpyHostToDevice, st),
@@ -453,6 +454,8 @@ int lrvol_to_bezier(lrvol_t v, int32_t storage, void *stream) {
   CU(cudaMemcpyAsync(v->d_inc_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice, st),
      "upload incidence");
   CU(cudaMemsetAsync(v->d_bez32, 0, sizeof(float) * (size_t)v->n_elem * v->elem_stride, st), "clear bezier32");
+  if (v->d_bezc)
+    CU(cudaMemsetAsync(v->d_bezc, 0, sizeof(float) * (size_t)v->n_elem * v->elemc_stride, st), "clear bezier plain");
   CU(launch_to_bezier(v, st), "to_bezier kernel");
   CU(launch_elem_records(v, st), "element record kernel");
   CU(cudaStreamSynchronize(st), "to_bezier sync");  // host incidence goes out of scope
@@ -490,7 +493,8 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   prm.n_elem = v->n_elem;
   prm.bez = v->d_bez32;
   prm.elem_stride = v->elem_stride;
-  prm.comp_stride = v->comp_stride;
+  prm.bezc = v->d_bezc;
+  prm.elemc_stride = v->elemc_stride;
   prm.comp = field == LRVOL_FIELD_COMPONENT ? step->component : 0;
   prm.forest = forest_view(v);
   prm.out = rgba_dev;
@@ -503,8 +507,8 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   prm.h = (float)step->h;
   prm.inv_xi = (float)(1.0 / step->xi);
   prm.alpha_stop = (float)step->alpha_stop;
-  prm.tf_off = (float)tf->vmin;
   prm.tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
+  prm.tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
   prm.counters = v->d_counters;
   prm.status = v->d_status;
   for (int q = 0; q < 256; ++q) prm.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
@@ -514,7 +518,7 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
 }
 
 // The allocation-free render: same checks and kernel as lrvol_render, but the
-// kernel's scratch (tile counter, statistics, status word) is the library's
+// kernel's scratch (statistics counters, status word) is the library's
 // static device array instead of memory of the handle, and nothing is allocated.
 int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
                          float *rgba_dev, uint64_t *counters_dev, void *stream) {
@@ -543,7 +547,8 @@ int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf,
   prm.n_elem = v->n_elem;
   prm.bez = v->d_bez32;
   prm.elem_stride = v->elem_stride;
-  prm.comp_stride = v->comp_stride;
+  prm.bezc = v->d_bezc;
+  prm.elemc_stride = v->elemc_stride;
   prm.comp = field == LRVOL_FIELD_COMPONENT ? step->component : 0;
   prm.forest = forest_view(v);
   prm.out = rgba_dev;
@@ -556,8 +561,8 @@ int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf,
   prm.h = (float)step->h;
   prm.inv_xi = (float)(1.0 / step->xi);
   prm.alpha_stop = (float)step->alpha_stop;
-  prm.tf_off = (float)tf->vmin;
   prm.tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
+  prm.tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
   for (int q = 0; q < 256; ++q) prm.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
   cudaError_t e = launch_render_static(prm, v->p[0], field, (cudaStream_t)stream,
                                        reinterpret_cast<unsigned long long *>(counters_dev));
@@ -621,7 +626,7 @@ void lrvol_destroy(lrvol_t v) {
   if (!v) return;
   cudaDeviceSynchronize();
   void *ptrs[] = {v->d_box,   v->d_knots, v->d_coef,  v->d_weight, v->d_inc_ptr,  v->d_inc_idx, v->d_bez64,
-                  v->d_bez32, v->d_elem,  v->d_head,  v->d_nodes,  v->d_counters, v->d_status};
+                  v->d_bez32, v->d_bezc,  v->d_elem,  v->d_head,  v->d_nodes, v->d_counters, v->d_status};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete v;

@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(32 * kBezWarps) k_to_bezier(
     const double *__restrict__ box, const double *__restrict__ knots, const double *__restrict__ coef,
     const double *__restrict__ weight, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_idx,
     int p0, int p1, int p2, int nc, int kw, int64_t n_elem, double *__restrict__ out64, float *__restrict__ out32,
-    int comp_stride, int elem_stride) {
+    int elem_stride, float *__restrict__ outc, int elemc_stride) {
   __shared__ double sb[kBezWarps][kChunk][3 * (kMaxDeg + 1)];
   __shared__ double sg[kBezWarps][kChunk][3];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -115,7 +115,8 @@ __global__ void __launch_bounds__(32 * kBezWarps) k_to_bezier(
       const double binom = binomial(p0, ix) * binomial(p1, iy) * binomial(p2, iz);
       for (int c = 0; c < nc; ++c) {
         out64[(e * nc + c) * nb + q] = acc[r][c];
-        out32[e * elem_stride + c * comp_stride + q] = (float)(acc[r][c] * binom);
+        out32[e * elem_stride + render_off(nc, n0, nb, iz * n1 + iy, ix, c)] = (float)(acc[r][c] * binom);
+        if (outc) outc[e * elemc_stride + c * roundup8(nb) + q] = (float)(acc[r][c] * binom);
       }
     }
   }
@@ -256,7 +257,7 @@ __device__ float eval_generic(const float *c, const int *deg, float ux, float uy
 }
 
 __global__ void k_eval(ForestView f, const ElemRec *__restrict__ elem, int64_t n_elem, const float *__restrict__ bez,
-                       int elem_stride, int comp_stride, int p0, int p1, int p2, int nc,
+                       int elem_stride, int p0, int p1, int p2, int nc,
                        const float *__restrict__ pts, int64_t n, float *__restrict__ out, uint32_t *status) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
@@ -272,11 +273,11 @@ __global__ void k_eval(ForestView f, const ElemRec *__restrict__ elem, int64_t n
   const float uy = local_u(y, r.a.y, r.c.y, r.d.y);
   const float uz = local_u(z, r.a.z, r.c.z, r.d.z);
   const int deg[3] = {p0, p1, p2};
+  const int n0 = p0 + 1, n1 = p1 + 1, nb = n0 * n1 * (p2 + 1);
+  const float *eb = bez + (int64_t)e * elem_stride;
   for (int c = 0; c < nc; ++c) {
-    const float *cb = bez + (int64_t)e * elem_stride + c * comp_stride;
     float cl[(kMaxDeg + 1) * (kMaxDeg + 1) * (kMaxDeg + 1)];
-    const int nb = (p0 + 1) * (p1 + 1) * (p2 + 1);
-    for (int t = 0; t < nb; ++t) cl[t] = __ldg(cb + t);
+    for (int t = 0; t < nb; ++t) cl[t] = __ldg(eb + render_off(nc, n0, nb, t / n0, t % n0, c));
     out[q * nc + c] = eval_generic(cl, deg, ux, uy, uz);
   }
 }
@@ -295,17 +296,6 @@ __device__ __forceinline__ float lg2_approx(float x) {
   float y;
   asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
   return y;
-}
-
-// 8x4-pixel warp tiles, numbered so that 4 consecutive tiles form a 16x8 patch
-// and consecutive patches run along rows (spatial locality between the warps
-// that fetch neighbouring tile numbers).
-__device__ __forceinline__ void tile_origin(int tile, int tiles_x, int *i0, int *j0) {
-  const int patch = tile >> 2, sub = tile & 3;
-  const int patches_x = (tiles_x + 1) >> 1;
-  const int px = patch % patches_x, py = patch / patches_x;
-  *i0 = (px * 2 + (sub & 1)) * 8;
-  *j0 = (py * 2 + (sub >> 1)) * 4;
 }
 
 struct Ray {
@@ -352,18 +342,224 @@ __device__ __forceinline__ bool make_ray(const RayConsts &K, int i, int j, Ray &
   return hit && tin < tout;
 }
 
+// Transfer function lookup and one Alg. 2 update in transmittance form
+// (Tr = 1 - alpha_dst): w = (1 - T) Tr, C += w C_src, Tr *= T.
+__device__ __forceinline__ void composite(const float4 *tfb, const float4 *tfd, float v, float seg,
+                                          const RenderParams &prm, float &C0, float &C1, float &C2, float &Tr) {
+  const float x = fminf(fmaxf(fmaf(v, prm.tf_scale, prm.tf_bias), 0.f), 255.f);
+  const int q = min((int)x, 254);
+  const float fr = x - (float)q;
+  const float4 e0 = tfb[q], de = tfd[q];
+  const float sa = fmaf(fr, de.w, e0.w);
+  const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (seg * prm.inv_xi));
+  const float w = fmaf(-Tr, T, Tr);
+  C0 = fmaf(w, fmaf(fr, de.x, e0.x), C0);
+  C1 = fmaf(w, fmaf(fr, de.y, e0.y), C1);
+  C2 = fmaf(w, fmaf(fr, de.z, e0.z), C2);
+  Tr *= T;
+}
+
 // FIELD: 0 = one component (scalar or chosen), 1 = magnitude of 3 components.
-// Persistent warps: each warp takes 8x4-pixel tiles from a counter until the
-// image is done; one lane traces one ray.  In the sample loop the Alg. 2 update
-// of sample k is issued together with the evaluation of sample k+1 (they are
-// independent), so the scheduler can overlap their latencies; a ray that
-// terminates after sample k discards the already evaluated sample k+1.
+// One CTA of 4 warps renders a 16x8-pixel tile (each warp an 8x4 patch), so
+// the warps sharing an SM's L1 march through neighbouring elements; one lane
+// traces one ray.  The element-change branch (look-up and block loads) is kept
+// minimal: a warp runs it whenever any of its lanes changes element, which
+// happens almost every iteration.
+//
+// In the sample loop the Alg. 2 update of sample k is issued together with
+// the evaluation of sample k+1 (they are independent), so the scheduler can
+// overlap their latencies; a ray that terminates after sample k discards the
+// already evaluated sample k+1.
+// ---- packed two-lane FP32 (fma.rn.f32x2 and friends; lane "lo" first) ----
+typedef unsigned long long f2;
+
+__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
+  f2 d;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
+  return d;
+}
+__device__ __forceinline__ void f2_unpack(f2 a, float &lo, float &hi) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
+}
+__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
+  f2 d;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
+  return d;
+}
+__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
+  f2 d;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
+  return d;
+}
+// 256-bit read-only load (32-byte aligned address)
+__device__ __forceinline__ void ld256(const void *p, f2 &a, f2 &b, f2 &c, f2 &d) {
+  asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
+}
+__device__ __forceinline__ float4 f2x2_to_float4(f2 a, f2 b) {
+  float4 r;
+  f2_unpack(a, r.x, r.y);
+  f2_unpack(b, r.z, r.w);
+  return r;
+}
+
+// Element record: two 256-bit loads.
+__device__ __forceinline__ void load_record(const ElemRec *er, float4 &ra, float4 &rb, float4 &rc, float4 &rd) {
+  f2 w0, w1, w2, w3, w4, w5, w6, w7;
+  ld256(er, w0, w1, w2, w3);
+  ld256(reinterpret_cast<const char *>(er) + 32, w4, w5, w6, w7);
+  ra = f2x2_to_float4(w0, w1);
+  rb = f2x2_to_float4(w2, w3);
+  rc = f2x2_to_float4(w4, w5);
+  rd = f2x2_to_float4(w6, w7);
+}
+
+// One element's block in registers and its evaluation at monomials bx, by, bz.
+//   FIELD 0: scalar volume; 1: |v| of a 3-vector; 2: one component of a
+//   3-vector, read from the plain per-component copy.
+template <int P, int FIELD>
+struct Block {
+  static constexpr int N = P + 1;
+  static constexpr int NB = N * N * N;
+  static constexpr bool ROWPAIR = FIELD == 0 && P == 3;   // scalar tricubic: packed row pairs
+  static constexpr bool SCALAR_GENERIC = FIELD == 0 && P != 3;
+  static constexpr bool PAIRS = FIELD == 1;                // components 0 and 1 packed
+  static constexpr bool COMP2 = FIELD == 1 || FIELD == 2;  // one component as plain floats
+  static constexpr int SGF = ((N * N + 1) / 2) * 2 * N;    // scalar generic: floats used (<= stride)
+  static constexpr int PAIRF = (2 * NB + 7) & ~7;          // floats of the component pair block
+  static constexpr int C2F = (NB + 7) & ~7;                // floats of component 2
+
+  f2 rp[ROWPAIR ? 8 : 1][4];                 // row pairs (2m, 2m+1), value i
+  float sg[SCALAR_GENERIC ? ((SGF + 3) & ~3) : 1];
+  f2 cp[PAIRS ? PAIRF / 2 : 1];              // (c0, c1) per q
+  float c2[COMP2 ? C2F : 1];
+
+  __device__ __forceinline__ void load(const float *eb) {
+    if constexpr (ROWPAIR) {
+#pragma unroll
+      for (int m = 0; m < 8; ++m) ld256(eb + 8 * m, rp[m][0], rp[m][1], rp[m][2], rp[m][3]);
+    }
+    if constexpr (SCALAR_GENERIC) {
+      const float4 *b4 = reinterpret_cast<const float4 *>(eb);
+#pragma unroll
+      for (int q = 0; q < (SGF + 3) / 4; ++q) {
+        const float4 v = __ldg(b4 + q);
+        sg[4 * q] = v.x;
+        sg[4 * q + 1] = v.y;
+        sg[4 * q + 2] = v.z;
+        sg[4 * q + 3] = v.w;
+      }
+    }
+    if constexpr (PAIRS) {
+#pragma unroll
+      for (int q = 0; q < PAIRF / 8; ++q) ld256(eb + 8 * q, cp[4 * q], cp[4 * q + 1], cp[4 * q + 2], cp[4 * q + 3]);
+    }
+    if constexpr (COMP2) {
+      const float4 *b4 = reinterpret_cast<const float4 *>(FIELD == 1 ? eb + PAIRF : eb);
+#pragma unroll
+      for (int q = 0; q < C2F / 4; ++q) {
+        const float4 v = __ldg(b4 + q);
+        c2[4 * q] = v.x;
+        c2[4 * q + 1] = v.y;
+        c2[4 * q + 2] = v.z;
+        c2[4 * q + 3] = v.w;
+      }
+    }
+  }
+
+  __device__ __forceinline__ float eval(const float *bx, const float *by, const float *bz, int comp) const {
+    if constexpr (ROWPAIR) {
+      // rows r = k*4 + j; pair m = 2k + (j >> 1) holds (row 2m, row 2m+1)
+      const f2 X0 = f2_pack(bx[0], bx[0]), X1 = f2_pack(bx[1], bx[1]);
+      const f2 X2 = f2_pack(bx[2], bx[2]), X3 = f2_pack(bx[3], bx[3]);
+      const f2 Y01 = f2_pack(by[0], by[1]), Y23 = f2_pack(by[2], by[3]);
+      f2 F = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const f2 *a = rp[2 * k], *b = rp[2 * k + 1];
+        const f2 S0 = f2_fma(a[3], X3, f2_fma(a[2], X2, f2_fma(a[1], X1, f2_mul(a[0], X0))));
+        const f2 S1 = f2_fma(b[3], X3, f2_fma(b[2], X2, f2_fma(b[1], X1, f2_mul(b[0], X0))));
+        const f2 T = f2_fma(S1, Y23, f2_mul(S0, Y01));   // (t_k over j even, t_k over j odd)
+        const f2 Z = f2_pack(bz[k], bz[k]);
+        F = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, F);
+      }
+      float lo, hi;
+      f2_unpack(F, lo, hi);
+      return lo + hi;
+    } else if constexpr (SCALAR_GENERIC) {
+      float f = 0.f;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        float t = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const int r = k * N + j;
+          float sx = 0.f;
+#pragma unroll
+          for (int i = 0; i < N; ++i) sx = fmaf(sg[(r >> 1) * 2 * N + 2 * i + (r & 1)], bx[i], sx);
+          t = fmaf(sx, by[j], t);
+        }
+        f = fmaf(t, bz[k], f);
+      }
+      return f;
+    } else {
+      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+      if constexpr (PAIRS) {
+        f2 X[N], Y[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          X[i] = f2_pack(bx[i], bx[i]);
+          Y[i] = f2_pack(by[i], by[i]);
+        }
+        f2 V = 0;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          f2 T = 0;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            const f2 *c = &cp[(k * N + j) * N];
+            f2 S = f2_mul(c[0], X[0]);
+#pragma unroll
+            for (int i = 1; i < N; ++i) S = f2_fma(c[i], X[i], S);
+            T = j == 0 ? f2_mul(S, Y[0]) : f2_fma(S, Y[j], T);
+          }
+          const f2 Z = f2_pack(bz[k], bz[k]);
+          V = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, V);
+        }
+        f2_unpack(V, v0, v1);
+      }
+      if constexpr (COMP2) {
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+          float t = 0.f;
+#pragma unroll
+          for (int j = 0; j < N; ++j) {
+            float sx = 0.f;
+#pragma unroll
+            for (int i = 0; i < N; ++i) sx = fmaf(c2[(k * N + j) * N + i], bx[i], sx);
+            t = fmaf(sx, by[j], t);
+          }
+          v2 = fmaf(t, bz[k], v2);
+        }
+      }
+      if constexpr (FIELD == 1) return sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+      return v2;
+    }
+  }
+};
+
+// One CTA of 4 warps renders a 16x8-pixel tile (each warp an 8x4 patch), so
+// the warps sharing an SM's L1 march through neighbouring elements; one lane
+// traces one ray.  The element-change branch (look-up and block loads) is kept
+// minimal: a warp runs it whenever any of its lanes changes element, which
+// happens almost every iteration.
+//
+// In the sample loop the Alg. 2 update of sample k is issued together with
+// the evaluation of sample k+1 (they are independent), so the scheduler can
+// overlap their latencies; a ray that terminates after sample k discards the
+// already evaluated sample k+1.
 template <int P, int FIELD>
 __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ RenderParams prm) {
   constexpr int N = P + 1;
-  constexpr int NB = N * N * N;
-  constexpr int CS = (NB + 3) & ~3;
-  constexpr int NCE = FIELD == 1 ? 3 : 1;
   __shared__ float4 tfb[256], tfd[256];
   for (int q = threadIdx.x; q < 256; q += blockDim.x) {
     const float4 e0 = prm.tf[q], e1 = prm.tf[q < 255 ? q + 1 : 255];
@@ -372,30 +568,20 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
   }
   __syncthreads();
 
-  const int lane = threadIdx.x & 31;
-  const int tiles_x = (prm.width + 7) >> 3;
-  const int tiles_y = (prm.row_end - prm.row_begin + 3) >> 2;
-  const int n_tiles = ((tiles_x + 1) >> 1) * 2 * (((tiles_y + 1) >> 1) * 2);
-  unsigned long long nsamp = 0, nlook = 0, nhit = 0;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+  const int j = prm.row_begin + blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+  unsigned nsamp = 0, nlook = 0, nhit = 0;
+  const float inf = __int_as_float(0x7f800000);
 
-  for (;;) {
-    int tile = 0;
-    if (lane == 0) tile = (int)atomicAdd(prm.counters + kCntTiles, 1ull);
-    tile = __shfl_sync(0xffffffffu, tile, 0);
-    if (tile >= n_tiles) break;
-    int i0, j0;
-    tile_origin(tile, tiles_x, &i0, &j0);
-    const int i = i0 + (lane & 7);
-    const int j = prm.row_begin + j0 + (lane >> 3);
-    if (i >= prm.width || j >= prm.row_end) continue;
-
-    Ray ray;
-    float C0 = 0.f, C1 = 0.f, C2 = 0.f, A = 0.f;
+  Ray ray;
+  if (i < prm.width && j < prm.row_end) {
+    float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.f;
     if (make_ray(prm.ray, i, j, ray)) {
       ++nhit;
-      uint32_t cur = kNone;
+      const float tr_stop = 1.f - prm.alpha_stop;
       float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
-      float cf[NCE][CS];
+      Block<P, FIELD> blk;
       float t = ray.tin;
       int k = 0;
       bool pend = false;     // a sample evaluated but not yet composited
@@ -403,17 +589,7 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
       for (;;) {
         if (!(t < ray.tout)) {
           if (pend) {
-            const float x = fminf(fmaxf((pv - prm.tf_off) * prm.tf_scale, 0.f), 255.f);
-            const int q = min((int)x, 254);
-            const float fr = x - (float)q;
-            const float4 e0 = tfb[q], de = tfd[q];
-            const float sa = fmaf(fr, de.w, e0.w);
-            const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (pseg * prm.inv_xi));
-            const float wgt = (1.f - T) * (1.f - A);
-            C0 = fmaf(wgt, fmaf(fr, de.x, e0.x), C0);
-            C1 = fmaf(wgt, fmaf(fr, de.y, e0.y), C1);
-            C2 = fmaf(wgt, fmaf(fr, de.z, e0.z), C2);
-            A += wgt;
+            composite(tfb, tfd, pv, pseg, prm, C0, C1, C2, Tr);
             ++nsamp;
           }
           break;
@@ -423,62 +599,32 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
         const float pz = fminf(fmaxf(__fmaf_rn(t, ray.d[2], ray.o[2]), 0.f), 1.f);
         const bool inside = px >= ra.x && py >= ra.y && pz >= ra.z && px < rb.x && py < rb.y && pz < rb.z;
         if (!inside) {
-          cur = forest_lookup(prm.forest, px, py, pz, prm.status);
+          const uint32_t cur = forest_lookup(prm.forest, px, py, pz, prm.status);
           if (cur == kNone || (int64_t)cur >= prm.n_elem) {
             set_status(prm.status, kStatusBounds);
             break;
           }
           ++nlook;
-          const ElemRec *er = prm.elem + cur;
-          ra = __ldg(&er->a);
-          rb = __ldg(&er->b);
-          rc = __ldg(&er->c);
-          rd = __ldg(&er->d);
-          const float4 *cb = reinterpret_cast<const float4 *>(prm.bez + (int64_t)cur * prm.elem_stride +
-                                                              (FIELD == 1 ? 0 : prm.comp * prm.comp_stride));
-#pragma unroll
-          for (int c = 0; c < NCE; ++c)
-#pragma unroll
-            for (int q = 0; q < CS / 4; ++q) {
-              const float4 v = __ldg(cb + c * (prm.comp_stride / 4) + q);
-              cf[c][4 * q] = v.x;
-              cf[c][4 * q + 1] = v.y;
-              cf[c][4 * q + 2] = v.z;
-              cf[c][4 * q + 3] = v.w;
-            }
+          load_record(prm.elem + cur, ra, rb, rc, rd);
+          if constexpr (FIELD == 2)
+            blk.load(prm.bezc + (int64_t)cur * prm.elemc_stride + prm.comp * ((Block<P, FIELD>::NB + 7) & ~7));
+          else
+            blk.load(prm.bez + (int64_t)cur * prm.elem_stride);
         }
         float tn = prm.mode == LRVOL_STEP_HEURISTIC ? __fadd_rn(t, ra.w) : __fmaf_rn((float)(k + 1), prm.h, ray.tin);
-        if (!(tn > t)) tn = nextafterf(t, __int_as_float(0x7f800000));
+        if (!(tn > t)) tn = nextafterf(t, inf);
         const float seg = __fsub_rn(fminf(tn, ray.tout), t);
         // evaluate sample k ...
         float bx[N], by[N], bz[N];
         monomials<P>(local_u(px, ra.x, rc.x, rd.x), bx);
         monomials<P>(local_u(py, ra.y, rc.y, rd.y), by);
         monomials<P>(local_u(pz, ra.z, rc.z, rd.z), bz);
-        float v;
-        if constexpr (FIELD == 1) {
-          const float v0 = contract<P>(cf[0], bx, by, bz);
-          const float v1 = contract<P>(cf[NCE > 1 ? 1 : 0], bx, by, bz);
-          const float v2 = contract<P>(cf[NCE > 2 ? 2 : 0], bx, by, bz);
-          v = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
-        } else {
-          v = contract<P>(cf[0], bx, by, bz);
-        }
-        // ... while compositing sample k-1 (transfer function + Alg. 2)
+        const float v = blk.eval(bx, by, bz, prm.comp);
+        // ... while compositing sample k-1
         if (pend) {
-          const float x = fminf(fmaxf((pv - prm.tf_off) * prm.tf_scale, 0.f), 255.f);
-          const int q = min((int)x, 254);
-          const float fr = x - (float)q;
-          const float4 e0 = tfb[q], de = tfd[q];
-          const float sa = fmaf(fr, de.w, e0.w);
-          const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (pseg * prm.inv_xi));
-          const float wgt = (1.f - T) * (1.f - A);
-          C0 = fmaf(wgt, fmaf(fr, de.x, e0.x), C0);
-          C1 = fmaf(wgt, fmaf(fr, de.y, e0.y), C1);
-          C2 = fmaf(wgt, fmaf(fr, de.z, e0.z), C2);
-          A += wgt;
+          composite(tfb, tfd, pv, pseg, prm, C0, C1, C2, Tr);
           ++nsamp;
-          if (A >= prm.alpha_stop) break;
+          if (Tr <= tr_stop) break;
         }
         pend = true;
         pv = v;
@@ -490,7 +636,7 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
         }
       }
     }
-    reinterpret_cast<float4 *>(prm.out)[(int64_t)j * prm.width + i] = make_float4(C0, C1, C2, A);
+    reinterpret_cast<float4 *>(prm.out)[(int64_t)j * prm.width + i] = make_float4(C0, C1, C2, 1.f - Tr);
   }
   // per-warp counters
 #pragma unroll
@@ -500,9 +646,9 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
     nhit += __shfl_down_sync(0xffffffffu, nhit, o);
   }
   if (lane == 0) {
-    atomicAdd(prm.counters + kCntSamples, nsamp);
-    atomicAdd(prm.counters + kCntLookups, nlook);
-    atomicAdd(prm.counters + kCntRays, nhit);
+    atomicAdd(prm.counters + kCntSamples, (unsigned long long)nsamp);
+    atomicAdd(prm.counters + kCntLookups, (unsigned long long)nlook);
+    atomicAdd(prm.counters + kCntRays, (unsigned long long)nhit);
   }
 }
 
@@ -512,8 +658,8 @@ cudaError_t launch_to_bezier(const lrvol_s *v, cudaStream_t s) {
   const int64_t blocks = (v->n_elem + kBezWarps - 1) / kBezWarps;
   k_to_bezier<<<(unsigned)blocks, 32 * kBezWarps, 0, s>>>(v->d_box, v->d_knots, v->d_coef, v->d_weight, v->d_inc_ptr,
                                                          v->d_inc_idx, v->p[0], v->p[1], v->p[2], v->nc, v->kw,
-                                                         v->n_elem, v->d_bez64, v->d_bez32, v->comp_stride,
-                                                         v->elem_stride);
+                                                         v->n_elem, v->d_bez64, v->d_bez32, v->elem_stride,
+                                                         v->d_bezc, v->elemc_stride);
   return cudaGetLastError();
 }
 
@@ -532,47 +678,43 @@ cudaError_t launch_lookup(const lrvol_s *v, const float *pts, int64_t n, uint32_
 
 cudaError_t launch_eval(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s) {
   k_eval<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(forest_view(v), v->d_elem, v->n_elem, v->d_bez32,
-                                                    v->elem_stride, v->comp_stride, v->p[0], v->p[1], v->p[2],
+                                                    v->elem_stride, v->p[0], v->p[1], v->p[2],
                                                     v->nc, pts, n, out, v->d_status);
   return cudaGetLastError();
 }
 
 template <int P, int FIELD>
 cudaError_t launch_render_t(const RenderParams &prm, cudaStream_t s) {
-  static int grid = 0;  // per-instantiation: SMs x resident CTAs (the device does not change in a process)
-  if (grid == 0) {
-    int dev = 0, sms = 0, per_sm = 0;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_render<P, FIELD>, 128, 0);
-    grid = sms * (per_sm > 0 ? per_sm : 1);
-  }
+  const dim3 grid((unsigned)((prm.width + 15) / 16), (unsigned)((prm.row_end - prm.row_begin + 7) / 8));
   k_render<P, FIELD><<<grid, 128, 0, s>>>(prm);
   return cudaGetLastError();
 }
 
 cudaError_t launch_render(const RenderParams &prm, int degree, int field, cudaStream_t s) {
-  const bool mag = field == LRVOL_FIELD_MAGNITUDE;
-  switch (degree * 2 + (mag ? 1 : 0)) {
-    case 2: return launch_render_t<1, 0>(prm, s);
-    case 3: return launch_render_t<1, 1>(prm, s);
-    case 4: return launch_render_t<2, 0>(prm, s);
-    case 5: return launch_render_t<2, 1>(prm, s);
-    case 6: return launch_render_t<3, 0>(prm, s);
-    case 7: return launch_render_t<3, 1>(prm, s);
+  const int f = field == LRVOL_FIELD_MAGNITUDE ? 1 : (field == LRVOL_FIELD_COMPONENT ? 2 : 0);
+  switch (degree * 3 + f) {
+    case 3: return launch_render_t<1, 0>(prm, s);
+    case 4: return launch_render_t<1, 1>(prm, s);
+    case 5: return launch_render_t<1, 2>(prm, s);
+    case 6: return launch_render_t<2, 0>(prm, s);
+    case 7: return launch_render_t<2, 1>(prm, s);
+    case 8: return launch_render_t<2, 2>(prm, s);
+    case 9: return launch_render_t<3, 0>(prm, s);
+    case 10: return launch_render_t<3, 1>(prm, s);
+    case 11: return launch_render_t<3, 2>(prm, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 // ----------------------------------------------------------------------------
 // Scratch for lrvol_render_noalloc.  The render kernel needs a little global
-// memory beyond its inputs and outputs: the tile counter that hands out work,
-// three statistics counters and a status word.  lrvol_render takes them from
-// the handle; lrvol_render_noalloc takes them from this file-scope array, so
-// that the call itself allocates nothing.  Every GPU that loads the library
-// holds these bytes until the process exits.  Host code must not pass the
-// symbol itself to a kernel (on the host it names a stand-in, not device
-// memory): its device address is looked up once per device below.
+// memory beyond its inputs and outputs: three statistics counters and a status
+// word.  lrvol_render takes them from the handle; lrvol_render_noalloc takes
+// them from this file-scope array, so that the call itself allocates nothing.
+// Every GPU that loads the library holds these 256 bytes until the process
+// exits.  Host code must not pass the symbol itself to a kernel (on the host it
+// names a stand-in, not device memory): its device address is looked up once
+// per device below.
 // ----------------------------------------------------------------------------
 }  // namespace lrvol
 

@@ -62,20 +62,44 @@ struct RayConsts {
   int persp;
 };
 
+// FP32 render layout of one element's Bezier block (binomials folded in),
+// arranged for packed two-lane FP32 arithmetic (fma.rn.f32x2) and 256-bit
+// loads; element strides are multiples of 8 floats (32 bytes).
+//   Scalar volumes (nc = 1): rows r = k*(p1+1) + j of (p0+1) values, stored
+//     in pairs: value i of rows 2m and 2m+1 side by side,
+//     off(r, i) = (r >> 1) * 2*(p0+1) + 2*i + (r & 1).
+//   Vector volumes (nc = 3): with q = r*(p0+1) + i, components 0 and 1
+//     interleaved, off(q, c) = 2q + c (c = 0, 1), then component 2 at
+//     pair_floats + q, pair_floats = roundup8(2*nb).  These volumes also keep
+//     a plain copy for component renders: component c at c*roundup8(nb) + q.
+__host__ __device__ inline int roundup8(int x) { return (x + 7) & ~7; }
+__host__ __device__ inline int render_pair_floats(int nb) { return roundup8(2 * nb); }
+__host__ __device__ inline int render_stride(int nc, int n0, int n1, int n2) {
+  const int nb = n0 * n1 * n2;
+  if (nc == 1) return roundup8(((n1 * n2 + 1) / 2) * 2 * n0);
+  return render_pair_floats(nb) + roundup8(nb);
+}
+__host__ __device__ inline int render_off(int nc, int n0, int nb, int r, int i, int c) {
+  if (nc == 1) return (r >> 1) * 2 * n0 + 2 * i + (r & 1);
+  const int q = r * n0 + i;
+  return c < 2 ? 2 * q + c : render_pair_floats(nb) + q;
+}
+
 struct RenderParams {
   const ElemRec *elem;
   int64_t n_elem;
-  const float *bez;       // FP32 Bezier blocks
+  const float *bez;       // FP32 render blocks (layout above)
   int elem_stride;        // floats per element
-  int comp_stride;        // floats per component (multiple of 4)
-  int comp;               // component evaluated (FIELD_COMPONENT / SCALAR)
+  const float *bezc;      // vector volumes: plain per-component copy
+  int elemc_stride;       // floats per element of bezc
+  int comp;               // component evaluated (FIELD_COMPONENT)
   ForestView forest;
   float *out;
   int width, height, row_begin, row_end;
   RayConsts ray;
   int mode;               // LRVOL_STEP_*
   float h, inv_xi, alpha_stop;
-  float tf_off, tf_scale; // x = (v - tf_off) * tf_scale in [0, 255]
+  float tf_scale, tf_bias; // x = v * tf_scale + tf_bias, clamped to [0, 255]
   unsigned long long *counters;
   uint32_t *status;
   float4 tf[256];
@@ -101,8 +125,10 @@ struct lrvol_s {
   int64_t inc_entries = 0;
   double *d_bez64 = nullptr;
   float *d_bez32 = nullptr;
+  float *d_bezc = nullptr;  // vector volumes: plain per-component FP32 copy
+  int elemc_stride = 0;
   int storage = -1;
-  int comp_stride = 0, elem_stride = 0;
+  int elem_stride = 0;  // floats per element of the FP32 render blocks
   lrvol::ElemRec *d_elem = nullptr;
   bool have_bezier = false;
   // forest
