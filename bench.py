@@ -220,7 +220,8 @@ def run_ours(args):
     gv.build_accel(BLOCKS, stream=stream)
     torch.cuda.synchronize()
     t2 = time.perf_counter()
-    gv.to_bezier(stream=stream)
+    gv.to_bezier(storage={"f32": lv.STORE_F32, "f16": lv.STORE_F16, "bf16": lv.STORE_BF16}[args.storage],
+                 stream=stream)
     torch.cuda.synchronize()
     t3 = time.perf_counter()
     ccam, ctf, cstep = lv.make_camera(cam), lv.make_tf(tf), lv.make_step(step)
@@ -289,6 +290,7 @@ def run_ours(args):
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": WORKLOADS[args.workload] + f", forest {BLOCKS[0]}^3",
+                       "block_storage": args.storage,
                        "l2": "flushed between frames (512 MB write, outside the timed events)",
                        "samples_per_frame": samples_per_frame, "rays_hit": st["rays_hit"],
                        "lookups_per_frame": st["lookups"], "parallelism": f"replicas x{ws}"},
@@ -314,6 +316,8 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="Bezier block storage (FP32 accumulation in every case)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up frames
     if args.impl == "reference":

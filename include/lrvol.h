@@ -136,9 +136,13 @@ int lrvol_build_accel(lrvol_t vol, const int32_t blocks[3], void *stream);
 
 /* Change of basis to Bezier blocks (Sec. 3.2.3), FP64 on the GPU by blossoming
  * each incident B-spline's univariate factors over the element (exact up to
- * rounding); blocks are stored as `storage` (LRVOL_STORE_F32 in this build)
- * for rendering and kept in FP64 for lrvol_get_bezier.
- * Errors: LRVOL_ERR_ARG, LRVOL_ERR_UNSUPPORTED (F16/BF16 not built), LRVOL_ERR_OOM, LRVOL_ERR_CUDA. */
+ * rounding); kept in FP64 for lrvol_get_bezier, and stored for rendering as
+ *   LRVOL_STORE_F32   FP32 coefficients;
+ *   LRVOL_STORE_F16 / LRVOL_STORE_BF16   16-bit values with a per-element,
+ *     per-component FP32 offset o = (max+min)/2 and scale s = (max-min)/2:
+ *     a sample differs from the FP32-storage value by at most s*u,
+ *     u = 2^-11 (FP16) or 2^-8 (BF16); accumulation stays FP32.
+ * Errors: LRVOL_ERR_ARG (bad storage), LRVOL_ERR_OOM, LRVOL_ERR_CUDA. */
 int lrvol_to_bezier(lrvol_t vol, int32_t storage, void *stream);
 
 /* Render one image into rgba_dev (height x width x 4 floats, row major,

@@ -429,38 +429,35 @@ int lrvol_build_accel(lrvol_t v, const int32_t blocks[3], void *stream) {
 
 int lrvol_to_bezier(lrvol_t v, int32_t storage, void *stream) {
   if (!v) return fail(LRVOL_ERR_ARG, "null handle");
-  if (storage != LRVOL_STORE_F32) {
-    if (storage == LRVOL_STORE_F16 || storage == LRVOL_STORE_BF16)
-      return fail(LRVOL_ERR_UNSUPPORTED, "reduced-precision storage not built");
+  if (storage != LRVOL_STORE_F32 && storage != LRVOL_STORE_F16 && storage != LRVOL_STORE_BF16)
     return fail(LRVOL_ERR_ARG, "bad storage");
-  }
   std::vector<int64_t> ptr;
   std::vector<int32_t> idx;
   int rc = build_incidence(v, ptr, idx);
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
-  const int nb = (v->p[0] + 1) * (v->p[1] + 1) * (v->p[2] + 1);
-  v->elem_stride = render_stride(v->nc, v->p[0] + 1, v->p[1] + 1, v->p[2] + 1);
-  v->elemc_stride = v->nc == 3 ? 3 * roundup8(nb) : 0;
+  const int n0 = v->p[0] + 1, n1 = v->p[1] + 1, n2 = v->p[2] + 1, nb = n0 * n1 * n2;
+  v->storage = storage;
+  v->elem_bytes = elem_bytes(storage, render_slots(v->nc, n0, n1, n2));
+  v->elemc_bytes = v->nc == 3 ? elem_bytes(storage, 3 * roundup8(nb)) : 0;
   if ((rc = dev_alloc(v, &v->d_inc_ptr, ptr.size(), "alloc incidence ptr")) ||
       (rc = dev_alloc(v, &v->d_inc_idx, idx.size(), "alloc incidence")) ||
       (rc = dev_alloc(v, &v->d_bez64, (size_t)v->n_elem * v->nc * nb, "alloc bezier64")) ||
-      (rc = dev_alloc(v, &v->d_bez32, (size_t)v->n_elem * v->elem_stride, "alloc bezier32")) ||
-      (v->nc == 3 && (rc = dev_alloc(v, &v->d_bezc, (size_t)v->n_elem * v->elemc_stride, "alloc bezier plain"))) ||
+      (rc = dev_alloc(v, &v->d_bez, (size_t)v->n_elem * v->elem_bytes, "alloc render blocks")) ||
+      (v->nc == 3 && (rc = dev_alloc(v, &v->d_bezc, (size_t)v->n_elem * v->elemc_bytes, "alloc render copy"))) ||
       (rc = dev_alloc(v, &v->d_elem, (size_t)v->n_elem, "alloc element records")))
     return rc;
   CU(cudaMemcpyAsync(v->d_inc_ptr, ptr.data(), sizeof(int64_t) * ptr.size(), cudaMemcpyHostToDevice, st),
      "upload incidence ptr");
   CU(cudaMemcpyAsync(v->d_inc_idx, idx.data(), sizeof(int32_t) * idx.size(), cudaMemcpyHostToDevice, st),
      "upload incidence");
-  CU(cudaMemsetAsync(v->d_bez32, 0, sizeof(float) * (size_t)v->n_elem * v->elem_stride, st), "clear bezier32");
-  if (v->d_bezc)
-    CU(cudaMemsetAsync(v->d_bezc, 0, sizeof(float) * (size_t)v->n_elem * v->elemc_stride, st), "clear bezier plain");
+  CU(cudaMemsetAsync(v->d_bez, 0, (size_t)v->n_elem * v->elem_bytes, st), "clear render blocks");
+  if (v->d_bezc) CU(cudaMemsetAsync(v->d_bezc, 0, (size_t)v->n_elem * v->elemc_bytes, st), "clear render copy");
   CU(launch_to_bezier(v, st), "to_bezier kernel");
+  CU(launch_pack(v, st), "pack kernel");
   CU(launch_elem_records(v, st), "element record kernel");
   CU(cudaStreamSynchronize(st), "to_bezier sync");  // host incidence goes out of scope
   v->inc_entries = (int64_t)idx.size();
-  v->storage = storage;
   v->have_bezier = true;
   return LRVOL_OK;
 }
@@ -491,10 +488,10 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   std::memset(&prm, 0, sizeof(prm));
   prm.elem = v->d_elem;
   prm.n_elem = v->n_elem;
-  prm.bez = v->d_bez32;
-  prm.elem_stride = v->elem_stride;
+  prm.bez = v->d_bez;
+  prm.elem_bytes = v->elem_bytes;
   prm.bezc = v->d_bezc;
-  prm.elemc_stride = v->elemc_stride;
+  prm.elemc_bytes = v->elemc_bytes;
   prm.comp = field == LRVOL_FIELD_COMPONENT ? step->component : 0;
   prm.forest = forest_view(v);
   prm.out = rgba_dev;
@@ -513,7 +510,7 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   prm.status = v->d_status;
   for (int q = 0; q < 256; ++q) prm.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
   CU(cudaMemsetAsync(v->d_counters, 0, sizeof(unsigned long long) * kNumCounters, st), "clear counters");
-  if (r1 > r0) CU(launch_render(prm, v->p[0], field, st), "render kernel");
+  if (r1 > r0) CU(launch_render(prm, v->p[0], field, v->storage, st), "render kernel");
   return LRVOL_OK;
 }
 
@@ -545,10 +542,10 @@ int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf,
   std::memset(&prm, 0, sizeof(prm));
   prm.elem = v->d_elem;
   prm.n_elem = v->n_elem;
-  prm.bez = v->d_bez32;
-  prm.elem_stride = v->elem_stride;
+  prm.bez = v->d_bez;
+  prm.elem_bytes = v->elem_bytes;
   prm.bezc = v->d_bezc;
-  prm.elemc_stride = v->elemc_stride;
+  prm.elemc_bytes = v->elemc_bytes;
   prm.comp = field == LRVOL_FIELD_COMPONENT ? step->component : 0;
   prm.forest = forest_view(v);
   prm.out = rgba_dev;
@@ -564,7 +561,7 @@ int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf,
   prm.tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
   prm.tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
   for (int q = 0; q < 256; ++q) prm.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
-  cudaError_t e = launch_render_static(prm, v->p[0], field, (cudaStream_t)stream,
+  cudaError_t e = launch_render_static(prm, v->p[0], field, v->storage, (cudaStream_t)stream,
                                        reinterpret_cast<unsigned long long *>(counters_dev));
   if (e != cudaSuccess) return cuda_fail(e, "render_noalloc");
   return LRVOL_OK;
@@ -626,7 +623,7 @@ void lrvol_destroy(lrvol_t v) {
   if (!v) return;
   cudaDeviceSynchronize();
   void *ptrs[] = {v->d_box,   v->d_knots, v->d_coef,  v->d_weight, v->d_inc_ptr,  v->d_inc_idx, v->d_bez64,
-                  v->d_bez32, v->d_bezc,  v->d_elem,  v->d_head,  v->d_nodes, v->d_counters, v->d_status};
+                  v->d_bez,   v->d_bezc,  v->d_elem,  v->d_head,  v->d_nodes, v->d_counters, v->d_status};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete v;

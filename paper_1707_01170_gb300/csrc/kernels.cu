@@ -8,6 +8,8 @@
 //   k_eval         look-up + Bezier block evaluation at points.
 //   k_render       Sec. 4: per-pixel ray casting with element reuse, Eq. 4
 //                  steps, transfer function and Alg. 2 compositing.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -65,8 +67,7 @@ constexpr int kChunk = 32;
 __global__ void __launch_bounds__(32 * kBezWarps) k_to_bezier(
     const double *__restrict__ box, const double *__restrict__ knots, const double *__restrict__ coef,
     const double *__restrict__ weight, const int64_t *__restrict__ inc_ptr, const int32_t *__restrict__ inc_idx,
-    int p0, int p1, int p2, int nc, int kw, int64_t n_elem, double *__restrict__ out64, float *__restrict__ out32,
-    int elem_stride, float *__restrict__ outc, int elemc_stride) {
+    int p0, int p1, int p2, int nc, int kw, int64_t n_elem, double *__restrict__ out64) {
   __shared__ double sb[kBezWarps][kChunk][3 * (kMaxDeg + 1)];
   __shared__ double sg[kBezWarps][kChunk][3];
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -106,18 +107,64 @@ __global__ void __launch_bounds__(32 * kBezWarps) k_to_bezier(
     }
     __syncwarp();
   }
-  // FP32 render copy with the binomials folded in: c_ijk C(p0,i) C(p1,j) C(p2,k),
-  // so that evaluation multiplies by plain monomials u^i (1-u)^(p-i).
   for (int r = 0; r < 4; ++r) {
     const int q = lane + 32 * r;
-    if (q < nb) {
-      const int ix = q % n0, iy = (q / n0) % n1, iz = q / (n0 * n1);
-      const double binom = binomial(p0, ix) * binomial(p1, iy) * binomial(p2, iz);
-      for (int c = 0; c < nc; ++c) {
-        out64[(e * nc + c) * nb + q] = acc[r][c];
-        out32[e * elem_stride + render_off(nc, n0, nb, iz * n1 + iy, ix, c)] = (float)(acc[r][c] * binom);
-        if (outc) outc[e * elemc_stride + c * roundup8(nb) + q] = (float)(acc[r][c] * binom);
+    if (q < nb)
+      for (int c = 0; c < nc; ++c) out64[(e * nc + c) * nb + q] = acc[r][c];
+  }
+}
+
+// Render copy of the FP64 blocks (layout and storage in lrvol_internal.h):
+// binomials folded in; for 16-bit storage a per-element, per-component offset
+// o = (max+min)/2 and scale s = (max-min)/2 of the FP64 coefficients, and
+// q' = binomial*(c - o)/s rounded once from FP64.  One warp per element.
+__device__ __forceinline__ void store_slot(unsigned char *base, int storage, int slot, double x) {
+  if (storage == LRVOL_STORE_F32) {
+    reinterpret_cast<float *>(base)[slot] = (float)x;
+  } else if (storage == LRVOL_STORE_F16) {
+    reinterpret_cast<__half *>(base + kHeaderBytes)[slot] = __double2half(x);
+  } else {
+    reinterpret_cast<__nv_bfloat16 *>(base + kHeaderBytes)[slot] = __double2bfloat16(x);
+  }
+}
+
+__global__ void __launch_bounds__(32 * kBezWarps) k_pack(const double *__restrict__ b64, int p0, int p1, int p2, int nc,
+                                                        int64_t n_elem, int storage, unsigned char *__restrict__ out,
+                                                        int ebytes, unsigned char *__restrict__ outc, int ecbytes) {
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t e = (int64_t)blockIdx.x * kBezWarps + w;
+  if (e >= n_elem) return;
+  const int n0 = p0 + 1, n1 = p1 + 1, nb = n0 * n1 * (p2 + 1);
+  const double *be = b64 + e * nc * nb;
+  double o[3] = {0.0, 0.0, 0.0}, sc[3] = {1.0, 1.0, 1.0};
+  if (storage != LRVOL_STORE_F32) {
+    for (int c = 0; c < nc; ++c) {
+      double mn = __longlong_as_double(0x7ff0000000000000ll), mx = -mn;
+      for (int q = lane; q < nb; q += 32) {
+        mn = fmin(mn, be[c * nb + q]);
+        mx = fmax(mx, be[c * nb + q]);
       }
+      for (int off = 16; off > 0; off >>= 1) {
+        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+      }
+      o[c] = 0.5 * (mx + mn);
+      sc[c] = 0.5 * (mx - mn);
+      if (!(sc[c] > 0.0)) sc[c] = 1.0;
+    }
+    if (lane < 8) {
+      const float hv = lane < 3 ? (float)o[lane] : (lane < 6 ? (float)sc[lane - 3] : 0.f);
+      reinterpret_cast<float *>(out + e * ebytes)[lane] = hv;
+      if (outc) reinterpret_cast<float *>(outc + e * ecbytes)[lane] = hv;
+    }
+  }
+  for (int q = lane; q < nb; q += 32) {
+    const int ix = q % n0, iy = (q / n0) % n1, iz = q / (n0 * n1);
+    const double binom = binomial(p0, ix) * binomial(p1, iy) * binomial(p2, iz);
+    for (int c = 0; c < nc; ++c) {
+      const double x = binom * (be[c * nb + q] - o[c]) / sc[c];
+      store_slot(out + e * ebytes, storage, render_slot(nc, n0, nb, iz * n1 + iy, ix, c), x);
+      if (outc) store_slot(outc + e * ecbytes, storage, c * roundup8(nb) + q, x);
     }
   }
 }
@@ -256,8 +303,15 @@ __device__ float eval_generic(const float *c, const int *deg, float ux, float uy
   return f;
 }
 
-__global__ void k_eval(ForestView f, const ElemRec *__restrict__ elem, int64_t n_elem, const float *__restrict__ bez,
-                       int elem_stride, int p0, int p1, int p2, int nc,
+__device__ __forceinline__ float load_slot(const unsigned char *eb, int storage, int slot) {
+  if (storage == LRVOL_STORE_F32) return __ldg(reinterpret_cast<const float *>(eb) + slot);
+  const unsigned short h = __ldg(reinterpret_cast<const unsigned short *>(eb + kHeaderBytes) + slot);
+  if (storage == LRVOL_STORE_F16) return __half2float(__ushort_as_half(h));
+  return __uint_as_float((unsigned)h << 16);
+}
+
+__global__ void k_eval(ForestView f, const ElemRec *__restrict__ elem, int64_t n_elem,
+                       const unsigned char *__restrict__ bez, int ebytes, int storage, int p0, int p1, int p2, int nc,
                        const float *__restrict__ pts, int64_t n, float *__restrict__ out, uint32_t *status) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= n) return;
@@ -274,11 +328,17 @@ __global__ void k_eval(ForestView f, const ElemRec *__restrict__ elem, int64_t n
   const float uz = local_u(z, r.a.z, r.c.z, r.d.z);
   const int deg[3] = {p0, p1, p2};
   const int n0 = p0 + 1, n1 = p1 + 1, nb = n0 * n1 * (p2 + 1);
-  const float *eb = bez + (int64_t)e * elem_stride;
+  const unsigned char *eb = bez + (int64_t)e * ebytes;
   for (int c = 0; c < nc; ++c) {
     float cl[(kMaxDeg + 1) * (kMaxDeg + 1) * (kMaxDeg + 1)];
-    for (int t = 0; t < nb; ++t) cl[t] = __ldg(eb + render_off(nc, n0, nb, t / n0, t % n0, c));
-    out[q * nc + c] = eval_generic(cl, deg, ux, uy, uz);
+    for (int t = 0; t < nb; ++t) cl[t] = load_slot(eb, storage, render_slot(nc, n0, nb, t / n0, t % n0, c));
+    const float v = eval_generic(cl, deg, ux, uy, uz);
+    if (storage == LRVOL_STORE_F32) {
+      out[q * nc + c] = v;
+    } else {
+      const float *hdr = reinterpret_cast<const float *>(eb);
+      out[q * nc + c] = fmaf(__ldg(hdr + 3 + c), v, __ldg(hdr + c));
+    }
   }
 }
 
@@ -359,17 +419,6 @@ __device__ __forceinline__ void composite(const float4 *tfb, const float4 *tfd, 
   Tr *= T;
 }
 
-// FIELD: 0 = one component (scalar or chosen), 1 = magnitude of 3 components.
-// One CTA of 4 warps renders a 16x8-pixel tile (each warp an 8x4 patch), so
-// the warps sharing an SM's L1 march through neighbouring elements; one lane
-// traces one ray.  The element-change branch (look-up and block loads) is kept
-// minimal: a warp runs it whenever any of its lanes changes element, which
-// happens almost every iteration.
-//
-// In the sample loop the Alg. 2 update of sample k is issued together with
-// the evaluation of sample k+1 (they are independent), so the scheduler can
-// overlap their latencies; a ray that terminates after sample k discards the
-// already evaluated sample k+1.
 // ---- packed two-lane FP32 (fma.rn.f32x2 and friends; lane "lo" first) ----
 typedef unsigned long long f2;
 
@@ -413,10 +462,27 @@ __device__ __forceinline__ void load_record(const ElemRec *er, float4 &ra, float
   rd = f2x2_to_float4(w6, w7);
 }
 
+// 16-bit storage: two values of one 32-bit word -> FP32 pair (lo = low half).
+template <int STORE>
+__device__ __forceinline__ float h_to_f(unsigned h) {
+  if constexpr (STORE == LRVOL_STORE_F16) return __half2float(__ushort_as_half((unsigned short)h));
+  return __uint_as_float(h << 16);
+}
+template <int STORE>
+__device__ __forceinline__ f2 word_to_f2(unsigned w) {
+  if constexpr (STORE == LRVOL_STORE_BF16) {
+    return ((f2)(w & 0xffff0000u) << 32) | (f2)(w << 16);
+  } else {
+    return f2_pack(h_to_f<STORE>(w & 0xffffu), h_to_f<STORE>(w >> 16));
+  }
+}
+
 // One element's block in registers and its evaluation at monomials bx, by, bz.
 //   FIELD 0: scalar volume; 1: |v| of a 3-vector; 2: one component of a
 //   3-vector, read from the plain per-component copy.
-template <int P, int FIELD>
+//   STORE: LRVOL_STORE_F32, or F16/BF16 values converted to FP32 when the
+//   element is entered, with the value of component c = o_c + s_c * contraction.
+template <int P, int FIELD, int STORE>
 struct Block {
   static constexpr int N = P + 1;
   static constexpr int NB = N * N * N;
@@ -424,49 +490,118 @@ struct Block {
   static constexpr bool SCALAR_GENERIC = FIELD == 0 && P != 3;
   static constexpr bool PAIRS = FIELD == 1;                // components 0 and 1 packed
   static constexpr bool COMP2 = FIELD == 1 || FIELD == 2;  // one component as plain floats
-  static constexpr int SGF = ((N * N + 1) / 2) * 2 * N;    // scalar generic: floats used (<= stride)
-  static constexpr int PAIRF = (2 * NB + 7) & ~7;          // floats of the component pair block
-  static constexpr int C2F = (NB + 7) & ~7;                // floats of component 2
+  static constexpr bool F32 = STORE == LRVOL_STORE_F32;
+  static constexpr int SGF = ((N * N + 1) / 2) * 2 * N;    // scalar generic: slots used (<= stride)
+  static constexpr int PAIRF = (2 * NB + 7) & ~7;          // slots of the component pair block
+  static constexpr int C2F = (NB + 7) & ~7;                // slots of one plain component
 
   f2 rp[ROWPAIR ? 8 : 1][4];                 // row pairs (2m, 2m+1), value i
-  float sg[SCALAR_GENERIC ? ((SGF + 3) & ~3) : 1];
+  float sg[SCALAR_GENERIC ? ((SGF + 7) & ~7) : 1];
   f2 cp[PAIRS ? PAIRF / 2 : 1];              // (c0, c1) per q
   float c2[COMP2 ? C2F : 1];
+  float oa, sa, ob, sb, oc, sc;              // affine map of 16-bit storage (component a/b/c)
 
-  __device__ __forceinline__ void load(const float *eb) {
-    if constexpr (ROWPAIR) {
+  __device__ __forceinline__ void load(const unsigned char *eb, int comp) {
+    if constexpr (F32) {
+      const float *fb = reinterpret_cast<const float *>(eb);
+      if constexpr (ROWPAIR) {
 #pragma unroll
-      for (int m = 0; m < 8; ++m) ld256(eb + 8 * m, rp[m][0], rp[m][1], rp[m][2], rp[m][3]);
-    }
-    if constexpr (SCALAR_GENERIC) {
-      const float4 *b4 = reinterpret_cast<const float4 *>(eb);
-#pragma unroll
-      for (int q = 0; q < (SGF + 3) / 4; ++q) {
-        const float4 v = __ldg(b4 + q);
-        sg[4 * q] = v.x;
-        sg[4 * q + 1] = v.y;
-        sg[4 * q + 2] = v.z;
-        sg[4 * q + 3] = v.w;
+        for (int m = 0; m < 8; ++m) ld256(fb + 8 * m, rp[m][0], rp[m][1], rp[m][2], rp[m][3]);
       }
-    }
-    if constexpr (PAIRS) {
+      if constexpr (SCALAR_GENERIC) {
+        const float4 *b4 = reinterpret_cast<const float4 *>(fb);
 #pragma unroll
-      for (int q = 0; q < PAIRF / 8; ++q) ld256(eb + 8 * q, cp[4 * q], cp[4 * q + 1], cp[4 * q + 2], cp[4 * q + 3]);
-    }
-    if constexpr (COMP2) {
-      const float4 *b4 = reinterpret_cast<const float4 *>(FIELD == 1 ? eb + PAIRF : eb);
+        for (int q = 0; q < (SGF + 3) / 4; ++q) {
+          const float4 v = __ldg(b4 + q);
+          sg[4 * q] = v.x;
+          sg[4 * q + 1] = v.y;
+          sg[4 * q + 2] = v.z;
+          sg[4 * q + 3] = v.w;
+        }
+      }
+      if constexpr (PAIRS) {
 #pragma unroll
-      for (int q = 0; q < C2F / 4; ++q) {
-        const float4 v = __ldg(b4 + q);
-        c2[4 * q] = v.x;
-        c2[4 * q + 1] = v.y;
-        c2[4 * q + 2] = v.z;
-        c2[4 * q + 3] = v.w;
+        for (int q = 0; q < PAIRF / 8; ++q) ld256(fb + 8 * q, cp[4 * q], cp[4 * q + 1], cp[4 * q + 2], cp[4 * q + 3]);
+      }
+      if constexpr (COMP2) {
+        const float4 *b4 = reinterpret_cast<const float4 *>(FIELD == 1 ? fb + PAIRF : fb + comp * C2F);
+#pragma unroll
+        for (int q = 0; q < C2F / 4; ++q) {
+          const float4 v = __ldg(b4 + q);
+          c2[4 * q] = v.x;
+          c2[4 * q + 1] = v.y;
+          c2[4 * q + 2] = v.z;
+          c2[4 * q + 3] = v.w;
+        }
+      }
+    } else {
+      const float4 *hdr = reinterpret_cast<const float4 *>(eb);
+      const float4 h0 = __ldg(hdr), h1 = __ldg(hdr + 1);   // o0 o1 o2 s0 | s1 s2 - -
+      const uint4 *d = reinterpret_cast<const uint4 *>(eb + kHeaderBytes);   // 8 slots per chunk
+      if constexpr (ROWPAIR) {
+        oa = h0.x;
+        sa = h0.w;
+#pragma unroll
+        for (int m = 0; m < 8; ++m) {   // chunk m holds words 4m+i = (row 2m, row 2m+1) value i
+          const uint4 w = __ldg(d + m);
+          rp[m][0] = word_to_f2<STORE>(w.x);
+          rp[m][1] = word_to_f2<STORE>(w.y);
+          rp[m][2] = word_to_f2<STORE>(w.z);
+          rp[m][3] = word_to_f2<STORE>(w.w);
+        }
+      }
+      if constexpr (SCALAR_GENERIC) {
+        oa = h0.x;
+        sa = h0.w;
+#pragma unroll
+        for (int q = 0; q < (SGF + 7) / 8; ++q) {
+          const uint4 w = __ldg(d + q);
+          const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            sg[8 * q + 2 * t] = h_to_f<STORE>(ws[t] & 0xffffu);
+            sg[8 * q + 2 * t + 1] = h_to_f<STORE>(ws[t] >> 16);
+          }
+        }
+      }
+      if constexpr (PAIRS) {
+        oa = h0.x;
+        ob = h0.y;
+        sa = h0.w;
+        sb = h1.x;
+#pragma unroll
+        for (int q = 0; q < PAIRF / 8; ++q) {
+          const uint4 w = __ldg(d + q);
+          cp[4 * q] = word_to_f2<STORE>(w.x);
+          cp[4 * q + 1] = word_to_f2<STORE>(w.y);
+          cp[4 * q + 2] = word_to_f2<STORE>(w.z);
+          cp[4 * q + 3] = word_to_f2<STORE>(w.w);
+        }
+      }
+      if constexpr (COMP2) {
+        if constexpr (FIELD == 1) {
+          oc = h0.z;
+          sc = h1.y;
+        } else {
+          oc = comp == 0 ? h0.x : (comp == 1 ? h0.y : h0.z);
+          sc = comp == 0 ? h0.w : (comp == 1 ? h1.x : h1.y);
+        }
+        const uint4 *dc = d + (FIELD == 1 ? PAIRF : comp * C2F) / 8;
+#pragma unroll
+        for (int q = 0; q < C2F / 8; ++q) {
+          const uint4 w = __ldg(dc + q);
+          const unsigned ws[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t) {
+            c2[8 * q + 2 * t] = h_to_f<STORE>(ws[t] & 0xffffu);
+            c2[8 * q + 2 * t + 1] = h_to_f<STORE>(ws[t] >> 16);
+          }
+        }
       }
     }
   }
 
-  __device__ __forceinline__ float eval(const float *bx, const float *by, const float *bz, int comp) const {
+  __device__ __forceinline__ float eval(const float *bx, const float *by, const float *bz) const {
     if constexpr (ROWPAIR) {
       // rows r = k*4 + j; pair m = 2k + (j >> 1) holds (row 2m, row 2m+1)
       const f2 X0 = f2_pack(bx[0], bx[0]), X1 = f2_pack(bx[1], bx[1]);
@@ -484,7 +619,7 @@ struct Block {
       }
       float lo, hi;
       f2_unpack(F, lo, hi);
-      return lo + hi;
+      return F32 ? lo + hi : fmaf(sa, lo + hi, oa);
     } else if constexpr (SCALAR_GENERIC) {
       float f = 0.f;
 #pragma unroll
@@ -500,7 +635,7 @@ struct Block {
         }
         f = fmaf(t, bz[k], f);
       }
-      return f;
+      return F32 ? f : fmaf(sa, f, oa);
     } else {
       float v0 = 0.f, v1 = 0.f, v2 = 0.f;
       if constexpr (PAIRS) {
@@ -526,6 +661,10 @@ struct Block {
           V = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, V);
         }
         f2_unpack(V, v0, v1);
+        if constexpr (!F32) {
+          v0 = fmaf(sa, v0, oa);
+          v1 = fmaf(sb, v1, ob);
+        }
       }
       if constexpr (COMP2) {
 #pragma unroll
@@ -540,6 +679,7 @@ struct Block {
           }
           v2 = fmaf(t, bz[k], v2);
         }
+        if constexpr (!F32) v2 = fmaf(sc, v2, oc);
       }
       if constexpr (FIELD == 1) return sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
       return v2;
@@ -557,7 +697,7 @@ struct Block {
 // the evaluation of sample k+1 (they are independent), so the scheduler can
 // overlap their latencies; a ray that terminates after sample k discards the
 // already evaluated sample k+1.
-template <int P, int FIELD>
+template <int P, int FIELD, int STORE>
 __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ RenderParams prm) {
   constexpr int N = P + 1;
   __shared__ float4 tfb[256], tfd[256];
@@ -581,7 +721,7 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
       ++nhit;
       const float tr_stop = 1.f - prm.alpha_stop;
       float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
-      Block<P, FIELD> blk;
+      Block<P, FIELD, STORE> blk;
       float t = ray.tin;
       int k = 0;
       bool pend = false;     // a sample evaluated but not yet composited
@@ -607,9 +747,9 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
           ++nlook;
           load_record(prm.elem + cur, ra, rb, rc, rd);
           if constexpr (FIELD == 2)
-            blk.load(prm.bezc + (int64_t)cur * prm.elemc_stride + prm.comp * ((Block<P, FIELD>::NB + 7) & ~7));
+            blk.load(prm.bezc + (int64_t)cur * prm.elemc_bytes, prm.comp);
           else
-            blk.load(prm.bez + (int64_t)cur * prm.elem_stride);
+            blk.load(prm.bez + (int64_t)cur * prm.elem_bytes, 0);
         }
         float tn = prm.mode == LRVOL_STEP_HEURISTIC ? __fadd_rn(t, ra.w) : __fmaf_rn((float)(k + 1), prm.h, ray.tin);
         if (!(tn > t)) tn = nextafterf(t, inf);
@@ -619,7 +759,7 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
         monomials<P>(local_u(px, ra.x, rc.x, rd.x), bx);
         monomials<P>(local_u(py, ra.y, rc.y, rd.y), by);
         monomials<P>(local_u(pz, ra.z, rc.z, rd.z), bz);
-        const float v = blk.eval(bx, by, bz, prm.comp);
+        const float v = blk.eval(bx, by, bz);
         // ... while compositing sample k-1
         if (pend) {
           composite(tfb, tfd, pv, pseg, prm, C0, C1, C2, Tr);
@@ -658,8 +798,14 @@ cudaError_t launch_to_bezier(const lrvol_s *v, cudaStream_t s) {
   const int64_t blocks = (v->n_elem + kBezWarps - 1) / kBezWarps;
   k_to_bezier<<<(unsigned)blocks, 32 * kBezWarps, 0, s>>>(v->d_box, v->d_knots, v->d_coef, v->d_weight, v->d_inc_ptr,
                                                          v->d_inc_idx, v->p[0], v->p[1], v->p[2], v->nc, v->kw,
-                                                         v->n_elem, v->d_bez64, v->d_bez32, v->elem_stride,
-                                                         v->d_bezc, v->elemc_stride);
+                                                         v->n_elem, v->d_bez64);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const lrvol_s *v, cudaStream_t s) {
+  const int64_t blocks = (v->n_elem + kBezWarps - 1) / kBezWarps;
+  k_pack<<<(unsigned)blocks, 32 * kBezWarps, 0, s>>>(v->d_bez64, v->p[0], v->p[1], v->p[2], v->nc, v->n_elem,
+                                                    v->storage, v->d_bez, v->elem_bytes, v->d_bezc, v->elemc_bytes);
   return cudaGetLastError();
 }
 
@@ -677,31 +823,41 @@ cudaError_t launch_lookup(const lrvol_s *v, const float *pts, int64_t n, uint32_
 }
 
 cudaError_t launch_eval(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s) {
-  k_eval<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(forest_view(v), v->d_elem, v->n_elem, v->d_bez32,
-                                                    v->elem_stride, v->p[0], v->p[1], v->p[2],
+  k_eval<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(forest_view(v), v->d_elem, v->n_elem, v->d_bez,
+                                                    v->elem_bytes, v->storage, v->p[0], v->p[1], v->p[2],
                                                     v->nc, pts, n, out, v->d_status);
   return cudaGetLastError();
 }
 
-template <int P, int FIELD>
+template <int P, int FIELD, int STORE>
 cudaError_t launch_render_t(const RenderParams &prm, cudaStream_t s) {
   const dim3 grid((unsigned)((prm.width + 15) / 16), (unsigned)((prm.row_end - prm.row_begin + 7) / 8));
-  k_render<P, FIELD><<<grid, 128, 0, s>>>(prm);
+  k_render<P, FIELD, STORE><<<grid, 128, 0, s>>>(prm);
   return cudaGetLastError();
 }
 
-cudaError_t launch_render(const RenderParams &prm, int degree, int field, cudaStream_t s) {
-  const int f = field == LRVOL_FIELD_MAGNITUDE ? 1 : (field == LRVOL_FIELD_COMPONENT ? 2 : 0);
+template <int STORE>
+cudaError_t launch_render_s(const RenderParams &prm, int degree, int f, cudaStream_t s) {
   switch (degree * 3 + f) {
-    case 3: return launch_render_t<1, 0>(prm, s);
-    case 4: return launch_render_t<1, 1>(prm, s);
-    case 5: return launch_render_t<1, 2>(prm, s);
-    case 6: return launch_render_t<2, 0>(prm, s);
-    case 7: return launch_render_t<2, 1>(prm, s);
-    case 8: return launch_render_t<2, 2>(prm, s);
-    case 9: return launch_render_t<3, 0>(prm, s);
-    case 10: return launch_render_t<3, 1>(prm, s);
-    case 11: return launch_render_t<3, 2>(prm, s);
+    case 3: return launch_render_t<1, 0, STORE>(prm, s);
+    case 4: return launch_render_t<1, 1, STORE>(prm, s);
+    case 5: return launch_render_t<1, 2, STORE>(prm, s);
+    case 6: return launch_render_t<2, 0, STORE>(prm, s);
+    case 7: return launch_render_t<2, 1, STORE>(prm, s);
+    case 8: return launch_render_t<2, 2, STORE>(prm, s);
+    case 9: return launch_render_t<3, 0, STORE>(prm, s);
+    case 10: return launch_render_t<3, 1, STORE>(prm, s);
+    case 11: return launch_render_t<3, 2, STORE>(prm, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_render(const RenderParams &prm, int degree, int field, int storage, cudaStream_t s) {
+  const int f = field == LRVOL_FIELD_MAGNITUDE ? 1 : (field == LRVOL_FIELD_COMPONENT ? 2 : 0);
+  switch (storage) {
+    case LRVOL_STORE_F32: return launch_render_s<LRVOL_STORE_F32>(prm, degree, f, s);
+    case LRVOL_STORE_F16: return launch_render_s<LRVOL_STORE_F16>(prm, degree, f, s);
+    case LRVOL_STORE_BF16: return launch_render_s<LRVOL_STORE_BF16>(prm, degree, f, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -748,7 +904,7 @@ cudaError_t static_scratch(unsigned long long **out) {
 
 // Same kernel as launch_render, with the counters and the status word in the
 // static scratch (cleared on the stream before the launch).
-cudaError_t launch_render_static(RenderParams prm, int degree, int field, cudaStream_t s,
+cudaError_t launch_render_static(RenderParams prm, int degree, int field, int storage, cudaStream_t s,
                                  unsigned long long *counters_out) {
   unsigned long long *scratch = nullptr;
   cudaError_t e = static_scratch(&scratch);
@@ -757,7 +913,7 @@ cudaError_t launch_render_static(RenderParams prm, int degree, int field, cudaSt
   if (e != cudaSuccess) return e;
   prm.counters = scratch;
   prm.status = reinterpret_cast<uint32_t *>(scratch + kNumCounters);
-  e = launch_render(prm, degree, field, s);
+  e = launch_render(prm, degree, field, storage, s);
   if (e != cudaSuccess) return e;
   if (counters_out) {
     // samples, lookups, rays hit, then the status word widened to 64 bits

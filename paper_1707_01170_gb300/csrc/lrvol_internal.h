@@ -62,36 +62,47 @@ struct RayConsts {
   int persp;
 };
 
-// FP32 render layout of one element's Bezier block (binomials folded in),
+// Render layout of one element's Bezier block (binomials folded in),
 // arranged for packed two-lane FP32 arithmetic (fma.rn.f32x2) and 256-bit
-// loads; element strides are multiples of 8 floats (32 bytes).
+// loads.  Values sit in "slots":
 //   Scalar volumes (nc = 1): rows r = k*(p1+1) + j of (p0+1) values, stored
 //     in pairs: value i of rows 2m and 2m+1 side by side,
-//     off(r, i) = (r >> 1) * 2*(p0+1) + 2*i + (r & 1).
+//     slot(r, i) = (r >> 1) * 2*(p0+1) + 2*i + (r & 1).
 //   Vector volumes (nc = 3): with q = r*(p0+1) + i, components 0 and 1
-//     interleaved, off(q, c) = 2q + c (c = 0, 1), then component 2 at
-//     pair_floats + q, pair_floats = roundup8(2*nb).  These volumes also keep
+//     interleaved, slot(q, c) = 2q + c (c = 0, 1), then component 2 at
+//     pair_slots + q, pair_slots = roundup8(2*nb).  These volumes also keep
 //     a plain copy for component renders: component c at c*roundup8(nb) + q.
+// Storage: FP32 slots (4 bytes each); or FP16/BF16 slots (2 bytes each) after
+// a 32-byte header of FP32 offsets o[3] and scales s[3], holding
+// q' = (c' - binomial*o)/s, so a component's value is o + s * contraction(q').
+// Element strides are multiples of 32 bytes.
 __host__ __device__ inline int roundup8(int x) { return (x + 7) & ~7; }
-__host__ __device__ inline int render_pair_floats(int nb) { return roundup8(2 * nb); }
-__host__ __device__ inline int render_stride(int nc, int n0, int n1, int n2) {
+__host__ __device__ inline int roundup32(int x) { return (x + 31) & ~31; }
+__host__ __device__ inline int render_pair_slots(int nb) { return roundup8(2 * nb); }
+__host__ __device__ inline int render_slots(int nc, int n0, int n1, int n2) {
   const int nb = n0 * n1 * n2;
   if (nc == 1) return roundup8(((n1 * n2 + 1) / 2) * 2 * n0);
-  return render_pair_floats(nb) + roundup8(nb);
+  return render_pair_slots(nb) + roundup8(nb);
 }
-__host__ __device__ inline int render_off(int nc, int n0, int nb, int r, int i, int c) {
+__host__ __device__ inline int render_slot(int nc, int n0, int nb, int r, int i, int c) {
   if (nc == 1) return (r >> 1) * 2 * n0 + 2 * i + (r & 1);
   const int q = r * n0 + i;
-  return c < 2 ? 2 * q + c : render_pair_floats(nb) + q;
+  return c < 2 ? 2 * q + c : render_pair_slots(nb) + q;
+}
+constexpr int kHeaderBytes = 32;  // FP32 o[3], s[3], 2 unused (16-bit storage only)
+__host__ __device__ inline int slot_bytes(int storage) { return storage == LRVOL_STORE_F32 ? 4 : 2; }
+__host__ __device__ inline int header_bytes(int storage) { return storage == LRVOL_STORE_F32 ? 0 : kHeaderBytes; }
+__host__ __device__ inline int elem_bytes(int storage, int slots) {
+  return roundup32(header_bytes(storage) + slot_bytes(storage) * slots);
 }
 
 struct RenderParams {
   const ElemRec *elem;
   int64_t n_elem;
-  const float *bez;       // FP32 render blocks (layout above)
-  int elem_stride;        // floats per element
-  const float *bezc;      // vector volumes: plain per-component copy
-  int elemc_stride;       // floats per element of bezc
+  const unsigned char *bez;   // render blocks (layout above)
+  int elem_bytes;             // bytes per element
+  const unsigned char *bezc;  // vector volumes: plain per-component copy
+  int elemc_bytes;            // bytes per element of bezc
   int comp;               // component evaluated (FIELD_COMPONENT)
   ForestView forest;
   float *out;
@@ -124,11 +135,10 @@ struct lrvol_s {
   int32_t *d_inc_idx = nullptr;
   int64_t inc_entries = 0;
   double *d_bez64 = nullptr;
-  float *d_bez32 = nullptr;
-  float *d_bezc = nullptr;  // vector volumes: plain per-component FP32 copy
-  int elemc_stride = 0;
+  unsigned char *d_bez = nullptr;   // render blocks in `storage`
+  unsigned char *d_bezc = nullptr;  // vector volumes: plain per-component copy
+  int elem_bytes = 0, elemc_bytes = 0;
   int storage = -1;
-  int elem_stride = 0;  // floats per element of the FP32 render blocks
   lrvol::ElemRec *d_elem = nullptr;
   bool have_bezier = false;
   // forest
@@ -149,11 +159,12 @@ namespace lrvol {
 
 // kernels.cu
 cudaError_t launch_to_bezier(const lrvol_s *v, cudaStream_t s);
+cudaError_t launch_pack(const lrvol_s *v, cudaStream_t s);
 cudaError_t launch_elem_records(const lrvol_s *v, cudaStream_t s);
 cudaError_t launch_lookup(const lrvol_s *v, const float *pts, int64_t n, uint32_t *out, cudaStream_t s);
 cudaError_t launch_eval(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s);
-cudaError_t launch_render(const RenderParams &prm, int degree, int field, cudaStream_t s);
-cudaError_t launch_render_static(RenderParams prm, int degree, int field, cudaStream_t s,
+cudaError_t launch_render(const RenderParams &prm, int degree, int field, int storage, cudaStream_t s);
+cudaError_t launch_render_static(RenderParams prm, int degree, int field, int storage, cudaStream_t s,
                                  unsigned long long *counters_out);
 
 // host.cpp
