@@ -8,7 +8,14 @@ The once-per-volume change of basis and forest build are timed separately
 (`setup`).  Metric: Gsamples/s (a sample = one field evaluation that is
 composited); ms/frame beside it.
 
+At one GPU the line also carries `learned_step`: the same frame rendered with
+learned step sizes (per-element multipliers from the BF16 network, trained
+first on seeded cameras of configs 1 and 2) on FP16 blocks, timed whole
+(features, network, render) against the plain FP32 Eq. 4 frame, with both
+images' RMSE against the fine-step (1/2048) reference.
+
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                [--learned off|f32|f16|bf16]
 Under torchrun each rank renders its own frame (replicas; weak scaling) and
 rank 0 prints one JSON line.
 """
@@ -201,6 +208,69 @@ def run_reference(args):
     return 0
 
 
+def learned_leg(vol, tf, cam, step, plain, steps: int, storage: str, flush, stream):
+    """Learned step sizes with reduced-precision blocks against the plain FP32
+    Eq. 4 renderer on the same frame: both images against the fine-step
+    (1/2048) reference, and the learned frame timed whole (features, BF16
+    network, render), L2 flushed between frames like the main loop."""
+    import torch
+    from paper_1707_01170_gb300 import learned as LS
+    from paper_1707_01170_gb300 import lrvol as lv
+    from paper_1707_01170_gb300.synth import volumes as V
+    t0 = time.perf_counter()
+    gv32 = plain["gv32"]
+    v1 = V.load_config(1)
+    tf1 = V.config1_render()[0]
+    g1 = lv.Volume(v1).build_accel(BLOCKS, stream=stream).to_bezier(stream=stream)
+    model, losses, rows = LS.fit([(g1, tf1), (gv32, tf)], step)
+    torch.cuda.synchronize()
+    g1.close()
+    train_s = time.perf_counter() - t0
+    code = {"f32": lv.STORE_F32, "f16": lv.STORE_F16, "bf16": lv.STORE_BF16}[storage]
+    gq = lv.Volume(vol).build_accel(BLOCKS, stream=stream).to_bezier(storage=code, stream=stream)
+    ccam, ctf = lv.make_camera(cam), lv.make_tf(tf)
+    fine = gv32.render(ccam, ctf, V.StepParams(mode="fixed", h=1 / 2048, xi=step.xi, alpha_stop=step.alpha_stop),
+                       stream=stream)
+    feat = torch.empty((vol.n_elem, lv.MLP_IN), dtype=torch.float32, device="cuda")
+    mult = torch.empty(vol.n_elem, dtype=torch.float32, device="cuda")
+    lstep = lv.make_step(V.StepParams(mode="learned", xi=step.xi, alpha_stop=step.alpha_stop, field=step.field,
+                                      component=step.component, mult=mult))
+    out = torch.empty_like(fine)
+
+    def frame():
+        model.multipliers(gq, ccam, ctf, step, feat=feat, out=mult, stream=stream)
+        gq.render(ccam, ctf, lstep, out=out, stream=stream)
+
+    for _ in range(3):
+        frame()
+    torch.cuda.synchronize()
+    samples = gq.stats()["samples"]
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        model.multipliers(gq, ccam, ctf, step, feat=feat, out=mult, stream=stream)
+        evs[k][1].record(stream)
+        gq.render(ccam, ctf, lstep, out=out, stream=stream)
+        evs[k][2].record(stream)
+    torch.cuda.synchronize()
+    ms_mult = sum(a.elapsed_time(b) for a, b, _ in evs) / steps
+    ms_render = sum(b.elapsed_time(c) for _, b, c in evs) / steps
+    rmse = lambda a, b: float(torch.sqrt(torch.mean((a.double() - b.double()) ** 2)))
+    res = {"storage": storage, "ms_per_frame": ms_mult + ms_render, "ms_multipliers": ms_mult,
+           "ms_render": ms_render, "samples_per_frame": samples, "rmse_vs_fine": rmse(out, fine),
+           "plain_f32_ms_per_frame": plain["ms"], "plain_f32_samples_per_frame": plain["samples"],
+           "plain_f32_rmse_vs_fine": rmse(plain["img"], fine),
+           "speedup_vs_plain_f32": plain["ms"] / (ms_mult + ms_render),
+           "fine_reference": "fixed step 1/2048, FP32 blocks, same alpha_stop",
+           "gpu_launches_per_frame": 3,
+           "model": {"train_s": train_s, "rows": rows, "loss": losses[-1][1], "tau": model.cfg.tau,
+                     "margin": model.cfg.margin, "ymax": model.cfg.ymax, "steps": model.cfg.steps,
+                     "recipe": "16 seeded 320x180 cameras on each of configs 1 and 2"}}
+    gq.close()
+    return res
+
+
 def run_ours(args):
     import torch
     ws, rank, local = _dist()
@@ -259,6 +329,13 @@ def run_ours(args):
     value = total_samples / (dev_ms / 1e3) / 1e9
     ms_per_step = dev_ms / args.steps
 
+    learned = None
+    if args.learned != "off" and ws == 1 and step.field == "scalar":
+        if args.storage == "f32":
+            plain = {"gv32": gv, "ms": ms_per_step, "samples": samples_per_frame, "img": out.clone()}
+            learned = learned_leg(vol, tf, cam, step, plain, max(3, min(args.steps, 50)), args.learned, flush,
+                                  stream)
+
     # ---- end to end through the C ABI with host buffers ----
     host = torch.empty((HEIGHT, WIDTH, 4), dtype=torch.float32, pin_memory=True)
     e2e_steps = max(3, min(args.steps, 10))
@@ -299,6 +376,8 @@ def run_ours(args):
             "setup": {"create_s": t1 - t0, "build_accel_s": t2 - t1, "to_bezier_s": t3 - t2,
                       "forest_depth": [st["depth_min"], st["depth_max"], st["depth_mean"], st["depth_var"]],
                       "n_nodes": st["n_nodes"], "incidence_entries": st["incidence_entries"]}}
+    if learned is not None:
+        line["learned_step"] = learned
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(vol, tf, cam, step)
     print(json.dumps(line))
@@ -318,6 +397,8 @@ def main():
     ap.add_argument("--workload", default="cfg2", choices=sorted(WORKLOADS))
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="Bezier block storage (FP32 accumulation in every case)")
+    ap.add_argument("--learned", default="f16", choices=["off", "f32", "f16", "bf16"],
+                    help="also time learned step sizes with this block storage against plain FP32 Eq. 4")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up frames
     if args.impl == "reference":

@@ -49,7 +49,7 @@ typedef enum {
 } lrvol_status;
 
 enum { LRVOL_ORTHO = 0, LRVOL_PERSP = 1 };
-enum { LRVOL_STEP_FIXED = 0, LRVOL_STEP_HEURISTIC = 1 };
+enum { LRVOL_STEP_FIXED = 0, LRVOL_STEP_HEURISTIC = 1, LRVOL_STEP_LEARNED = 2 };
 enum { LRVOL_FIELD_SCALAR = 0, LRVOL_FIELD_MAGNITUDE = 1, LRVOL_FIELD_COMPONENT = 2 };
 enum { LRVOL_STORE_F32 = 0, LRVOL_STORE_F16 = 1, LRVOL_STORE_BF16 = 2 };
 
@@ -88,17 +88,21 @@ typedef struct {
  *   FIXED:     t_k = fmaf((float)k, h, t_in)
  *   HEURISTIC: t_{k+1} = t_k + ds(e_k), ds(e) = (float)(2^-d * min side of e),
  *              d = max(p1,p2,p3), e_k the element holding sample k (Eq. 4)
+ *   LEARNED:   t_{k+1} = t_k + ds(e_k) * mult[e_k] (one FP32 product), with
+ *              mult a caller-owned device array of one multiplier per element
+ *              (e.g. from lrvol_learned_multipliers); Eq. 4 when all are 1
  * Sample k sits at p_k = clamp(fmaf(t_k, d, o), 0, 1); its segment is
  * min(t_{k+1}, t_out) - t_k; T = (1 - alpha_src)^(segment/xi);
  * C += (1-T)(1-alpha) C_src; alpha += (1-T)(1-alpha); the ray stops at
  * t_out or once alpha >= alpha_stop.  Output is premultiplied RGBA. */
 typedef struct {
-  int32_t mode;      /* LRVOL_STEP_FIXED | LRVOL_STEP_HEURISTIC */
+  int32_t mode;      /* LRVOL_STEP_FIXED | LRVOL_STEP_HEURISTIC | LRVOL_STEP_LEARNED */
   int32_t field;     /* LRVOL_FIELD_SCALAR | _MAGNITUDE (|v| of a 3-vector) | _COMPONENT */
   int32_t component; /* for LRVOL_FIELD_COMPONENT */
   double h;          /* fixed step (FIXED only) */
   double xi;         /* reference length xi of Alg. 2 (T = (1 - alpha)^(segment / xi)) */
   double alpha_stop; /* early ray termination threshold; 1.0 = only when fully opaque */
+  const float *mult; /* LEARNED: n_elem step multipliers (device), read during the render */
 } lrvol_step;
 
 /* Diagnostics; the depth rows match the paper's tables (Sec. 4.3). */
@@ -178,6 +182,85 @@ int lrvol_render(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const
  * rejected with LRVOL_ERR_ARG.  Other errors: as lrvol_render. */
 int lrvol_render_noalloc(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
                          float *rgba_dev, uint64_t *counters_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Learned step sizes.  The paper's Eq. 4 step is multiplied per element by
+ * m = 2^clamp(y, 0, ymax), y the output of a small network run once per
+ * element and frame on 16 block-local features; LRVOL_STEP_LEARNED renders
+ * with these multipliers.  Network: 16 -> 64 -> 64 -> 64 -> 1, ReLU on the
+ * hidden layers.  FP32 master parameters (LRVOL_MLP_PARAMS floats) are laid
+ * out W1[16][64], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[64], b4
+ * (W[in][out], row major).  The paper has no learned component; Eq. 4 stays
+ * the fallback (all multipliers 1).
+ * ------------------------------------------------------------------------- */
+#define LRVOL_MLP_IN 16
+#define LRVOL_MLP_HIDDEN 64
+#define LRVOL_MLP_PARAMS 9473
+#define LRVOL_MLP_PACKED 10120 /* uint16 entries: BF16 weight fragments, then FP32 biases */
+
+/* Features of every element for a camera and transfer function, n_elem x 16
+ * floats into feat_dev (device).  With w the element's sides, [cmin, cmax] the
+ * range of the rendered field on the element (from its Bezier block: the
+ * coefficient range for a component, bounds of |v| for the magnitude) and x =
+ * (c - vmin)/(vmax - vmin) the TF coordinate:
+ *   0..2  log2(64 w_a)
+ *   3, 4  x(cmin), x(cmax);  5  x(cmax) - x(cmin)
+ *   6, 7  max and mean TF alpha over the entries floor(255 x(cmin)) ..
+ *         ceil(255 x(cmax)) (coordinates clamped to [0, 1])
+ *   8     255 * max |alpha[i+1] - alpha[i]| over those entries
+ *   9     max over R, G, B of (max - min) over those entries
+ *   10..12  unit direction from the eye to the element centre
+ *   13    log2(2048 ds), ds the element's Eq. 4 step
+ *   14    (|d_x| w_x + |d_y| w_y + |d_z| w_z) / (8 ds), d the direction above
+ *   15    log2(1 + 255 (x(cmax) - x(cmin)))
+ * Needs to_bezier.  Field and component come from `step`. */
+int lrvol_features(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                   float *feat_dev, void *stream);
+
+/* Pack FP32 master parameters (device, LRVOL_MLP_PARAMS floats) into the BF16
+ * tensor-core fragment order lrvol_mlp_infer reads (device, LRVOL_MLP_PACKED
+ * uint16, caller-owned). */
+int lrvol_mlp_pack(const float *params_dev, uint16_t *packed_dev, void *stream);
+
+/* Network forward on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate;
+ * features and hidden activations rounded to BF16 as MMA operands) for n
+ * feature rows (device, n x 16); writes out_dev[n] = 2^clamp(y, 0, ymax).
+ * ymax in [0, 8]; packed_dev 16-byte aligned (it is read in 16-byte words). */
+int lrvol_mlp_infer(const float *feat_dev, int64_t n, const uint16_t *packed_dev, float ymax, float *out_dev,
+                    void *stream);
+
+/* FP32 training step of the network on a batch (device): loss = mean over
+ * rows of (y - target)^2 / 2.  lrvol_mlp_grad writes the gradient
+ * (LRVOL_MLP_PARAMS floats) and the loss (1 float); lrvol_mlp_train_step then
+ * applies Adam (beta1 0.9, beta2 0.999, eps 1e-8, step count t >= 1) to params
+ * with moment buffers m, v (LRVOL_MLP_PARAMS floats each, zero at t = 1).
+ * scratch_dev must hold lrvol_mlp_scratch_floats(n) floats (activations, their
+ * gradients and one gradient vector).  Batch n in 1 .. 2^20. */
+int64_t lrvol_mlp_scratch_floats(int64_t n);
+int lrvol_mlp_grad(const float *x_dev, const float *target_dev, int64_t n, const float *params_dev, float *grad_dev,
+                   float *loss_dev, float *scratch_dev, void *stream);
+int lrvol_mlp_train_step(const float *x_dev, const float *target_dev, int64_t n, float *params_dev, float *m_dev,
+                         float *v_dev, int64_t t, float lr, float *loss_dev, float *scratch_dev, void *stream);
+
+/* Training labels from fine-step samples (scalar volumes).  Every ray of the
+ * camera is marched with Eq. 4 steps; a visit of element e starts at the
+ * first heuristic sample in e, t_a, and ends at the first one past it, t_b.
+ * Candidate i marches from t_a with the step s_i = cand[i]*ds(e) (FP32
+ * product), samples fmaf(k, s_i, t_a), until its first sample outside e (or
+ * the ray's exit), t_i.  Over [t_a, t_i) Alg. 2 is run from transparent with
+ * the step s_i and with the fixed fine step h_fine (reference), every sample
+ * evaluated in the element that holds it; the error of candidate i is
+ * T_front * max(|dC_r|, |dC_g|, |dC_b|, |d alpha|), T_front the reference
+ * transmittance of the ray in front of t_a (fine-step composites of the
+ * earlier visits [t_a, t_b)).  For every visited element, label_dev[e]
+ * becomes min(label_dev[e], the largest i such that candidates 1..i all have
+ * error <= tau), so the caller initialises label_dev (n_elem int32) to
+ * n_cand.  Needs to_bezier with LRVOL_STORE_F32 and build_accel.  cand_dev:
+ * 1..8 increasing multipliers on the device (read back during the call),
+ * cand[0] = 1 (always accepted).  A ray stops when its reference
+ * transmittance is <= 1 - step->alpha_stop. */
+int lrvol_labels(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step, double h_fine,
+                 double tau, const float *cand_dev, int32_t n_cand, int32_t *label_dev, void *stream);
 
 /* Element look-up through the forest (Alg. 1) for n FP32 points (n x 3,
  * device) into elem_dev (n uint32, device).  Needs build_accel. */

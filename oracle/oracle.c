@@ -17,9 +17,10 @@
  *   orc_eval         f(x) = sum_i c_i gamma_i N_i(x)  (Eq. 2), the sum running
  *                    over the B-splines whose support contains the element of
  *                    x, found by scanning all B-splines
- *   orc_render       per pixel: ray setup, sampling at a fixed step or at the
- *                    adaptive distance of Eq. 4, transfer function, and
- *                    front-to-back compositing (Alg. 2)
+ *   orc_render       per pixel: ray setup, sampling at a fixed step, at the
+ *                    adaptive distance of Eq. 4, or at Eq. 4 scaled by a given
+ *                    per-element multiplier (the learned step), transfer
+ *                    function, and front-to-back compositing (Alg. 2)
  *
  * Readings of points the paper leaves open (each listed in the design notes):
  *   - intervals are half open, [lo, hi); the upper domain face x = 1 belongs
@@ -271,10 +272,11 @@ typedef struct {
 } orc_tf;
 
 typedef struct {
-  int32_t mode;  /* 0 fixed, 1 heuristic (Eq. 4) */
+  int32_t mode;  /* 0 fixed, 1 heuristic (Eq. 4), 2 learned: Eq. 4 times a per-element multiplier */
   int32_t field; /* 0 scalar, 1 magnitude, 2 component */
   int32_t component;
   double h, xi, alpha_stop;
+  const float *mult; /* mode 2: per-element step multipliers (FP32) */
 } orc_step;
 
 typedef struct {
@@ -425,6 +427,9 @@ static void *render_worker(void *arg) {
       float tn;
       if (J->st->mode == 1) {
         tn = t + orc_heuristic_step(v, cur);
+      } else if (J->st->mode == 2) {
+        /* learned step: the Eq. 4 step scaled by the element's multiplier, one FP32 product */
+        tn = t + orc_heuristic_step(v, cur) * J->st->mult[cur];
       } else {
         tn = fmaf((float)(k + 1), (float)J->st->h, tin);
       }
@@ -488,4 +493,150 @@ int orc_ray(const orc_camera *cam, int i, int j, float *o, float *d, float *tin,
   ray_consts K;
   camera_consts(cam, &K);
   return ray_setup(&K, i, j, o, d, tin, tout);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Training labels of the learned step (the definition in lrvol.h, FP64      */
+/* compositing).  Per ray: the Eq. 4 march defines visits [t_a, t_b) and the */
+/* reference transmittance T_front in front of each.  Candidate i marches    */
+/* from t_a with cand[i] times the element's Eq. 4 step until its first      */
+/* sample outside the element, t_i; over [t_a, t_i) Alg. 2 runs from         */
+/* transparent with that step and with the fine step (reference), every      */
+/* sample evaluated in the element that holds it, so the error includes     */
+/* what the long last step skips of the next elements.  Candidate i is       */
+/* acceptable when T_front * max(|dC|, |d alpha|) <= tau; the label of the  */
+/* element is the smallest, over its visits, largest prefix of acceptable    */
+/* candidates.                                                               */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  uint32_t cur;
+  int64_t ninc;
+  int64_t *inc;
+} seg_cache;
+
+static void seg_eval_at(const orc_vol *v, seg_cache *sc, const float pf[3], double val[3]) {
+  double x[3] = {(double)pf[0], (double)pf[1], (double)pf[2]};
+  if (sc->cur == ORC_NONE || !in_element(v, sc->cur, x)) {
+    sc->cur = orc_find_element(v, x);
+    sc->ninc = orc_incidence(v, sc->cur, sc->inc);
+  }
+  eval_with(v, sc->inc, sc->ninc, x, val);
+}
+
+/* Alg. 2 from transparent over [ta, tb) with samples fmaf(k, h, ta). */
+static void seg_composite(const orc_vol *v, const orc_tf *tf, const orc_step *st, const float o[3], const float d[3],
+                          float ta, float tb, float h, seg_cache *sc, double C[3], double *A) {
+  C[0] = C[1] = C[2] = 0.0;
+  *A = 0.0;
+  for (int64_t k = 0;; ++k) {
+    float t = fmaf((float)k, h, ta);
+    if (!(t < tb)) break;
+    float pf[3];
+    for (int c = 0; c < 3; ++c) pf[c] = fminf(fmaxf(fmaf(t, d[c], o[c]), 0.0f), 1.0f);
+    double val[3];
+    seg_eval_at(v, sc, pf, val);
+    float tn = fmaf((float)(k + 1), h, ta);
+    double seg = (double)fminf(tn, tb) - (double)t;
+    double src[4];
+    tf_lookup(tf, val[0], src);
+    double T = pow(1.0 - src[3], seg / st->xi);
+    double w = (1.0 - T) * (1.0 - *A);
+    for (int c = 0; c < 3; ++c) C[c] += w * src[c];
+    *A += w;
+  }
+}
+
+typedef struct {
+  const orc_vol *v;
+  const orc_camera *cam;
+  const orc_tf *tf;
+  const orc_step *st;
+  double h_fine, tau;
+  const float *cand;
+  int n_cand;
+  int32_t *label;
+  int tid, nth;
+} label_job;
+
+static void *label_worker(void *arg) {
+  label_job *J = (label_job *)arg;
+  const orc_vol *v = J->v;
+  ray_consts K;
+  camera_consts(J->cam, &K);
+  seg_cache sc = {ORC_NONE, 0, (int64_t *)malloc(sizeof(int64_t) * v->n_basis)};
+  int64_t npix = (int64_t)J->cam->width * J->cam->height;
+  for (int64_t q = J->tid; q < npix; q += J->nth) {
+    int i = (int)(q % J->cam->width), j = (int)(q / J->cam->width);
+    float o[3], d[3], tin, tout;
+    if (!ray_setup(&K, i, j, o, d, &tin, &tout)) continue;
+    double Tfront = 1.0;
+    float t = tin;
+    while (t < tout && Tfront > 1.0 - J->st->alpha_stop) {
+      float pf[3];
+      double x[3];
+      for (int c = 0; c < 3; ++c) {
+        pf[c] = fminf(fmaxf(fmaf(t, d[c], o[c]), 0.0f), 1.0f);
+        x[c] = (double)pf[c];
+      }
+      uint32_t e = orc_find_element(v, x);
+      float ds = orc_heuristic_step(v, e);
+      float tb = t;
+      for (;;) {
+        tb = tb + ds;
+        if (!(tb < tout)) break;
+        for (int c = 0; c < 3; ++c) x[c] = (double)fminf(fmaxf(fmaf(tb, d[c], o[c]), 0.0f), 1.0f);
+        if (!in_element(v, e, x)) break;
+      }
+      tb = fminf(tb, tout);
+      double R[3], RA, Cc[3], CA, F[3], FA;
+      seg_composite(v, J->tf, J->st, o, d, t, tb, (float)J->h_fine, &sc, R, &RA);
+      int best = 0;
+      for (int c = 1; c < J->n_cand; ++c) {
+        /* the candidate's first sample outside e (or the ray's exit) */
+        float s = ds * J->cand[c], tc = t;
+        for (int64_t k = 1;; ++k) {
+          tc = fmaf((float)k, s, t);
+          if (!(tc < tout)) break;
+          for (int ch = 0; ch < 3; ++ch) x[ch] = (double)fminf(fmaxf(fmaf(tc, d[ch], o[ch]), 0.0f), 1.0f);
+          if (!in_element(v, e, x)) break;
+        }
+        tc = fminf(tc, tout);
+        seg_composite(v, J->tf, J->st, o, d, t, tc, (float)J->h_fine, &sc, F, &FA);
+        seg_composite(v, J->tf, J->st, o, d, t, tc, s, &sc, Cc, &CA);
+        double err = fabs(CA - FA);
+        for (int ch = 0; ch < 3; ++ch)
+          if (fabs(Cc[ch] - F[ch]) > err) err = fabs(Cc[ch] - F[ch]);
+        if (!(Tfront * err <= J->tau)) break;
+        best = c;
+      }
+      if (best < J->label[e]) J->label[e] = best;
+      Tfront *= 1.0 - RA;
+      t = tb;
+    }
+  }
+  free(sc.inc);
+  return NULL;
+}
+
+/* label: n_elem int32, in/out (min over visits); thread-private copies merged by min. */
+void orc_labels(const orc_vol *v, const orc_camera *cam, const orc_tf *tf, const orc_step *st, double h_fine,
+                double tau, const float *cand, int n_cand, int32_t *label, int nth) {
+  if (nth < 1) nth = 1;
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nth);
+  label_job *jobs = (label_job *)malloc(sizeof(label_job) * nth);
+  for (int t = 0; t < nth; ++t) {
+    int32_t *own = (int32_t *)malloc(sizeof(int32_t) * v->n_elem);
+    memcpy(own, label, sizeof(int32_t) * v->n_elem);
+    label_job J = {v, cam, tf, st, h_fine, tau, cand, n_cand, own, t, nth};
+    jobs[t] = J;
+    pthread_create(&th[t], NULL, label_worker, &jobs[t]);
+  }
+  for (int t = 0; t < nth; ++t) {
+    pthread_join(th[t], NULL);
+    for (int64_t e = 0; e < v->n_elem; ++e)
+      if (jobs[t].label[e] < label[e]) label[e] = jobs[t].label[e];
+    free(jobs[t].label);
+  }
+  free(th);
+  free(jobs);
 }

@@ -71,7 +71,8 @@ class _TF(ctypes.Structure):
 
 class _Step(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("field", ctypes.c_int32), ("component", ctypes.c_int32),
-                ("h", ctypes.c_double), ("xi", ctypes.c_double), ("alpha_stop", ctypes.c_double)]
+                ("h", ctypes.c_double), ("xi", ctypes.c_double), ("alpha_stop", ctypes.c_double),
+                ("mult", ctypes.c_void_p)]
 
 
 class _Stats(ctypes.Structure):
@@ -103,6 +104,8 @@ def _load():
         L.orc_heuristic_step.argtypes = [vp, ctypes.c_uint32]
         L.orc_render.argtypes = [vp, ctypes.POINTER(_Cam), ctypes.POINTER(_TF), ctypes.POINTER(_Step),
                                  vp, i64, vp, i32, ctypes.POINTER(_Stats)]
+        L.orc_labels.argtypes = [vp, ctypes.POINTER(_Cam), ctypes.POINTER(_TF), ctypes.POINTER(_Step),
+                                 ctypes.c_double, ctypes.c_double, vp, i32, vp, i32]
         L.orc_ray.restype = i32
         L.orc_ray.argtypes = [ctypes.POINTER(_Cam), i32, i32, vp, vp, vp, vp]
         _lib = L
@@ -248,7 +251,13 @@ class Oracle:
         t.table = table.ctypes.data
         t.vmin, t.vmax = float(tf.vmin), float(tf.vmax)
         s = _Step()
-        s.mode = 1 if step.mode == "heuristic" else 0
+        s.mode = {"fixed": 0, "heuristic": 1, "learned": 2}[step.mode]
+        mult = None
+        if step.mode == "learned":
+            mult = np.ascontiguousarray(step.mult, dtype=np.float32).reshape(-1)
+            if mult.shape[0] != self.n_elem:
+                raise ValueError("learned steps need one multiplier per element")
+            s.mult = mult.ctypes.data
         s.field = {"scalar": 0, "magnitude": 1, "component": 2}[step.field]
         s.component = int(step.component)
         s.h, s.xi, s.alpha_stop = float(step.h), float(step.xi), float(step.alpha_stop)
@@ -266,3 +275,19 @@ class Oracle:
             _load().orc_render(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), pix.ctypes.data,
                                len(pix), out.ctypes.data, _threads(threads or self.threads), ctypes.byref(st))
         return out, {"samples": st.samples, "lookups": st.lookups, "rays_hit": st.rays_hit}
+
+    # --- learned-step training labels (definition of lrvol_labels) ------------
+    def labels(self, cam, tf, step, h_fine: float, tau: float, cand, threads: int | None = None):
+        table = np.ascontiguousarray(tf.table, dtype=np.float64).reshape(256, 4)
+        t = _TF()
+        t.table = table.ctypes.data
+        t.vmin, t.vmax = float(tf.vmin), float(tf.vmax)
+        s = _Step()
+        s.mode, s.field, s.component = 1, 0, 0
+        s.h, s.xi, s.alpha_stop = float(step.h), float(step.xi), float(step.alpha_stop)
+        c = _cam(cam)
+        cand = np.ascontiguousarray(cand, dtype=np.float32)
+        lab = np.full(self.n_elem, len(cand), dtype=np.int32)
+        _load().orc_labels(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), float(h_fine), float(tau),
+                           cand.ctypes.data, len(cand), lab.ctypes.data, _threads(threads or self.threads))
+        return lab

@@ -445,7 +445,8 @@ int lrvol_to_bezier(lrvol_t v, int32_t storage, void *stream) {
       (rc = dev_alloc(v, &v->d_bez64, (size_t)v->n_elem * v->nc * nb, "alloc bezier64")) ||
       (rc = dev_alloc(v, &v->d_bez, (size_t)v->n_elem * v->elem_bytes, "alloc render blocks")) ||
       (v->nc == 3 && (rc = dev_alloc(v, &v->d_bezc, (size_t)v->n_elem * v->elemc_bytes, "alloc render copy"))) ||
-      (rc = dev_alloc(v, &v->d_elem, (size_t)v->n_elem, "alloc element records")))
+      (rc = dev_alloc(v, &v->d_elem, (size_t)v->n_elem, "alloc element records")) ||
+      (rc = dev_alloc(v, &v->d_range, (size_t)v->n_elem * v->nc, "alloc coefficient ranges")))
     return rc;
   CU(cudaMemcpyAsync(v->d_inc_ptr, ptr.data(), sizeof(int64_t) * ptr.size(), cudaMemcpyHostToDevice, st),
      "upload incidence ptr");
@@ -472,7 +473,9 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   int r0 = cam->row_begin, r1 = cam->row_end;
   if (r0 == 0 && r1 == 0) r1 = cam->height;
   if (r0 < 0 || r1 > cam->height || r0 > r1) return fail(LRVOL_ERR_ARG, "bad row range");
-  if (step->mode != LRVOL_STEP_FIXED && step->mode != LRVOL_STEP_HEURISTIC) return fail(LRVOL_ERR_ARG, "bad step mode");
+  if (step->mode != LRVOL_STEP_FIXED && step->mode != LRVOL_STEP_HEURISTIC && step->mode != LRVOL_STEP_LEARNED)
+    return fail(LRVOL_ERR_ARG, "bad step mode");
+  if (step->mode == LRVOL_STEP_LEARNED && !step->mult) return fail(LRVOL_ERR_ARG, "learned steps need multipliers");
   if (step->mode == LRVOL_STEP_FIXED && !(step->h > 0)) return fail(LRVOL_ERR_ARG, "fixed step must be > 0");
   if (!(step->xi > 0) || !(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "xi and vmax - vmin must be > 0");
   int field = step->field;
@@ -501,6 +504,7 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   prm.row_end = r1;
   camera_consts(cam, &prm.ray);
   prm.mode = step->mode;
+  prm.mult = step->mult;
   prm.h = (float)step->h;
   prm.inv_xi = (float)(1.0 / step->xi);
   prm.alpha_stop = (float)step->alpha_stop;
@@ -527,7 +531,9 @@ int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf,
   int r0 = cam->row_begin, r1 = cam->row_end;
   if (r0 == 0 && r1 == 0) r1 = cam->height;
   if (r0 < 0 || r1 > cam->height || r0 > r1) return fail(LRVOL_ERR_ARG, "bad row range");
-  if (step->mode != LRVOL_STEP_FIXED && step->mode != LRVOL_STEP_HEURISTIC) return fail(LRVOL_ERR_ARG, "bad step mode");
+  if (step->mode != LRVOL_STEP_FIXED && step->mode != LRVOL_STEP_HEURISTIC && step->mode != LRVOL_STEP_LEARNED)
+    return fail(LRVOL_ERR_ARG, "bad step mode");
+  if (step->mode == LRVOL_STEP_LEARNED && !step->mult) return fail(LRVOL_ERR_ARG, "learned steps need multipliers");
   if (step->mode == LRVOL_STEP_FIXED && !(step->h > 0)) return fail(LRVOL_ERR_ARG, "fixed step must be > 0");
   if (!(step->xi > 0) || !(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "xi and vmax - vmin must be > 0");
   const int field = step->field;
@@ -555,6 +561,7 @@ int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf,
   prm.row_end = r1;
   camera_consts(cam, &prm.ray);
   prm.mode = step->mode;
+  prm.mult = step->mult;
   prm.h = (float)step->h;
   prm.inv_xi = (float)(1.0 / step->xi);
   prm.alpha_stop = (float)step->alpha_stop;
@@ -564,6 +571,113 @@ int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf,
   cudaError_t e = launch_render_static(prm, v->p[0], field, v->storage, (cudaStream_t)stream,
                                        reinterpret_cast<unsigned long long *>(counters_dev));
   if (e != cudaSuccess) return cuda_fail(e, "render_noalloc");
+  return LRVOL_OK;
+}
+
+// ---- learned step sizes ----------------------------------------------------
+
+int lrvol_features(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step, float *feat,
+                   void *stream) {
+  if (!v || !cam || !tf || !step || !feat) return fail(LRVOL_ERR_ARG, "null pointer");
+  if (!v->have_bezier) return fail(LRVOL_ERR_STATE, "features need to_bezier");
+  if (!(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "vmax - vmin must be > 0");
+  const int field = step->field;
+  if (field < 0 || field > 2 || (field == LRVOL_FIELD_SCALAR && v->nc != 1) ||
+      (field == LRVOL_FIELD_MAGNITUDE && v->nc != 3) ||
+      (field == LRVOL_FIELD_COMPONENT && (step->component < 0 || step->component >= v->nc)))
+    return fail(LRVOL_ERR_ARG, "bad field/component for this volume");
+  FeatureParams fp;
+  std::memset(&fp, 0, sizeof(fp));
+  fp.box = v->d_box;
+  fp.elem = v->d_elem;
+  fp.range = v->d_range;
+  fp.n_elem = v->n_elem;
+  fp.nc = v->nc;
+  fp.field = field;
+  fp.comp = step->component;
+  for (int a = 0; a < 3; ++a) fp.eye[a] = (float)cam->eye[a];
+  fp.tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
+  fp.tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
+  for (int q = 0; q < 256; ++q) fp.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
+  CU(launch_features(fp, feat, (cudaStream_t)stream), "features kernel");
+  return LRVOL_OK;
+}
+
+int lrvol_mlp_pack(const float *params, uint16_t *packed, void *stream) {
+  if (!params || !packed) return fail(LRVOL_ERR_ARG, "null pointer");
+  CU(launch_mlp_pack(params, packed, (cudaStream_t)stream), "mlp pack kernel");
+  return LRVOL_OK;
+}
+
+int lrvol_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out, void *stream) {
+  if (n < 0 || (n > 0 && (!x || !packed || !out))) return fail(LRVOL_ERR_ARG, "bad arguments");
+  if (!(ymax >= 0.f && ymax <= 8.f)) return fail(LRVOL_ERR_ARG, "ymax must be in [0, 8]");
+  if (n == 0) return LRVOL_OK;
+  if (reinterpret_cast<uintptr_t>(packed) & 15) return fail(LRVOL_ERR_ARG, "packed weights must be 16-byte aligned");
+  CU(launch_mlp_infer(x, n, packed, ymax, out, (cudaStream_t)stream), "mlp infer kernel");
+  return LRVOL_OK;
+}
+
+// activations and their gradients (n x (6*64 + 2)), then one gradient vector
+int64_t lrvol_mlp_scratch_floats(int64_t n) { return n < 0 ? 0 : n * (6 * (int64_t)kHid + 2) + kParams; }
+
+int lrvol_mlp_grad(const float *x, const float *target, int64_t n, const float *params, float *grad, float *loss,
+                   float *scratch, void *stream) {
+  if (!x || !target || !params || !grad || !scratch) return fail(LRVOL_ERR_ARG, "null pointer");
+  if (n < 1 || n > ((int64_t)1 << 20)) return fail(LRVOL_ERR_ARG, "batch must be 1 .. 2^20 rows");
+  CU(launch_mlp_grad(x, target, n, params, grad, loss, scratch, (cudaStream_t)stream), "mlp grad kernels");
+  return LRVOL_OK;
+}
+
+int lrvol_mlp_train_step(const float *x, const float *target, int64_t n, float *params, float *m, float *vv,
+                         int64_t t, float lr, float *loss, float *scratch, void *stream) {
+  if (!m || !vv || t < 1 || !(lr > 0.f)) return fail(LRVOL_ERR_ARG, "bad optimiser arguments");
+  // the gradient lands in the last kParams floats of the scratch
+  float *grad = scratch + lrvol_mlp_scratch_floats(n) - kParams;
+  int rc = lrvol_mlp_grad(x, target, n, params, grad, loss, scratch, stream);
+  if (rc) return rc;
+  CU(launch_adam(params, grad, m, vv, t, lr, (cudaStream_t)stream), "adam kernel");
+  return LRVOL_OK;
+}
+
+int lrvol_labels(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step, double h_fine,
+                 double tau, const float *cand, int32_t n_cand, int32_t *label, void *stream) {
+  if (!v || !cam || !tf || !step || !cand || !label) return fail(LRVOL_ERR_ARG, "null pointer");
+  if (!v->have_bezier || !v->have_accel) return fail(LRVOL_ERR_STATE, "labels need to_bezier and build_accel");
+  if (v->nc != 1 || v->storage != LRVOL_STORE_F32) return fail(LRVOL_ERR_UNSUPPORTED, "labels need a scalar FP32 volume");
+  if (v->p[0] != v->p[1] || v->p[0] != v->p[2] || v->p[0] > 3)
+    return fail(LRVOL_ERR_UNSUPPORTED, "labels need equal degrees 1..3");
+  if (n_cand < 1 || n_cand > 8 || !(h_fine > 0) || !(tau >= 0)) return fail(LRVOL_ERR_ARG, "bad label arguments");
+  if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+    return fail(LRVOL_ERR_ARG, "bad image size");
+  if (!(step->xi > 0) || !(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "xi and vmax - vmin must be > 0");
+  float hc[8];
+  CU(cudaMemcpy(hc, cand, sizeof(float) * n_cand, cudaMemcpyDeviceToHost), "read candidates");
+  if (hc[0] != 1.f) return fail(LRVOL_ERR_ARG, "cand[0] must be 1");
+  for (int q = 1; q < n_cand; ++q)
+    if (!(hc[q] > hc[q - 1])) return fail(LRVOL_ERR_ARG, "candidates must increase");
+  RenderParams prm;
+  std::memset(&prm, 0, sizeof(prm));
+  prm.elem = v->d_elem;
+  prm.n_elem = v->n_elem;
+  prm.bez = v->d_bez;
+  prm.elem_bytes = v->elem_bytes;
+  prm.forest = forest_view(v);
+  prm.width = cam->width;
+  prm.height = cam->height;
+  prm.row_begin = 0;
+  prm.row_end = cam->height;
+  camera_consts(cam, &prm.ray);
+  prm.mode = LRVOL_STEP_HEURISTIC;
+  prm.inv_xi = (float)(1.0 / step->xi);
+  prm.alpha_stop = (float)step->alpha_stop;
+  prm.tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
+  prm.tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
+  prm.counters = v->d_counters;
+  prm.status = v->d_status;
+  for (int q = 0; q < 256; ++q) prm.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
+  CU(launch_labels(prm, v->p[0], (float)h_fine, (float)tau, cand, n_cand, label, (cudaStream_t)stream),
+     "labels kernel");
   return LRVOL_OK;
 }
 
@@ -623,7 +737,8 @@ void lrvol_destroy(lrvol_t v) {
   if (!v) return;
   cudaDeviceSynchronize();
   void *ptrs[] = {v->d_box,   v->d_knots, v->d_coef,  v->d_weight, v->d_inc_ptr,  v->d_inc_idx, v->d_bez64,
-                  v->d_bez,   v->d_bezc,  v->d_elem,  v->d_head,  v->d_nodes, v->d_counters, v->d_status};
+                  v->d_bez,   v->d_bezc,  v->d_elem,  v->d_head,  v->d_nodes, v->d_counters, v->d_status,
+                  v->d_range};
   for (void *p : ptrs)
     if (p) cudaFree(p);
   delete v;

@@ -12,6 +12,7 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 #include <mutex>
 
@@ -130,28 +131,33 @@ __device__ __forceinline__ void store_slot(unsigned char *base, int storage, int
 
 __global__ void __launch_bounds__(32 * kBezWarps) k_pack(const double *__restrict__ b64, int p0, int p1, int p2, int nc,
                                                         int64_t n_elem, int storage, unsigned char *__restrict__ out,
-                                                        int ebytes, unsigned char *__restrict__ outc, int ecbytes) {
+                                                        int ebytes, unsigned char *__restrict__ outc, int ecbytes,
+                                                        float2 *__restrict__ range) {
   const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t e = (int64_t)blockIdx.x * kBezWarps + w;
   if (e >= n_elem) return;
   const int n0 = p0 + 1, n1 = p1 + 1, nb = n0 * n1 * (p2 + 1);
   const double *be = b64 + e * nc * nb;
   double o[3] = {0.0, 0.0, 0.0}, sc[3] = {1.0, 1.0, 1.0};
-  if (storage != LRVOL_STORE_F32) {
-    for (int c = 0; c < nc; ++c) {
-      double mn = __longlong_as_double(0x7ff0000000000000ll), mx = -mn;
-      for (int q = lane; q < nb; q += 32) {
-        mn = fmin(mn, be[c * nb + q]);
-        mx = fmax(mx, be[c * nb + q]);
-      }
-      for (int off = 16; off > 0; off >>= 1) {
-        mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, off));
-        mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
-      }
+  for (int c = 0; c < nc; ++c) {
+    // coefficient range (the block's convex hull bounds the field on the element)
+    double mn = __longlong_as_double(0x7ff0000000000000ll), mx = -mn;
+    for (int q = lane; q < nb; q += 32) {
+      mn = fmin(mn, be[c * nb + q]);
+      mx = fmax(mx, be[c * nb + q]);
+    }
+    for (int off = 16; off > 0; off >>= 1) {
+      mn = fmin(mn, __shfl_xor_sync(0xffffffffu, mn, off));
+      mx = fmax(mx, __shfl_xor_sync(0xffffffffu, mx, off));
+    }
+    if (lane == 0) range[e * nc + c] = make_float2(__double2float_rd(mn), __double2float_ru(mx));
+    if (storage != LRVOL_STORE_F32) {
       o[c] = 0.5 * (mx + mn);
       sc[c] = 0.5 * (mx - mn);
       if (!(sc[c] > 0.0)) sc[c] = 1.0;
     }
+  }
+  if (storage != LRVOL_STORE_F32) {
     if (lane < 8) {
       const float hv = lane < 3 ? (float)o[lane] : (lane < 6 ? (float)sc[lane - 3] : 0.f);
       reinterpret_cast<float *>(out + e * ebytes)[lane] = hv;
@@ -721,6 +727,7 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
       ++nhit;
       const float tr_stop = 1.f - prm.alpha_stop;
       float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
+      float dsv = 0.f;       // step inside the current element (Eq. 4, or Eq. 4 x learned multiplier)
       Block<P, FIELD, STORE> blk;
       float t = ray.tin;
       int k = 0;
@@ -746,12 +753,13 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
           }
           ++nlook;
           load_record(prm.elem + cur, ra, rb, rc, rd);
+          dsv = prm.mode == LRVOL_STEP_LEARNED ? __fmul_rn(ra.w, __ldg(prm.mult + cur)) : ra.w;
           if constexpr (FIELD == 2)
             blk.load(prm.bezc + (int64_t)cur * prm.elemc_bytes, prm.comp);
           else
             blk.load(prm.bez + (int64_t)cur * prm.elem_bytes, 0);
         }
-        float tn = prm.mode == LRVOL_STEP_HEURISTIC ? __fadd_rn(t, ra.w) : __fmaf_rn((float)(k + 1), prm.h, ray.tin);
+        float tn = prm.mode == LRVOL_STEP_FIXED ? __fmaf_rn((float)(k + 1), prm.h, ray.tin) : __fadd_rn(t, dsv);
         if (!(tn > t)) tn = nextafterf(t, inf);
         const float seg = __fsub_rn(fminf(tn, ray.tout), t);
         // evaluate sample k ...
@@ -805,7 +813,8 @@ cudaError_t launch_to_bezier(const lrvol_s *v, cudaStream_t s) {
 cudaError_t launch_pack(const lrvol_s *v, cudaStream_t s) {
   const int64_t blocks = (v->n_elem + kBezWarps - 1) / kBezWarps;
   k_pack<<<(unsigned)blocks, 32 * kBezWarps, 0, s>>>(v->d_bez64, v->p[0], v->p[1], v->p[2], v->nc, v->n_elem,
-                                                    v->storage, v->d_bez, v->elem_bytes, v->d_bezc, v->elemc_bytes);
+                                                    v->storage, v->d_bez, v->elem_bytes, v->d_bezc, v->elemc_bytes,
+                                                    v->d_range);
   return cudaGetLastError();
 }
 
@@ -860,6 +869,452 @@ cudaError_t launch_render(const RenderParams &prm, int degree, int field, int st
     case LRVOL_STORE_BF16: return launch_render_s<LRVOL_STORE_BF16>(prm, degree, f, s);
     default: return cudaErrorInvalidValue;
   }
+}
+
+// ----------------------------------------------------------------------------
+// Learned step sizes: features, BF16 tensor-core inference, FP32 training,
+// fine-step labels.  The network is 16 -> 64 -> 64 -> 64 -> 1 (ReLU).
+// ----------------------------------------------------------------------------
+namespace {
+
+// Range of the rendered field on an element: a component's coefficient range
+// (convex hull of the Bezier block), or bounds of |v| from the three ranges.
+__device__ __forceinline__ void field_range(const FeatureParams &fp, int64_t e, float &lo, float &hi) {
+  if (fp.field == LRVOL_FIELD_MAGNITUDE) {
+    float s_lo = 0.f, s_hi = 0.f;
+    for (int c = 0; c < 3; ++c) {
+      const float2 r = fp.range[e * fp.nc + c];
+      const float m = fmaxf(fabsf(r.x), fabsf(r.y));
+      const float d = r.x > 0.f ? r.x : (r.y < 0.f ? -r.y : 0.f);   // distance of 0 to [r.x, r.y]
+      s_hi = fmaf(m, m, s_hi);
+      s_lo = fmaf(d, d, s_lo);
+    }
+    lo = sqrtf(s_lo);
+    hi = sqrtf(s_hi);
+  } else {
+    const float2 r = fp.range[e * fp.nc + (fp.field == LRVOL_FIELD_COMPONENT ? fp.comp : 0)];
+    lo = r.x;
+    hi = r.y;
+  }
+}
+
+__global__ void k_features(const __grid_constant__ FeatureParams fp, float *__restrict__ out) {
+  const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= fp.n_elem) return;
+  const double *b = fp.box + 6 * e;
+  float w[3], ctr[3];
+  for (int a = 0; a < 3; ++a) {
+    w[a] = (float)(b[3 + a] - b[a]);
+    ctr[a] = (float)(0.5 * (b[a] + b[3 + a]));
+  }
+  const float ds = __ldg(&fp.elem[e].a.w);
+  float lo, hi;
+  field_range(fp, e, lo, hi);
+  const float xlo = fmaf(lo, fp.tf_scale, fp.tf_bias) * (1.f / 255.f);
+  const float xhi = fmaf(hi, fp.tf_scale, fp.tf_bias) * (1.f / 255.f);
+  const int i0 = (int)floorf(255.f * fminf(fmaxf(xlo, 0.f), 1.f));
+  const int i1 = min(255, (int)ceilf(255.f * fminf(fmaxf(xhi, 0.f), 1.f)));
+  float amax = 0.f, asum = 0.f, slope = 0.f;
+  float cmin[3] = {1e30f, 1e30f, 1e30f}, cmax[3] = {-1e30f, -1e30f, -1e30f};
+  for (int i = i0; i <= i1; ++i) {
+    const float4 t = fp.tf[i];
+    amax = fmaxf(amax, t.w);
+    asum += t.w;
+    if (i < i1) slope = fmaxf(slope, fabsf(fp.tf[i + 1].w - t.w));
+    cmin[0] = fminf(cmin[0], t.x); cmax[0] = fmaxf(cmax[0], t.x);
+    cmin[1] = fminf(cmin[1], t.y); cmax[1] = fmaxf(cmax[1], t.y);
+    cmin[2] = fminf(cmin[2], t.z); cmax[2] = fmaxf(cmax[2], t.z);
+  }
+  float dir[3];
+  float nn = 0.f;
+  for (int a = 0; a < 3; ++a) {
+    dir[a] = ctr[a] - fp.eye[a];
+    nn = fmaf(dir[a], dir[a], nn);
+  }
+  nn = rsqrtf(fmaxf(nn, 1e-30f));
+  float proj = 0.f;
+  for (int a = 0; a < 3; ++a) {
+    dir[a] *= nn;
+    proj = fmaf(fabsf(dir[a]), w[a], proj);
+  }
+  float *o = out + e * kIn;
+  o[0] = log2f(64.f * w[0]);
+  o[1] = log2f(64.f * w[1]);
+  o[2] = log2f(64.f * w[2]);
+  o[3] = xlo;
+  o[4] = xhi;
+  o[5] = xhi - xlo;
+  o[6] = amax;
+  o[7] = asum / (float)(i1 - i0 + 1);
+  o[8] = 255.f * slope;
+  o[9] = fmaxf(cmax[0] - cmin[0], fmaxf(cmax[1] - cmin[1], cmax[2] - cmin[2]));
+  o[10] = dir[0];
+  o[11] = dir[1];
+  o[12] = dir[2];
+  o[13] = log2f(2048.f * ds);
+  o[14] = proj / (8.f * ds);
+  o[15] = log2f(1.f + 255.f * (xhi - xlo));
+}
+
+// ---- BF16 weight fragments for mma.sync.m16n8k16 (B operand, "col") ----
+// Entry (ks, nt, lane, j): k = 16 ks + 2 t + (j & 1) + 8 (j >> 1), n = 8 nt + g,
+// with g = lane / 4, t = lane % 4.
+__global__ void k_mlp_pack(const float *__restrict__ p, uint16_t *__restrict__ out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= kPacked) return;
+  float w = 0.f;
+  bool weight = false;
+  int K = 0, N = 0, base = 0, woff = 0;
+  if (q < kPkL2) { K = kIn; N = kHid; base = kPkL1; woff = kOffW1; weight = true; }
+  else if (q < kPkL3) { K = kHid; N = kHid; base = kPkL2; woff = kOffW2; weight = true; }
+  else if (q < kPkL4) { K = kHid; N = kHid; base = kPkL3; woff = kOffW3; weight = true; }
+  else if (q < kPkBias) { K = kHid; N = 8; base = kPkL4; woff = kOffW4; weight = true; }
+  if (weight) {
+    const int r = q - base;
+    const int j = r & 3, lane = (r >> 2) & 31, tile = r >> 7;
+    const int ntn = N / 8, nt = tile % ntn, ks = tile / ntn;
+    const int g = lane >> 2, t = lane & 3;
+    const int k = 16 * ks + 2 * t + (j & 1) + 8 * (j >> 1), n = 8 * nt + g;
+    if (N == 8) w = n == 0 ? p[woff + k] : 0.f;
+    else w = p[woff + k * N + n];
+    out[q] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+    return;
+  }
+  // FP32 biases b1, b2, b3, b4 as pairs of uint16 (low half first)
+  const int r = q - kPkBias, f = r >> 1;
+  float bv = 0.f;
+  if (f < kHid) bv = p[kOffB1 + f];
+  else if (f < 2 * kHid) bv = p[kOffB2 + f - kHid];
+  else if (f < 3 * kHid) bv = p[kOffB3 + f - 2 * kHid];
+  else if (f == 3 * kHid) bv = p[kOffB4];
+  const unsigned bits = __float_as_uint(bv);
+  out[q] = (r & 1) ? (uint16_t)(bits >> 16) : (uint16_t)(bits & 0xffffu);
+}
+
+__device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
+  return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
+         ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
+}
+
+__device__ __forceinline__ void mma_bf16(float *d, const unsigned *a, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One warp evaluates 16 rows per tile; the C fragments of one layer are the A
+// fragments of the next (k-slice ks = n-tiles 2ks, 2ks+1), so activations stay
+// in registers.  Weights are staged in shared memory per CTA.
+__global__ void __launch_bounds__(128) k_mlp_infer(const float *__restrict__ x, int64_t n,
+                                                   const uint16_t *__restrict__ packed, float ymax,
+                                                   float *__restrict__ out) {
+  __shared__ __align__(16) uint16_t sw[kPacked];
+  for (int q = threadIdx.x; q < kPacked / 8; q += blockDim.x)
+    reinterpret_cast<uint4 *>(sw)[q] = reinterpret_cast<const uint4 *>(packed)[q];
+  __syncthreads();
+  const float *bias = reinterpret_cast<const float *>(sw + kPkBias);
+  const unsigned *wfrag = reinterpret_cast<const unsigned *>(sw);   // 2 registers per lane per fragment
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int64_t tiles = (n + 15) / 16;
+  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t tile = warp_id; tile < tiles; tile += n_warps) {
+    const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
+    auto xin = [&](int64_t r, int c) { return r < n ? __ldg(x + r * kIn + c) : 0.f; };
+    unsigned A[4][4];
+    A[0][0] = pack_bf16x2(xin(r0, 2 * t), xin(r0, 2 * t + 1));
+    A[0][1] = pack_bf16x2(xin(r1, 2 * t), xin(r1, 2 * t + 1));
+    A[0][2] = pack_bf16x2(xin(r0, 2 * t + 8), xin(r0, 2 * t + 9));
+    A[0][3] = pack_bf16x2(xin(r1, 2 * t + 8), xin(r1, 2 * t + 9));
+    float C[8][4];
+    // three hidden layers
+    for (int layer = 0; layer < 3; ++layer) {
+      const int ksteps = layer == 0 ? 1 : 4;
+      const int pk = layer == 0 ? kPkL1 : (layer == 1 ? kPkL2 : kPkL3);
+      const float *bl = bias + layer * kHid;
+#pragma unroll
+      for (int nt = 0; nt < 8; ++nt) {
+        const float b0 = bl[8 * nt + 2 * t], b1 = bl[8 * nt + 2 * t + 1];
+        C[nt][0] = b0; C[nt][1] = b1; C[nt][2] = b0; C[nt][3] = b1;
+      }
+      for (int ks = 0; ks < ksteps; ++ks)
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) {
+          const unsigned *bf = wfrag + (pk >> 1) + ((ks * 8 + nt) * 32 + lane) * 2;
+          mma_bf16(C[nt], A[ks], bf[0], bf[1]);
+        }
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        A[ks][0] = pack_bf16x2(fmaxf(C[2 * ks][0], 0.f), fmaxf(C[2 * ks][1], 0.f));
+        A[ks][1] = pack_bf16x2(fmaxf(C[2 * ks][2], 0.f), fmaxf(C[2 * ks][3], 0.f));
+        A[ks][2] = pack_bf16x2(fmaxf(C[2 * ks + 1][0], 0.f), fmaxf(C[2 * ks + 1][1], 0.f));
+        A[ks][3] = pack_bf16x2(fmaxf(C[2 * ks + 1][2], 0.f), fmaxf(C[2 * ks + 1][3], 0.f));
+      }
+    }
+    // output layer (n padded to 8; column 0 is the output)
+    float D[4] = {t == 0 ? bias[3 * kHid] : 0.f, 0.f, t == 0 ? bias[3 * kHid] : 0.f, 0.f};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+      const unsigned *bf = wfrag + (kPkL4 >> 1) + (ks * 32 + lane) * 2;
+      mma_bf16(D, A[ks], bf[0], bf[1]);
+    }
+    if (t == 0) {
+      if (r0 < n) out[r0] = exp2f(fminf(fmaxf(D[0], 0.f), ymax));
+      if (r1 < n) out[r1] = exp2f(fminf(fmaxf(D[2], 0.f), ymax));
+    }
+  }
+}
+
+// ---- FP32 training (plain CUDA-core kernels; batch up to 2^20 rows) ----
+// out[b][j] = act(sum_k in[b][k] W[k][j] + bias[j])
+__global__ void k_dense_fwd(const float *__restrict__ in, int K, const float *__restrict__ W,
+                            const float *__restrict__ bias, int N, int64_t n, bool relu, float *__restrict__ out) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * N) return;
+  const int64_t b = q / N;
+  const int j = (int)(q % N);
+  float acc = bias[j];
+  for (int k = 0; k < K; ++k) acc = fmaf(in[b * K + k], W[k * N + j], acc);
+  out[q] = relu ? fmaxf(acc, 0.f) : acc;
+}
+
+// dy[b] = (y[b] - t[b]) / n and the loss (one CTA, fixed order)
+__global__ void k_loss(const float *__restrict__ y, const float *__restrict__ tgt, int64_t n, float *__restrict__ dy,
+                       float *__restrict__ loss) {
+  __shared__ double red[256];
+  double acc = 0.0;
+  for (int64_t b = threadIdx.x; b < n; b += blockDim.x) {
+    const float r = y[b] - tgt[b];
+    dy[b] = r / (float)n;
+    acc += 0.5 * (double)r * (double)r;
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int s2 = blockDim.x / 2; s2 > 0; s2 >>= 1) {
+    if (threadIdx.x < s2) red[threadIdx.x] += red[threadIdx.x + s2];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0 && loss) *loss = (float)(red[0] / (double)n);
+}
+
+// gW[k][j] = sum_b in[b][k] d[b][j];  gb[j] = sum_b d[b][j]   (thread per (k, j), fixed order)
+__global__ void k_dense_wgrad(const float *__restrict__ in, int K, const float *__restrict__ d, int N, int64_t n,
+                              float *__restrict__ gW, float *__restrict__ gb) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (K + 1) * N) return;
+  const int k = q / N, j = q % N;
+  float acc = 0.f;
+  if (k < K) {
+    for (int64_t b = 0; b < n; ++b) acc = fmaf(in[b * K + k], d[b * N + j], acc);
+    gW[k * N + j] = acc;
+  } else {
+    for (int64_t b = 0; b < n; ++b) acc += d[b * N + j];
+    gb[j] = acc;
+  }
+}
+
+// din[b][k] = (sum_j d[b][j] W[k][j]) * (in[b][k] > 0)   (in = post-ReLU activations)
+__global__ void k_dense_dgrad(const float *__restrict__ d, int N, const float *__restrict__ W,
+                              const float *__restrict__ in, int K, int64_t n, float *__restrict__ din) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n * K) return;
+  const int64_t b = q / K;
+  const int k = (int)(q % K);
+  float acc = 0.f;
+  for (int j = 0; j < N; ++j) acc = fmaf(d[b * N + j], W[k * N + j], acc);
+  din[q] = in[q] > 0.f ? acc : 0.f;
+}
+
+__global__ void k_adam(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m,
+                       float *__restrict__ v, int count, float lr, float c1, float c2) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= count) return;
+  const float mq = 0.9f * m[q] + 0.1f * g[q];
+  const float vq = 0.999f * v[q] + 0.001f * g[q] * g[q];
+  m[q] = mq;
+  v[q] = vq;
+  p[q] -= lr * (mq / c1) / (sqrtf(vq / c2) + 1e-8f);
+}
+
+// ---- fine-step labels (scalar volumes, FP32 storage) ----
+struct SegState {
+  uint32_t e;
+  float4 ra, rb, rc, rd;
+};
+
+template <int P>
+__device__ __forceinline__ bool seg_locate(const RenderParams &prm, SegState &st, Block<P, 0, LRVOL_STORE_F32> &blk,
+                                           float px, float py, float pz) {
+  const bool inside = st.e != kNone && px >= st.ra.x && py >= st.ra.y && pz >= st.ra.z && px < st.rb.x &&
+                      py < st.rb.y && pz < st.rb.z;
+  if (inside) return true;
+  const uint32_t e = forest_lookup(prm.forest, px, py, pz, prm.status);
+  if (e == kNone || (int64_t)e >= prm.n_elem) {
+    set_status(prm.status, kStatusBounds);
+    return false;
+  }
+  st.e = e;
+  load_record(prm.elem + e, st.ra, st.rb, st.rc, st.rd);
+  blk.load(prm.bez + (int64_t)e * prm.elem_bytes, 0);
+  return true;
+}
+
+// Alg. 2 from transparent over [ta, tb) with samples ta + k*h (each in its element).
+template <int P>
+__device__ void seg_composite(const RenderParams &prm, const Ray &ray, const float4 *tfb, const float4 *tfd,
+                              float ta, float tb, float h, SegState &st, Block<P, 0, LRVOL_STORE_F32> &blk,
+                              float &C0, float &C1, float &C2, float &Tr) {
+  constexpr int N = P + 1;
+  C0 = C1 = C2 = 0.f;
+  Tr = 1.f;
+  for (int k = 0; k < kMaxSamplesPerRay; ++k) {
+    const float t = __fmaf_rn((float)k, h, ta);
+    if (!(t < tb)) break;
+    const float px = fminf(fmaxf(__fmaf_rn(t, ray.d[0], ray.o[0]), 0.f), 1.f);
+    const float py = fminf(fmaxf(__fmaf_rn(t, ray.d[1], ray.o[1]), 0.f), 1.f);
+    const float pz = fminf(fmaxf(__fmaf_rn(t, ray.d[2], ray.o[2]), 0.f), 1.f);
+    if (!seg_locate<P>(prm, st, blk, px, py, pz)) return;
+    float bx[N], by[N], bz[N];
+    monomials<P>(local_u(px, st.ra.x, st.rc.x, st.rd.x), bx);
+    monomials<P>(local_u(py, st.ra.y, st.rc.y, st.rd.y), by);
+    monomials<P>(local_u(pz, st.ra.z, st.rc.z, st.rd.z), bz);
+    const float v = blk.eval(bx, by, bz);
+    const float tn = __fmaf_rn((float)(k + 1), h, ta);
+    composite(tfb, tfd, v, __fsub_rn(fminf(tn, tb), t), prm, C0, C1, C2, Tr);
+  }
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_labels(const __grid_constant__ RenderParams prm, float h_fine, float tau,
+                                                const float *__restrict__ cand, int n_cand,
+                                                int32_t *__restrict__ label) {
+  __shared__ float4 tfb[256], tfd[256];
+  for (int q = threadIdx.x; q < 256; q += blockDim.x) {
+    const float4 e0 = prm.tf[q], e1 = prm.tf[q < 255 ? q + 1 : 255];
+    tfb[q] = e0;
+    tfd[q] = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+  const int j = prm.row_begin + blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+  if (i >= prm.width || j >= prm.row_end) return;
+  Ray ray;
+  if (!make_ray(prm.ray, i, j, ray)) return;
+  Block<P, 0, LRVOL_STORE_F32> blk;
+  SegState st;
+  st.e = kNone;
+  const float tr_stop = 1.f - prm.alpha_stop;
+  float Tfront = 1.f;
+  float t = ray.tin;
+  for (int visit = 0; visit < kMaxSamplesPerRay && t < ray.tout && Tfront > tr_stop; ++visit) {
+    // the visit: element of the heuristic sample at t, up to the first heuristic sample past it
+    float px = fminf(fmaxf(__fmaf_rn(t, ray.d[0], ray.o[0]), 0.f), 1.f);
+    float py = fminf(fmaxf(__fmaf_rn(t, ray.d[1], ray.o[1]), 0.f), 1.f);
+    float pz = fminf(fmaxf(__fmaf_rn(t, ray.d[2], ray.o[2]), 0.f), 1.f);
+    if (!seg_locate<P>(prm, st, blk, px, py, pz)) return;
+    const uint32_t e = st.e;
+    const float4 ra = st.ra, rb = st.rb;
+    const float ds = ra.w;
+    float tb = t;
+    for (int q = 0; q < kMaxSamplesPerRay; ++q) {
+      tb = __fadd_rn(tb, ds);
+      if (!(tb < ray.tout)) break;
+      px = fminf(fmaxf(__fmaf_rn(tb, ray.d[0], ray.o[0]), 0.f), 1.f);
+      py = fminf(fmaxf(__fmaf_rn(tb, ray.d[1], ray.o[1]), 0.f), 1.f);
+      pz = fminf(fmaxf(__fmaf_rn(tb, ray.d[2], ray.o[2]), 0.f), 1.f);
+      if (!(px >= ra.x && py >= ra.y && pz >= ra.z && px < rb.x && py < rb.y && pz < rb.z)) break;
+    }
+    tb = fminf(tb, ray.tout);
+    float R0, R1, R2, RT;
+    seg_composite<P>(prm, ray, tfb, tfd, t, tb, h_fine, st, blk, R0, R1, R2, RT);
+    int best = 0;
+    for (int c = 1; c < n_cand; ++c) {
+      // the candidate's first sample outside e (or the ray's exit)
+      const float sc = __fmul_rn(ds, cand[c]);
+      float tc = t;
+      for (int k = 1; k < kMaxSamplesPerRay; ++k) {
+        tc = __fmaf_rn((float)k, sc, t);
+        if (!(tc < ray.tout)) break;
+        px = fminf(fmaxf(__fmaf_rn(tc, ray.d[0], ray.o[0]), 0.f), 1.f);
+        py = fminf(fmaxf(__fmaf_rn(tc, ray.d[1], ray.o[1]), 0.f), 1.f);
+        pz = fminf(fmaxf(__fmaf_rn(tc, ray.d[2], ray.o[2]), 0.f), 1.f);
+        if (!(px >= ra.x && py >= ra.y && pz >= ra.z && px < rb.x && py < rb.y && pz < rb.z)) break;
+      }
+      tc = fminf(tc, ray.tout);
+      float F0, F1, F2, FT, A0, A1, A2, AT;
+      seg_composite<P>(prm, ray, tfb, tfd, t, tc, h_fine, st, blk, F0, F1, F2, FT);
+      seg_composite<P>(prm, ray, tfb, tfd, t, tc, sc, st, blk, A0, A1, A2, AT);
+      const float err = Tfront * fmaxf(fmaxf(fabsf(A0 - F0), fabsf(A1 - F1)), fmaxf(fabsf(A2 - F2), fabsf(AT - FT)));
+      if (!(err <= tau)) break;
+      best = c;
+    }
+    atomicMin(label + e, best);
+    Tfront *= RT;
+    t = tb;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_features(const FeatureParams &fp, float *out, cudaStream_t s) {
+  k_features<<<(unsigned)((fp.n_elem + 127) / 128), 128, 0, s>>>(fp, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_pack(const float *params, uint16_t *packed, cudaStream_t s) {
+  k_mlp_pack<<<(kPacked + 255) / 256, 256, 0, s>>>(params, packed);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
+                             cudaStream_t s) {
+  const int64_t tiles = (n + 15) / 16;
+  const int64_t blocks = std::min<int64_t>((tiles + 3) / 4, 152 * 8);
+  k_mlp_infer<<<(unsigned)std::max<int64_t>(blocks, 1), 128, 0, s>>>(x, n, packed, ymax, out);
+  return cudaGetLastError();
+}
+
+// Scratch layout (floats): h1, h2, h3 (n x 64 each), y (n), dy (n), d3, d2, d1 (n x 64 each)
+cudaError_t launch_mlp_grad(const float *x, const float *target, int64_t n, const float *p, float *grad,
+                            float *loss, float *scratch, cudaStream_t s) {
+  float *h1 = scratch, *h2 = h1 + n * kHid, *h3 = h2 + n * kHid, *y = h3 + n * kHid, *dy = y + n;
+  float *d3 = dy + n, *d2 = d3 + n * kHid, *d1 = d2 + n * kHid;
+  const unsigned thr = 256;
+  auto blocks = [&](int64_t c) { return (unsigned)((c + thr - 1) / thr); };
+  k_dense_fwd<<<blocks(n * kHid), thr, 0, s>>>(x, kIn, p + kOffW1, p + kOffB1, kHid, n, true, h1);
+  k_dense_fwd<<<blocks(n * kHid), thr, 0, s>>>(h1, kHid, p + kOffW2, p + kOffB2, kHid, n, true, h2);
+  k_dense_fwd<<<blocks(n * kHid), thr, 0, s>>>(h2, kHid, p + kOffW3, p + kOffB3, kHid, n, true, h3);
+  k_dense_fwd<<<blocks(n), thr, 0, s>>>(h3, kHid, p + kOffW4, p + kOffB4, 1, n, false, y);
+  k_loss<<<1, 256, 0, s>>>(y, target, n, dy, loss);
+  k_dense_wgrad<<<blocks((kHid + 1) * 1), thr, 0, s>>>(h3, kHid, dy, 1, n, grad + kOffW4, grad + kOffB4);
+  k_dense_dgrad<<<blocks(n * kHid), thr, 0, s>>>(dy, 1, p + kOffW4, h3, kHid, n, d3);
+  k_dense_wgrad<<<blocks((kHid + 1) * kHid), thr, 0, s>>>(h2, kHid, d3, kHid, n, grad + kOffW3, grad + kOffB3);
+  k_dense_dgrad<<<blocks(n * kHid), thr, 0, s>>>(d3, kHid, p + kOffW3, h2, kHid, n, d2);
+  k_dense_wgrad<<<blocks((kHid + 1) * kHid), thr, 0, s>>>(h1, kHid, d2, kHid, n, grad + kOffW2, grad + kOffB2);
+  k_dense_dgrad<<<blocks(n * kHid), thr, 0, s>>>(d2, kHid, p + kOffW2, h1, kHid, n, d1);
+  k_dense_wgrad<<<blocks((kIn + 1) * kHid), thr, 0, s>>>(x, kIn, d1, kHid, n, grad + kOffW1, grad + kOffB1);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int64_t t, float lr, cudaStream_t s) {
+  const float c1 = 1.f - powf(0.9f, (float)t), c2 = 1.f - powf(0.999f, (float)t);
+  k_adam<<<(kParams + 255) / 256, 256, 0, s>>>(params, grad, m, v, kParams, lr, c1, c2);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_labels(const RenderParams &prm, int degree, float h_fine, float tau, const float *cand, int n_cand,
+                          int32_t *label, cudaStream_t s) {
+  const dim3 grid((unsigned)((prm.width + 15) / 16), (unsigned)((prm.row_end - prm.row_begin + 7) / 8));
+  switch (degree) {
+    case 1: k_labels<1><<<grid, 128, 0, s>>>(prm, h_fine, tau, cand, n_cand, label); break;
+    case 2: k_labels<2><<<grid, 128, 0, s>>>(prm, h_fine, tau, cand, n_cand, label); break;
+    case 3: k_labels<3><<<grid, 128, 0, s>>>(prm, h_fine, tau, cand, n_cand, label); break;
+    default: return cudaErrorInvalidValue;
+  }
+  return cudaGetLastError();
 }
 
 // ----------------------------------------------------------------------------

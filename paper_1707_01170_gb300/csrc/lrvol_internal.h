@@ -109,6 +109,7 @@ struct RenderParams {
   int width, height, row_begin, row_end;
   RayConsts ray;
   int mode;               // LRVOL_STEP_*
+  const float *mult;      // LEARNED: per-element step multipliers
   float h, inv_xi, alpha_stop;
   float tf_scale, tf_bias; // x = v * tf_scale + tf_bias, clamped to [0, 255]
   unsigned long long *counters;
@@ -139,6 +140,7 @@ struct lrvol_s {
   unsigned char *d_bezc = nullptr;  // vector volumes: plain per-component copy
   int elem_bytes = 0, elemc_bytes = 0;
   int storage = -1;
+  float2 *d_range = nullptr;  // per element and component: coefficient min, max
   lrvol::ElemRec *d_elem = nullptr;
   bool have_bezier = false;
   // forest
@@ -170,5 +172,40 @@ cudaError_t launch_render_static(RenderParams prm, int degree, int field, int st
 // host.cpp
 void camera_consts(const lrvol_camera *c, RayConsts *k);
 ForestView forest_view(const lrvol_s *v);
+
+}  // namespace lrvol
+
+namespace lrvol {
+
+// Learned step sizes (lrvol.h): parameter offsets of the FP32 master vector
+constexpr int kIn = 16, kHid = 64;
+constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kIn * kHid, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid,
+              kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid, kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kHid,
+              kParams = kOffB4 + 1;
+// packed BF16 fragments (uint16 offsets): [k-step][n-tile][lane][4]
+constexpr int kPkL1 = 0, kPkL2 = kPkL1 + 1 * 8 * 128, kPkL3 = kPkL2 + 4 * 8 * 128, kPkL4 = kPkL3 + 4 * 8 * 128,
+              kPkBias = kPkL4 + 4 * 1 * 128, kPacked = ((kPkBias + 2 * (3 * kHid + 1)) + 7) & ~7;
+static_assert(kParams == 9473, "parameter count");
+static_assert(kPacked == 10120, "packed size");
+
+struct FeatureParams {
+  const double *box;
+  const ElemRec *elem;
+  const float2 *range;  // per element and component: coefficient min, max (rounded outward)
+  int64_t n_elem;
+  int nc, field, comp;
+  float eye[3];
+  float tf_scale, tf_bias;  // x = v * scale + bias in TF entries (0..255)
+  float4 tf[256];
+};
+
+cudaError_t launch_features(const FeatureParams &fp, float *out, cudaStream_t s);
+cudaError_t launch_mlp_pack(const float *params, uint16_t *packed, cudaStream_t s);
+cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out, cudaStream_t s);
+cudaError_t launch_mlp_grad(const float *x, const float *target, int64_t n, const float *params, float *grad,
+                            float *loss, float *scratch, cudaStream_t s);
+cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int64_t t, float lr, cudaStream_t s);
+cudaError_t launch_labels(const RenderParams &prm, int degree, float h_fine, float tau, const float *cand, int n_cand,
+                          int32_t *label, cudaStream_t s);
 
 }  // namespace lrvol

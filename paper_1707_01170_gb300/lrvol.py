@@ -16,14 +16,16 @@ LIB_PATH = os.path.join(_HERE, "liblrvol.so")
 
 OK, ERR_ARG, ERR_OOM, ERR_CUDA, ERR_STATE, ERR_BOUNDS, ERR_TIMEOUT, ERR_UNSUPPORTED = 0, -1, -2, -3, -4, -5, -6, -7
 ORTHO, PERSP = 0, 1
-STEP_FIXED, STEP_HEURISTIC = 0, 1
+STEP_FIXED, STEP_HEURISTIC, STEP_LEARNED = 0, 1, 2
 FIELD_SCALAR, FIELD_MAGNITUDE, FIELD_COMPONENT = 0, 1, 2
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 NONE = 0xFFFFFFFF
 
 EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
             "lrvol_eval", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
-            "lrvol_destroy", "lrvol_render_noalloc"]
+            "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features", "lrvol_mlp_pack", "lrvol_mlp_infer",
+            "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels"]
+MLP_IN, MLP_HIDDEN, MLP_PARAMS, MLP_PACKED = 16, 64, 9473, 10120
 
 
 class LrvolError(RuntimeError):
@@ -45,7 +47,8 @@ class TF(ctypes.Structure):
 
 class Step(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("field", ctypes.c_int32), ("component", ctypes.c_int32),
-                ("h", ctypes.c_double), ("xi", ctypes.c_double), ("alpha_stop", ctypes.c_double)]
+                ("h", ctypes.c_double), ("xi", ctypes.c_double), ("alpha_stop", ctypes.c_double),
+                ("mult", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -97,6 +100,21 @@ def load(path: str = LIB_PATH):
         L.lrvol_last_error.argtypes = []
         L.lrvol_destroy.restype = None
         L.lrvol_destroy.argtypes = [vp]
+        L.lrvol_features.restype = ctypes.c_int
+        L.lrvol_features.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step), vp, vp]
+        L.lrvol_mlp_pack.restype = ctypes.c_int
+        L.lrvol_mlp_pack.argtypes = [vp, vp, vp]
+        L.lrvol_mlp_infer.restype = ctypes.c_int
+        L.lrvol_mlp_infer.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
+        L.lrvol_mlp_scratch_floats.restype = i64
+        L.lrvol_mlp_scratch_floats.argtypes = [i64]
+        L.lrvol_mlp_grad.restype = ctypes.c_int
+        L.lrvol_mlp_grad.argtypes = [vp, vp, i64, vp, vp, vp, vp, vp]
+        L.lrvol_mlp_train_step.restype = ctypes.c_int
+        L.lrvol_mlp_train_step.argtypes = [vp, vp, i64, vp, vp, vp, i64, ctypes.c_float, vp, vp, vp]
+        L.lrvol_labels.restype = ctypes.c_int
+        L.lrvol_labels.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
+                                   ctypes.c_double, ctypes.c_double, vp, i32, vp, vp]
         _lib = L
     return _lib
 
@@ -150,8 +168,16 @@ def make_tf(tf) -> TF:
 
 
 def make_step(step) -> Step:
+    """From any object with mode ('fixed'|'heuristic'|'learned'), field,
+    component, h, xi, alpha_stop and, for learned steps, mult: a CUDA float32
+    tensor of one multiplier per element (kept alive by the caller)."""
     s = Step()
-    s.mode = STEP_HEURISTIC if step.mode == "heuristic" else STEP_FIXED
+    s.mode = {"fixed": STEP_FIXED, "heuristic": STEP_HEURISTIC, "learned": STEP_LEARNED}[step.mode]
+    if step.mode == "learned":
+        m = step.mult
+        if m is None or not getattr(m, "is_cuda", False) or not m.is_contiguous():
+            raise ValueError("learned steps need a contiguous CUDA tensor of multipliers")
+        s.mult = m.data_ptr()
     s.field = {"scalar": FIELD_SCALAR, "magnitude": FIELD_MAGNITUDE, "component": FIELD_COMPONENT}[step.field]
     s.component = int(step.component)
     s.h, s.xi, s.alpha_stop = float(step.h), float(step.xi), float(step.alpha_stop)
@@ -239,3 +265,87 @@ class Volume:
         s = Stats()
         _check(load().lrvol_stats(self._h, ctypes.byref(s)), "lrvol_stats")
         return s.as_dict()
+
+
+# ---- learned step sizes ----------------------------------------------------
+
+def _dev(t, dtype=None):
+    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
+    if dtype is not None:
+        assert t.dtype == dtype, f"expected {dtype}"
+    return t.data_ptr()
+
+
+def features(vol: "Volume", cam, tf, step, out=None, stream=None):
+    """Per-element features (n_elem x 16 float32 CUDA tensor) for a camera/TF."""
+    import torch
+    if out is None:
+        out = torch.empty((vol.n_elem, MLP_IN), dtype=torch.float32, device="cuda")
+    c = cam if isinstance(cam, Camera) else make_camera(cam)
+    t = tf if isinstance(tf, TF) else make_tf(tf)
+    s = step if isinstance(step, Step) else make_step(step)
+    _check(load().lrvol_features(vol.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), _dev(out),
+                                 _stream_ptr(stream)), "lrvol_features")
+    return out
+
+
+def mlp_pack(params, out=None, stream=None):
+    """FP32 master parameters -> BF16 fragment order (int16 CUDA tensor of MLP_PACKED)."""
+    import torch
+    if out is None:
+        out = torch.empty(MLP_PACKED, dtype=torch.int16, device="cuda")
+    _check(load().lrvol_mlp_pack(_dev(params, torch.float32), _dev(out), _stream_ptr(stream)), "lrvol_mlp_pack")
+    return out
+
+
+def mlp_infer(x, packed, ymax: float, out=None, stream=None):
+    """Multipliers 2^clamp(y, 0, ymax) for feature rows x (n x 16) on BF16 tensor cores."""
+    import torch
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(load().lrvol_mlp_infer(_dev(x, torch.float32), n, _dev(packed), float(ymax), _dev(out),
+                                  _stream_ptr(stream)), "lrvol_mlp_infer")
+    return out
+
+
+def mlp_scratch(n: int):
+    import torch
+    return torch.empty(int(load().lrvol_mlp_scratch_floats(n)), dtype=torch.float32, device="cuda")
+
+
+def mlp_grad(x, target, params, scratch=None, stream=None):
+    """Loss and gradient of the FP32 network on a batch (CUDA tensors)."""
+    import torch
+    n = x.shape[0]
+    scratch = mlp_scratch(n) if scratch is None else scratch
+    grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
+    loss = torch.empty(1, dtype=torch.float32, device="cuda")
+    _check(load().lrvol_mlp_grad(_dev(x, torch.float32), _dev(target, torch.float32), n, _dev(params, torch.float32),
+                                 _dev(grad), _dev(loss), _dev(scratch), _stream_ptr(stream)), "lrvol_mlp_grad")
+    return loss, grad
+
+
+def mlp_train_step(x, target, params, m, v, t: int, lr: float, scratch, loss=None, stream=None):
+    """One Adam step of the FP32 network on a batch (all CUDA tensors, in place)."""
+    import torch
+    n = x.shape[0]
+    _check(load().lrvol_mlp_train_step(_dev(x, torch.float32), _dev(target, torch.float32), n,
+                                       _dev(params, torch.float32), _dev(m), _dev(v), int(t), float(lr),
+                                       None if loss is None else _dev(loss), _dev(scratch), _stream_ptr(stream)),
+           "lrvol_mlp_train_step")
+
+
+def labels(vol: "Volume", cam, tf, step, h_fine: float, tau: float, cand, label=None, stream=None):
+    """Per-element training labels (int32 CUDA tensor; n_cand marks unvisited)."""
+    import torch
+    cand_t = torch.as_tensor(cand, dtype=torch.float32, device="cuda").contiguous()
+    if label is None:
+        label = torch.full((vol.n_elem,), len(cand_t), dtype=torch.int32, device="cuda")
+    c = cam if isinstance(cam, Camera) else make_camera(cam)
+    t = tf if isinstance(tf, TF) else make_tf(tf)
+    s = step if isinstance(step, Step) else make_step(step)
+    _check(load().lrvol_labels(vol.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), float(h_fine),
+                               float(tau), _dev(cand_t), len(cand_t), _dev(label), _stream_ptr(stream)),
+           "lrvol_labels")
+    return label

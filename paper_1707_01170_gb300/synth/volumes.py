@@ -52,12 +52,13 @@ class TransferFunction:
 
 @dataclass
 class StepParams:
-    mode: str = "fixed"      # "fixed" | "heuristic"
+    mode: str = "fixed"      # "fixed" | "heuristic" | "learned"
     h: float = 1.0 / 256     # fixed step
     xi: float = 1.0 / 256    # reference length xi of Alg. 2
     alpha_stop: float = 1.0  # early termination threshold (1 = off)
     field: str = "scalar"    # "scalar" | "magnitude" | "component"
     component: int = 0
+    mult: object = None      # learned: per-element step multipliers (array or device tensor)
 
 
 def seeded_tf(stream: Stream, n_ctrl: int = 8, alpha_max: float = 0.08, bands=()) -> TransferFunction:

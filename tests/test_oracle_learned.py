@@ -1,0 +1,102 @@
+"""Pins of the learned-step reference (oracle/learned.py, orc_labels) to
+things other than themselves: finite differences, a closed-form Adam step,
+BF16 rounding of known values, hand-computed features, and labels of
+constant fields (Alg. 2 telescopes, so every step size gives the same
+segment composite)."""
+import numpy as np
+import pytest
+
+from oracle import learned as OL
+from oracle.oracle import Oracle
+from paper_1707_01170_gb300.synth import volumes as V
+from paper_1707_01170_gb300.synth.lrgen import LRVolume
+
+
+def _params(seed, scale=0.3):
+    u = V.Stream(seed, OL.N_PARAMS + 8).take(OL.N_PARAMS)
+    return scale * (2 * u - 1)
+
+
+def test_gradient_matches_finite_differences():
+    rng = np.random.default_rng(0)
+    p = _params(5)
+    X = rng.normal(size=(37, OL.IN))
+    t = rng.normal(size=37)
+    loss, g = OL.loss_and_grad(p, X, t)
+    idx = np.concatenate([rng.choice(OL.N_PARAMS, 60, replace=False), [OL.N_PARAMS - 1]])
+    for i in idx:
+        e = np.zeros_like(p)
+        e[i] = 1e-6
+        fd = (OL.loss_and_grad(p + e, X, t)[0] - OL.loss_and_grad(p - e, X, t)[0]) / 2e-6
+        assert abs(fd - g[i]) <= 1e-6 + 1e-5 * abs(fd), i
+    assert loss == pytest.approx(0.5 * np.mean((OL.forward(p, X) - t) ** 2))
+
+
+def test_adam_first_step_closed_form():
+    p = np.array([1.0, -2.0, 0.5])
+    g = np.array([0.3, -4.0, 0.0])
+    p1, m, v = OL.adam(p, g, np.zeros(3), np.zeros(3), 1, 0.01)
+    # bias-corrected first step: lr * g / (|g| + eps)
+    np.testing.assert_allclose(p1, p - 0.01 * g / (np.abs(g) + 1e-8), rtol=1e-12)
+    np.testing.assert_allclose(m, 0.1 * g)
+    np.testing.assert_allclose(v, 0.001 * g * g)
+
+
+def test_bf16_rounding_known_values():
+    x = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -9, 1 + 2 ** -7, -2.5, 3.140625, 1 + 2 ** -8 + 2 ** -20])
+    want = np.array([1.0, 1.0, 1 + 2 ** -7, 1 + 2 ** -7, -2.5, 3.140625, 1 + 2 ** -7])
+    np.testing.assert_array_equal(OL.bf16(x), want)
+
+
+def test_forward_emulation_is_rounding_of_the_fp64_forward():
+    rng = np.random.default_rng(1)
+    p = _params(6)
+    X = rng.normal(size=(200, OL.IN))
+    a, b = OL.forward(p, X), OL.forward(p, X, emulate_bf16=True)
+    assert np.max(np.abs(a - b)) < 0.05 * (1 + np.max(np.abs(a)))
+    assert np.max(np.abs(a - b)) > 0
+
+
+def test_features_single_element_by_hand():
+    """One clamped tricubic element: the block equals the coefficients."""
+    coef = np.linspace(0.21, 0.61, 64)   # ends away from TF bin edges
+    vol = V.tensor_product((3, 3, 3), (1, 1, 1), coef=coef[:, None])
+    orc = Oracle(vol)
+    table = np.zeros((256, 4))
+    table[:, 3] = np.arange(256) / 255.0                      # alpha ramp
+    table[:, 0] = np.where(np.arange(256) < 128, 0.25, 0.75)  # red step at 128
+    tf = V.TransferFunction(table=table, vmin=0.0, vmax=1.0)
+    cam = V.Camera("persp", 8, 8, eye=(0.5, 0.5, 3.0), target=(0.5, 0.5, 0.5), up=(0.0, 1.0, 0.0), fovy=0.5)
+    F = OL.features(orc, vol.elem_box, cam, tf)[0]
+    np.testing.assert_allclose(F[0:3], np.log2(64.0))
+    assert F[3] == pytest.approx(0.21) and F[4] == pytest.approx(0.61) and F[5] == pytest.approx(0.4)
+    i0, i1 = 53, 156
+    assert F[6] == pytest.approx(i1 / 255) and F[7] == pytest.approx((i0 + i1) / 2 / 255)
+    assert F[8] == pytest.approx(1.0) and F[9] == pytest.approx(0.5)
+    np.testing.assert_allclose(F[10:13], [0, 0, -1], atol=1e-12)
+    assert F[13] == pytest.approx(np.log2(2048 / 8)) and F[14] == pytest.approx(1.0)
+    assert F[15] == pytest.approx(np.log2(1 + 255 * 0.4))
+
+
+def test_labels_constant_field_accept_every_candidate(cfg1):
+    vol = LRVolume(deg=cfg1.deg, elem_box=cfg1.elem_box, knots=cfg1.knots,
+                   coef=np.full((cfg1.n_basis, 1), 0.4), weight=cfg1.weight, grid=cfg1.grid)
+    orc = Oracle(vol)
+    tf, _ = V.config1_render()
+    cand = [1, 1.5, 2, 3, 4]
+    lab = orc.labels(V.ortho_z(8, 8), tf, V.StepParams(mode="heuristic"), 1 / 2048, 1e-9, cand)
+    visited = lab < len(cand)
+    assert visited.sum() > 20
+    assert np.all(lab[visited] == len(cand) - 1)
+
+
+def test_labels_monotone_in_tau(cfg1, cfg1_oracle):
+    tf, _ = V.config1_render()
+    cam = V.ortho_z(6, 6)
+    cand = [1, 2, 4, 8]
+    step = V.StepParams(mode="heuristic")
+    tight = cfg1_oracle.labels(cam, tf, step, 1 / 2048, 1e-7, cand)
+    loose = cfg1_oracle.labels(cam, tf, step, 1 / 2048, 1e-2, cand)
+    visited = tight < len(cand)
+    assert np.array_equal(visited, loose < len(cand))
+    assert np.all(tight[visited] <= loose[visited]) and np.any(tight[visited] < loose[visited])

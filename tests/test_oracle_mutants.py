@@ -51,6 +51,8 @@ MUTANTS = [
     ("slab test uses the wrong face", "float tb = (1.0f - o[c]) * inv;", "float tb = (0.5f - o[c]) * inv;"),
     ("fixed step doubled", "tn = fmaf((float)(k + 1), (float)J->st->h, tin);",
      "tn = fmaf((float)(k + 1), 2.0f * (float)J->st->h, tin);"),
+    ("learned step ignores the multiplier", "tn = t + orc_heuristic_step(v, cur) * J->st->mult[cur];",
+     "tn = t + orc_heuristic_step(v, cur);"),
 ]
 
 
@@ -74,6 +76,7 @@ def _pins(cfg1):
     yield lambda: P.test_tf_linear_interpolation(cfg1)
     yield lambda: P.heuristic_count_pin(cfg1, O)
     yield lambda: P.test_heuristic_step_counts_anisotropic()
+    yield lambda: P.test_learned_step_counts()
     yield lambda: P.test_early_termination_and_miss(O)
 
 

@@ -372,7 +372,7 @@ def test_tf_linear_interpolation(cfg1):
         assert img[0, 0, 3] == pytest.approx(1 - (1 - want) ** 4, abs=1e-12)
 
 
-def heuristic_count_pin(vol, O):
+def heuristic_count_pin(vol, O, mult=None):
     """Eq. 4 on axis-aligned rays, walked independently in exact rational
     arithmetic: from z = 1 downwards, the sample at z belongs to the element
     with lo_z <= z < hi_z (z = 1: the top element) and advances by 2^-d times
@@ -382,7 +382,10 @@ def heuristic_count_pin(vol, O):
     from fractions import Fraction as Fr
     cam = V.ortho_z(16, 16)
     tf = _const_tf([1, 1, 1, 0.0])
-    img, stats = O.render(cam, tf, V.StepParams(mode="heuristic"))
+    if mult is None:
+        img, stats = O.render(cam, tf, V.StepParams(mode="heuristic"))
+    else:
+        img, stats = O.render(cam, tf, V.StepParams(mode="learned", mult=mult))
     b = vol.elem_box
     d = int(max(vol.deg))
     total = 0
@@ -392,15 +395,17 @@ def heuristic_count_pin(vol, O):
             col = np.nonzero((b[:, 0] <= x) & (x < b[:, 3]) & (b[:, 1] <= y) & (y < b[:, 4]))[0]
             lo = [Fr(b[e, 2]) for e in col]
             hi = [Fr(b[e, 5]) for e in col]
-            step = [Fr(float(np.min(b[e, 3:] - b[e, :3]))) / 2 ** d for e in col]
+            step = [Fr(float(np.min(b[e, 3:] - b[e, :3]))) / 2 ** d * Fr(1 if mult is None else float(mult[e]))
+                    for e in col]
             z, per = Fr(1), {}
             while z > 0:
                 k = next(q for q in range(len(col)) if lo[q] <= z and (z < hi[q] or z == 1 == hi[q]))
                 per[k] = per.get(k, 0) + 1
                 z -= step[k]
             total += sum(per.values())
-            for k, n in per.items():
-                assert abs(n - (hi[k] - lo[k]) / step[k]) <= 1
+            if mult is None:
+                for k, n in per.items():
+                    assert abs(n - (hi[k] - lo[k]) / step[k]) <= 1
     assert stats["samples"] == total
     e0 = int(np.argmin(np.min(b[:, 3:] - b[:, :3], axis=1)))
     assert O.heuristic_step(e0) == pytest.approx(np.min(b[e0, 3:] - b[e0, :3]) / 2 ** d)
@@ -419,6 +424,22 @@ def test_heuristic_step_counts(cfg1, cfg1_oracle):
 def test_heuristic_step_counts_anisotropic():
     vol = anisotropic_volume()
     heuristic_count_pin(vol, Oracle(vol))
+
+
+def test_learned_step_counts():
+    """Learned steps (Eq. 4 times a per-element multiplier): power-of-two
+    multipliers keep the walk exact, so the counts match a rational walk."""
+    vol = anisotropic_volume()
+    mult = (2.0 ** np.floor(V.Stream(77).uniform(0.0, 3.0, vol.n_elem))).astype(np.float32)
+    heuristic_count_pin(vol, Oracle(vol), mult=mult)
+
+
+def test_learned_unit_multipliers_equal_heuristic(cfg1, cfg1_oracle):
+    tf, cams = V.config1_render()
+    a, sa = cfg1_oracle.render(cams[1], tf, V.StepParams(mode="heuristic", alpha_stop=0.99))
+    b, sb = cfg1_oracle.render(cams[1], tf, V.StepParams(mode="learned", alpha_stop=0.99,
+                                                          mult=np.ones(cfg1.n_elem, np.float32)))
+    assert np.array_equal(a, b) and sa == sb
 
 
 def test_fixed_step_converges(cfg1, cfg1_oracle):
