@@ -100,3 +100,47 @@ def test_labels_monotone_in_tau(cfg1, cfg1_oracle):
     visited = tight < len(cand)
     assert np.array_equal(visited, loose < len(cand))
     assert np.all(tight[visited] <= loose[visited]) and np.any(tight[visited] < loose[visited])
+
+
+def _slab_volume():
+    """Trilinear, constant in x and y; z knots 0, 0.5, 0.75, 1: elements
+    e0 = z in [0, 0.5) (zero field), e1 = [0.5, 0.75) (ramp 0 -> 1),
+    e2 = [0.75, 1] (ramp 1 -> 0).  Eq. 4 steps: 1/4 in e0, 1/8 in e1, e2."""
+    zk = [[0, 0, 0.5], [0, 0.5, 0.75], [0.5, 0.75, 1], [0.75, 1, 1]]
+    zc = [0.0, 0.0, 1.0, 0.0]
+    xk = [[0, 0, 1], [0, 1, 1]]
+    knots, coef = [], []
+    for kz, cz in zip(zk, zc):
+        for ky in xk:
+            for kx in xk:
+                knots.append(kx + ky + kz)
+                coef.append([cz])
+    box = np.array([[0, 0, 0, 1, 1, 0.5], [0, 0, 0.5, 1, 1, 0.75], [0, 0, 0.75, 1, 1, 1]], dtype=np.float64)
+    return LRVolume(deg=np.array([1, 1, 1]), elem_box=box, knots=np.array(knots, dtype=np.float64),
+                    coef=np.array(coef), weight=np.ones(len(knots)), grid=np.array([1, 1, 4]))
+
+
+def _slab_tf():
+    table = np.ones((256, 4))
+    table[:, 3] = 0.5 * np.arange(256) / 255.0
+    return V.TransferFunction(table=table, vmin=0.0, vmax=1.0)
+
+
+def test_labels_count_what_the_last_step_skips():
+    """Looking along +z, every step longer than Eq. 4's from e0 lands at or
+    past z = 0.75 and skips the opaque ramp in e1, so e0 takes label 0."""
+    orc = Oracle(_slab_volume())
+    cam = V.Camera("ortho", 2, 2, eye=(0.5, 0.5, -2.0), target=(0.5, 0.5, 0.0), up=(0.0, 1.0, 0.0), extent=0.5)
+    lab = orc.labels(cam, _slab_tf(), V.StepParams(mode="heuristic", xi=1 / 256), 1 / 2048, 1e-3, [1, 1.5, 2, 4, 8])
+    assert lab[0] == 0
+
+
+def test_labels_weigh_errors_by_front_transmittance():
+    """Looking along -z, e2's ramp leaves a transmittance of about 5e-7 in
+    front of e1, so every candidate of e1 is acceptable there."""
+    orc = Oracle(_slab_volume())
+    cam = V.Camera("ortho", 2, 2, eye=(0.5, 0.5, 3.0), target=(0.5, 0.5, 0.5), up=(0.0, 1.0, 0.0), extent=0.5)
+    cand = [1, 1.5, 2, 4, 8]
+    lab = orc.labels(cam, _slab_tf(), V.StepParams(mode="heuristic", xi=1 / 256), 1 / 2048, 1e-3, cand)
+    assert lab[1] == len(cand) - 1
+    assert lab[2] < len(cand) - 1          # the ramp in front is judged at full weight

@@ -3,7 +3,8 @@
 Each case edits one line of oracle.c (a dropped term, a wrong index or sign,
 a transposed axis, an off-by-one), builds the edited copy on the CPU into a
 temporary directory, points the oracle module at it, and runs the pins of
-test_oracle_pins; at least one must fail.  The default build is restored
+test_oracle_pins and the label pins of test_oracle_learned; at least one
+must fail.  The default build is restored
 afterwards.  No GPU is involved.
 """
 import os
@@ -11,6 +12,7 @@ import pytest
 
 import oracle.oracle as orc
 
+import test_oracle_learned as L
 import test_oracle_pins as P
 
 SRC = os.path.join(os.path.dirname(orc.__file__), "oracle.c")
@@ -53,6 +55,15 @@ MUTANTS = [
      "tn = fmaf((float)(k + 1), 2.0f * (float)J->st->h, tin);"),
     ("learned step ignores the multiplier", "tn = t + orc_heuristic_step(v, cur) * J->st->mult[cur];",
      "tn = t + orc_heuristic_step(v, cur);"),
+    ("labels judged only over the Eq. 4 visit",
+     "seg_composite(v, J->tf, J->st, o, d, t, tc, (float)J->h_fine, &sc, F, &FA);\n"
+     "        seg_composite(v, J->tf, J->st, o, d, t, tc, s, &sc, Cc, &CA);",
+     "seg_composite(v, J->tf, J->st, o, d, t, tb, (float)J->h_fine, &sc, F, &FA);\n"
+     "        seg_composite(v, J->tf, J->st, o, d, t, tb, s, &sc, Cc, &CA);"),
+    ("labels ignore the front transmittance", "if (!(Tfront * err <= J->tau)) break;",
+     "if (!(err <= J->tau)) break;"),
+    ("labels compare candidates with the Eq. 4 step", "float s = ds * J->cand[c], tc = t;",
+     "float s = ds, tc = t;"),
 ]
 
 
@@ -78,6 +89,10 @@ def _pins(cfg1):
     yield lambda: P.test_heuristic_step_counts_anisotropic()
     yield lambda: P.test_learned_step_counts()
     yield lambda: P.test_early_termination_and_miss(O)
+    yield lambda: L.test_labels_constant_field_accept_every_candidate(cfg1)
+    yield lambda: L.test_labels_monotone_in_tau(cfg1, O)
+    yield lambda: L.test_labels_count_what_the_last_step_skips()
+    yield lambda: L.test_labels_weigh_errors_by_front_transmittance()
 
 
 def test_unmutated_source_passes_the_same_pins(cfg1):
