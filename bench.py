@@ -12,10 +12,12 @@ At one GPU the line also carries `learned_step`: the same frame rendered with
 learned step sizes (per-element multipliers from the BF16 network, trained
 first on seeded cameras of configs 1 and 2) on FP16 blocks, timed whole
 (features, network, render) against the plain FP32 Eq. 4 frame, with both
-images' RMSE against the fine-step (1/2048) reference.
+images' RMSE against the fine-step (1/2048) reference, and `serving`: the
+continuous-batching frame server over configs 1-3 resident at once, fed
+seeded Poisson streams of mixed-size requests (latency p50/p99, frames/s).
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
-                [--learned off|f32|f16|bf16]
+                [--learned off|f32|f16|bf16] [--serve off|plain|learned|both]
 Under torchrun each rank renders its own frame (replicas; weak scaling) and
 rank 0 prints one JSON line.
 """
@@ -33,6 +35,9 @@ import numpy as np
 
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
+# the frame server runs 3 streams per slot; give each its own hardware queue
+# (read when the CUDA context is created, before any CUDA call below)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
 
 WIDTH, HEIGHT = 1920, 1080
 BLOCKS = (64, 64, 64)
@@ -268,7 +273,58 @@ def learned_leg(vol, tf, cam, step, plain, steps: int, storage: str, flush, stre
                      "margin": model.cfg.margin, "ymax": model.cfg.ymax, "steps": model.cfg.steps,
                      "recipe": "16 seeded 320x180 cameras on each of configs 1 and 2"}}
     gq.close()
+    res["_model"] = model
     return res
+
+
+SERVE_PLAN = ((60.0, 500), (120.0, 1000), (240.0, 2000))   # (requests/s, requests): about 8 s each
+
+
+def serving_leg(model, modes, plan=SERVE_PLAN, slots: int = 8, arena_gb: int = 4):
+    """Continuous-batching frame server over three resident volumes (configs
+    1, 2 and 3 as |v|): seeded Poisson request streams mixing 256x256,
+    1920x1080 and 3840x2160 frames on orbiting cameras, admitted by free
+    slot and arena memory.  Per mode and arrival rate: latency p50/p99 (ms,
+    completion minus arrival, host clock), frames/s and Gsamples/s."""
+    import torch
+    from paper_1707_01170_gb300 import lrvol as lv
+    from paper_1707_01170_gb300 import serve
+    from paper_1707_01170_gb300.synth import volumes as V
+    vols = [V.load_config(1), V.load_config(2), V.load_config(3)]
+    tf1 = V.config1_render()[0]
+    tf2 = V.config2_render(vol=vols[1])[0]
+    tf3 = V.config3_render()[0]
+    tf3.vmin, tf3.vmax = 0.0, 1.5
+    tfs = [tf1, tf2, tf3]
+    plain = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
+    mag = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, field="magnitude")
+    learned = V.StepParams(mode="learned", xi=1 / 256, alpha_stop=0.99)
+    out = {"volumes": ["config 1 (9,864 elements)", "config 2 (174,000)", "config 3 |v| (388,016)"],
+           "sizes": [f"{w}x{h}" for w, h in serve.SIZES], "slots": slots, "arena_bytes": arena_gb << 30,
+           "priority_pixels": 1 << 20, "latency": "host clock, from scheduled arrival to the poll that saw the "
+                                                  "frame finished; images stay on the device", "runs": []}
+    for mode in modes:
+        store = lv.STORE_F32 if mode == "plain" else lv.STORE_F16
+        gvs = [lv.Volume(v).build_accel(BLOCKS).to_bezier(store) for v in vols]
+        steps = [plain, plain, mag] if mode == "plain" else [learned, learned, mag]
+        for rate, n in plan:
+            srv = lv.Server(slots=slots, arena_bytes=arena_gb << 30)
+            srv.set_priority_pixels(1 << 20)
+            if mode != "plain":
+                srv.set_step_model(model.packed, model.cfg.ymax)
+            reqs = serve.request_stream(1707011700 + 5000 + int(rate), n, rate, 3)
+            torch.cuda.synchronize()
+            recs = serve.run_stream(srv, gvs, tfs, steps, reqs)
+            summ = serve.summarize(recs)
+            st = srv.stats()
+            srv.close()
+            out["runs"].append({"mode": "FP32 blocks, Eq. 4" if mode == "plain" else
+                                "FP16 blocks, learned steps on configs 1-2 (server-side network), Eq. 4 on config 3",
+                                "rate_per_s": rate, "requests": n, "max_in_flight": st["max_running"],
+                                "arena_high_water": st["arena_high_water"], **summ})
+        for g in gvs:
+            g.close()
+    return out
 
 
 def run_ours(args):
@@ -336,6 +392,13 @@ def run_ours(args):
             learned = learned_leg(vol, tf, cam, step, plain, max(3, min(args.steps, 50)), args.learned, flush,
                                   stream)
 
+    serving = None
+    if args.serve != "off" and ws == 1:
+        modes = ["plain", "learned"] if args.serve == "both" else [args.serve]
+        if "learned" in modes and (learned is None or "_model" not in learned):
+            modes = [m for m in modes if m != "learned"]
+        serving = serving_leg(learned.get("_model") if learned else None, modes)
+
     # ---- end to end through the C ABI with host buffers ----
     host = torch.empty((HEIGHT, WIDTH, 4), dtype=torch.float32, pin_memory=True)
     e2e_steps = max(3, min(args.steps, 10))
@@ -377,7 +440,10 @@ def run_ours(args):
                       "forest_depth": [st["depth_min"], st["depth_max"], st["depth_mean"], st["depth_var"]],
                       "n_nodes": st["n_nodes"], "incidence_entries": st["incidence_entries"]}}
     if learned is not None:
+        learned.pop("_model", None)
         line["learned_step"] = learned
+    if serving is not None:
+        line["serving"] = serving
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(vol, tf, cam, step)
     print(json.dumps(line))
@@ -399,6 +465,8 @@ def main():
                     help="Bezier block storage (FP32 accumulation in every case)")
     ap.add_argument("--learned", default="f16", choices=["off", "f32", "f16", "bf16"],
                     help="also time learned step sizes with this block storage against plain FP32 Eq. 4")
+    ap.add_argument("--serve", default="both", choices=["off", "plain", "learned", "both"],
+                    help="frame-server runs over three resident volumes (learned needs --learned)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up frames
     if args.impl == "reference":

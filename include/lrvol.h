@@ -274,6 +274,115 @@ int lrvol_eval(lrvol_t vol, const float *pts_dev, int64_t n, float *val_dev, voi
  * x (p1+1) doubles, x index fastest.  Synchronous. */
 int lrvol_get_bezier(lrvol_t vol, double *host_out);
 
+/* ---------------------------------------------------------------------------
+ * Host-side arena bookkeeping (first fit, coalescing): offsets into a range
+ * of `bytes`, every block aligned to `align` (a power of two).  The frame
+ * server below carves its output images from one device allocation with it;
+ * the functions touch no device memory.  Not thread-safe.
+ * ------------------------------------------------------------------------- */
+typedef struct lrvol_arena_s *lrvol_arena_t;
+int lrvol_arena_create(int64_t bytes, int64_t align, lrvol_arena_t *out);
+/* Offset of a free block of at least `bytes` (the lowest that fits), or -1. */
+int64_t lrvol_arena_alloc(lrvol_arena_t a, int64_t bytes);
+/* Return a block by the offset lrvol_arena_alloc gave; LRVOL_ERR_ARG if none. */
+int lrvol_arena_free(lrvol_arena_t a, int64_t offset);
+/* Bytes in use (rounded up to the alignment) and the largest free block. */
+int64_t lrvol_arena_used(lrvol_arena_t a);
+int64_t lrvol_arena_largest_free(lrvol_arena_t a);
+void lrvol_arena_destroy(lrvol_arena_t a);
+
+/* ---------------------------------------------------------------------------
+ * Frame server: continuous batching of frame requests over resident volumes
+ * (the paper renders one interactive view; it has no counterpart).
+ *
+ * A server owns `slots` slots (each three CUDA streams of different
+ * priority, two events and statistics counters) and one device arena of `arena_bytes`
+ * for output images (and, for learned steps, per-frame features and
+ * multipliers).  lrvol_server_submit queues a request (FIFO) and returns at
+ * once.  lrvol_server_progress, called from the host loop, first retires the
+ * frames whose work has finished, then admits waiting requests in order
+ * while a slot is free and the arena holds the request's memory, launching
+ * each on its slot's stream: frames of different requests run concurrently
+ * on the device.  A request whose memory does not fit waits at the head of
+ * the queue (no overtaking) until retired frames free enough.  Results are
+ * identical to lrvol_render of the same request alone: the same kernel with
+ * the same parameters, and statistics counters of its own.
+ *
+ * All calls on one server must come from one host thread.  Volumes must stay
+ * alive while requests on them are queued or running.
+ * ------------------------------------------------------------------------- */
+typedef struct lrvol_server_s *lrvol_server_t;
+
+enum { LRVOL_REQ_QUEUED = 0, LRVOL_REQ_RUNNING = 1, LRVOL_REQ_DONE = 2, LRVOL_REQ_FAILED = 3 };
+
+typedef struct {
+  int32_t state;                 /* LRVOL_REQ_* */
+  int32_t status;                /* LRVOL_OK, or the error of a failed request */
+  const float *rgba_dev;         /* DONE: the image (height x width x 4) in the arena, until released;
+                                    NULL once released or when the request copied to host_out */
+  double t_submit, t_admit, t_done; /* lrvol_server_clock() at submission, launch, and when progress
+                                    saw the frame finished (0 while not reached) */
+  float device_ms;               /* between events recorded before and after the frame's work */
+  float dev_start_ms, dev_end_ms; /* those events relative to one recorded at server creation: frames
+                                    whose [start, end] intervals intersect ran concurrently */
+  int64_t samples, lookups, rays_hit; /* counters of this frame's render */
+  int64_t bytes;                 /* arena bytes the request holds while admitted */
+} lrvol_frame_info;
+
+typedef struct {
+  int64_t submitted, queued, running, done, failed;
+  int64_t arena_bytes, arena_used, arena_high_water;
+  int32_t slots, max_running;    /* max_running: most frames in flight at once so far */
+} lrvol_server_stats;
+
+/* slots 1..64, arena_bytes >= 1 MiB (allocated here, once).  The arena and
+ * the slot streams live until lrvol_server_destroy. */
+int lrvol_server_create(int32_t slots, int64_t arena_bytes, lrvol_server_t *out);
+/* Attach a learned step model for requests with mode LRVOL_STEP_LEARNED and
+ * mult == NULL: the server then runs lrvol_features and lrvol_mlp_infer for
+ * the request's volume and camera before its render, on the same stream, with
+ * the features and multipliers in the arena.  packed_dev (LRVOL_MLP_PACKED
+ * uint16, 16-byte aligned) stays caller-owned and must outlive the server. */
+int lrvol_server_set_step_model(lrvol_server_t s, const uint16_t *packed_dev, float ymax);
+/* Stream priority tiers by frame size: frames of at most max_pixels pixels
+ * run at the device's greatest stream priority, frames of at most
+ * 4 * max_pixels at a middle one, larger frames at the least, so the block
+ * scheduler dispatches the CTAs of smaller frames ahead of those of larger
+ * frames already running.  0 (the default) puts every frame in the last
+ * tier.  Each slot holds one stream per tier (3 x slots streams): a process
+ * that serves should set CUDA_DEVICE_MAX_CONNECTIONS to at least that many
+ * (at most 32) before its CUDA context exists, or streams share hardware
+ * queues and a small frame can wait behind a large one. */
+int lrvol_server_set_priority_pixels(lrvol_server_t s, int64_t max_pixels);
+/* Queue one frame.  cam, tf and step are copied.  host_out: NULL, or a host
+ * buffer (pinned for an asynchronous copy) of height x width x 4 floats that
+ * receives the image as part of the frame's work; the arena memory is then
+ * returned when the frame retires.  Without host_out the image stays in the
+ * arena until lrvol_server_release.  Errors: LRVOL_ERR_ARG for requests that
+ * fail lrvol_render's checks or that need more memory than the whole arena. */
+int lrvol_server_submit(lrvol_server_t s, lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf,
+                        const lrvol_step *step, float *host_out, int64_t *ticket);
+/* Retire finished frames, then admit and launch waiting requests.  Never
+ * waits for the device.  n_retired (may be NULL) receives the number of
+ * frames retired by this call. */
+int lrvol_server_progress(lrvol_server_t s, int32_t *n_retired);
+/* Block until every submitted request is done or failed (progress in a loop;
+ * waits on the oldest running frame's event between rounds). */
+int lrvol_server_drain(lrvol_server_t s);
+/* Tickets of requests that became done or failed since the previous call, in
+ * the order they were retired (at most max_n; the rest stay for the next
+ * call).  *n receives the count. */
+int lrvol_server_poll(lrvol_server_t s, int64_t *tickets, int32_t max_n, int32_t *n);
+int lrvol_server_info(lrvol_server_t s, int64_t ticket, lrvol_frame_info *info);
+/* Forget a finished request and return its arena memory (LRVOL_ERR_STATE while
+ * it is queued or running). */
+int lrvol_server_release(lrvol_server_t s, int64_t ticket);
+int lrvol_server_get_stats(lrvol_server_t s, lrvol_server_stats *out);
+/* The host clock of the t_* fields: seconds of a monotonic clock. */
+double lrvol_server_clock(void);
+/* Synchronises the slot streams, then frees the arena, streams and events. */
+void lrvol_server_destroy(lrvol_server_t s);
+
 /* Statistics of the forest and of the last render.  Synchronous; also
  * reports a pending device-side status (LRVOL_ERR_BOUNDS / _TIMEOUT). */
 int lrvol_stats(lrvol_t vol, lrvol_stats_t *out);

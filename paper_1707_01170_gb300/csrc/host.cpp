@@ -13,8 +13,10 @@
 using namespace lrvol;
 
 namespace {
-
 thread_local std::string g_last_error;
+}  // namespace
+
+namespace lrvol {
 
 int fail(int status, const std::string &msg) {
   g_last_error = msg;
@@ -26,11 +28,9 @@ int cuda_fail(cudaError_t e, const char *what) {
   return e == cudaErrorMemoryAllocation ? LRVOL_ERR_OOM : LRVOL_ERR_CUDA;
 }
 
-#define CU(call, what)                         \
-  do {                                         \
-    cudaError_t _e = (call);                   \
-    if (_e != cudaSuccess) return cuda_fail(_e, what); \
-  } while (0)
+}  // namespace lrvol
+
+namespace {
 
 template <class T>
 int dev_alloc(lrvol_s *v, T **p, size_t count, const char *what) {
@@ -300,6 +300,88 @@ ForestView forest_view(const lrvol_s *v) {
 
 }  // namespace lrvol
 
+namespace lrvol {
+
+// Checks of lrvol_render and the kernel parameters of a frame, except the
+// scratch pointers (counters, status), which the caller sets.
+int prepare_render(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                   float *rgba_dev, RenderParams *prm, int *field_out) {
+  if (!v || !cam || !tf || !step || !rgba_dev) return fail(LRVOL_ERR_ARG, "null pointer");
+  if (!v->have_bezier || !v->have_accel) return fail(LRVOL_ERR_STATE, "render needs to_bezier and build_accel");
+  if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+    return fail(LRVOL_ERR_ARG, "bad image size");
+  if (cam->projection != LRVOL_ORTHO && cam->projection != LRVOL_PERSP) return fail(LRVOL_ERR_ARG, "bad projection");
+  int r0 = cam->row_begin, r1 = cam->row_end;
+  if (r0 == 0 && r1 == 0) r1 = cam->height;
+  if (r0 < 0 || r1 > cam->height || r0 > r1) return fail(LRVOL_ERR_ARG, "bad row range");
+  if (step->mode != LRVOL_STEP_FIXED && step->mode != LRVOL_STEP_HEURISTIC && step->mode != LRVOL_STEP_LEARNED)
+    return fail(LRVOL_ERR_ARG, "bad step mode");
+  if (step->mode == LRVOL_STEP_LEARNED && !step->mult) return fail(LRVOL_ERR_ARG, "learned steps need multipliers");
+  if (step->mode == LRVOL_STEP_FIXED && !(step->h > 0)) return fail(LRVOL_ERR_ARG, "fixed step must be > 0");
+  if (!(step->xi > 0) || !(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "xi and vmax - vmin must be > 0");
+  int field = step->field;
+  if (field == LRVOL_FIELD_SCALAR && v->nc != 1) return fail(LRVOL_ERR_ARG, "scalar field needs ncomp = 1");
+  if (field == LRVOL_FIELD_MAGNITUDE && v->nc != 3) return fail(LRVOL_ERR_ARG, "magnitude needs ncomp = 3");
+  if (field == LRVOL_FIELD_COMPONENT && (step->component < 0 || step->component >= v->nc))
+    return fail(LRVOL_ERR_ARG, "bad component");
+  if (field < 0 || field > 2) return fail(LRVOL_ERR_ARG, "bad field");
+  if (v->p[0] != v->p[1] || v->p[0] != v->p[2] || v->p[0] > 3)
+    return fail(LRVOL_ERR_UNSUPPORTED, "render needs equal degrees 1..3");
+  std::memset(prm, 0, sizeof(*prm));
+  prm->elem = v->d_elem;
+  prm->n_elem = v->n_elem;
+  prm->bez = v->d_bez;
+  prm->elem_bytes = v->elem_bytes;
+  prm->bezc = v->d_bezc;
+  prm->elemc_bytes = v->elemc_bytes;
+  prm->comp = field == LRVOL_FIELD_COMPONENT ? step->component : 0;
+  prm->forest = forest_view(v);
+  prm->out = rgba_dev;
+  prm->width = cam->width;
+  prm->height = cam->height;
+  prm->row_begin = r0;
+  prm->row_end = r1;
+  camera_consts(cam, &prm->ray);
+  prm->mode = step->mode;
+  prm->mult = step->mult;
+  prm->h = (float)step->h;
+  prm->inv_xi = (float)(1.0 / step->xi);
+  prm->alpha_stop = (float)step->alpha_stop;
+  prm->tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
+  prm->tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
+  for (int q = 0; q < 256; ++q) prm->tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
+  *field_out = field;
+  return LRVOL_OK;
+}
+
+// Checks of lrvol_features and its kernel parameters.
+int prepare_features(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                     FeatureParams *fp) {
+  if (!v || !cam || !tf || !step) return fail(LRVOL_ERR_ARG, "null pointer");
+  if (!v->have_bezier) return fail(LRVOL_ERR_STATE, "features need to_bezier");
+  if (!(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "vmax - vmin must be > 0");
+  const int field = step->field;
+  if (field < 0 || field > 2 || (field == LRVOL_FIELD_SCALAR && v->nc != 1) ||
+      (field == LRVOL_FIELD_MAGNITUDE && v->nc != 3) ||
+      (field == LRVOL_FIELD_COMPONENT && (step->component < 0 || step->component >= v->nc)))
+    return fail(LRVOL_ERR_ARG, "bad field/component for this volume");
+  std::memset(fp, 0, sizeof(*fp));
+  fp->box = v->d_box;
+  fp->elem = v->d_elem;
+  fp->range = v->d_range;
+  fp->n_elem = v->n_elem;
+  fp->nc = v->nc;
+  fp->field = field;
+  fp->comp = step->component;
+  for (int a = 0; a < 3; ++a) fp->eye[a] = (float)cam->eye[a];
+  fp->tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
+  fp->tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
+  for (int q = 0; q < 256; ++q) fp->tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
+  return LRVOL_OK;
+}
+
+}  // namespace lrvol
+
 extern "C" {
 
 const char *lrvol_status_string(int s) {
@@ -465,56 +547,15 @@ int lrvol_to_bezier(lrvol_t v, int32_t storage, void *stream) {
 
 int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
                  float *rgba_dev, void *stream) {
-  if (!v || !cam || !tf || !step || !rgba_dev) return fail(LRVOL_ERR_ARG, "null pointer");
-  if (!v->have_bezier || !v->have_accel) return fail(LRVOL_ERR_STATE, "render needs to_bezier and build_accel");
-  if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
-    return fail(LRVOL_ERR_ARG, "bad image size");
-  if (cam->projection != LRVOL_ORTHO && cam->projection != LRVOL_PERSP) return fail(LRVOL_ERR_ARG, "bad projection");
-  int r0 = cam->row_begin, r1 = cam->row_end;
-  if (r0 == 0 && r1 == 0) r1 = cam->height;
-  if (r0 < 0 || r1 > cam->height || r0 > r1) return fail(LRVOL_ERR_ARG, "bad row range");
-  if (step->mode != LRVOL_STEP_FIXED && step->mode != LRVOL_STEP_HEURISTIC && step->mode != LRVOL_STEP_LEARNED)
-    return fail(LRVOL_ERR_ARG, "bad step mode");
-  if (step->mode == LRVOL_STEP_LEARNED && !step->mult) return fail(LRVOL_ERR_ARG, "learned steps need multipliers");
-  if (step->mode == LRVOL_STEP_FIXED && !(step->h > 0)) return fail(LRVOL_ERR_ARG, "fixed step must be > 0");
-  if (!(step->xi > 0) || !(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "xi and vmax - vmin must be > 0");
-  int field = step->field;
-  if (field == LRVOL_FIELD_SCALAR && v->nc != 1) return fail(LRVOL_ERR_ARG, "scalar field needs ncomp = 1");
-  if (field == LRVOL_FIELD_MAGNITUDE && v->nc != 3) return fail(LRVOL_ERR_ARG, "magnitude needs ncomp = 3");
-  if (field == LRVOL_FIELD_COMPONENT && (step->component < 0 || step->component >= v->nc))
-    return fail(LRVOL_ERR_ARG, "bad component");
-  if (field < 0 || field > 2) return fail(LRVOL_ERR_ARG, "bad field");
-  if (v->p[0] != v->p[1] || v->p[0] != v->p[2] || v->p[0] > 3)
-    return fail(LRVOL_ERR_UNSUPPORTED, "render needs equal degrees 1..3");
-  cudaStream_t st = (cudaStream_t)stream;
   RenderParams prm;
-  std::memset(&prm, 0, sizeof(prm));
-  prm.elem = v->d_elem;
-  prm.n_elem = v->n_elem;
-  prm.bez = v->d_bez;
-  prm.elem_bytes = v->elem_bytes;
-  prm.bezc = v->d_bezc;
-  prm.elemc_bytes = v->elemc_bytes;
-  prm.comp = field == LRVOL_FIELD_COMPONENT ? step->component : 0;
-  prm.forest = forest_view(v);
-  prm.out = rgba_dev;
-  prm.width = cam->width;
-  prm.height = cam->height;
-  prm.row_begin = r0;
-  prm.row_end = r1;
-  camera_consts(cam, &prm.ray);
-  prm.mode = step->mode;
-  prm.mult = step->mult;
-  prm.h = (float)step->h;
-  prm.inv_xi = (float)(1.0 / step->xi);
-  prm.alpha_stop = (float)step->alpha_stop;
-  prm.tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
-  prm.tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
+  int field = 0;
+  int rc = prepare_render(v, cam, tf, step, rgba_dev, &prm, &field);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
   prm.counters = v->d_counters;
   prm.status = v->d_status;
-  for (int q = 0; q < 256; ++q) prm.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
   CU(cudaMemsetAsync(v->d_counters, 0, sizeof(unsigned long long) * kNumCounters, st), "clear counters");
-  if (r1 > r0) CU(launch_render(prm, v->p[0], field, v->storage, st), "render kernel");
+  if (prm.row_end > prm.row_begin) CU(launch_render(prm, v->p[0], field, v->storage, st), "render kernel");
   return LRVOL_OK;
 }
 
@@ -578,27 +619,10 @@ int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf,
 
 int lrvol_features(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step, float *feat,
                    void *stream) {
-  if (!v || !cam || !tf || !step || !feat) return fail(LRVOL_ERR_ARG, "null pointer");
-  if (!v->have_bezier) return fail(LRVOL_ERR_STATE, "features need to_bezier");
-  if (!(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "vmax - vmin must be > 0");
-  const int field = step->field;
-  if (field < 0 || field > 2 || (field == LRVOL_FIELD_SCALAR && v->nc != 1) ||
-      (field == LRVOL_FIELD_MAGNITUDE && v->nc != 3) ||
-      (field == LRVOL_FIELD_COMPONENT && (step->component < 0 || step->component >= v->nc)))
-    return fail(LRVOL_ERR_ARG, "bad field/component for this volume");
+  if (!feat) return fail(LRVOL_ERR_ARG, "null pointer");
   FeatureParams fp;
-  std::memset(&fp, 0, sizeof(fp));
-  fp.box = v->d_box;
-  fp.elem = v->d_elem;
-  fp.range = v->d_range;
-  fp.n_elem = v->n_elem;
-  fp.nc = v->nc;
-  fp.field = field;
-  fp.comp = step->component;
-  for (int a = 0; a < 3; ++a) fp.eye[a] = (float)cam->eye[a];
-  fp.tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
-  fp.tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
-  for (int q = 0; q < 256; ++q) fp.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
+  int rc = prepare_features(v, cam, tf, step, &fp);
+  if (rc) return rc;
   CU(launch_features(fp, feat, (cudaStream_t)stream), "features kernel");
   return LRVOL_OK;
 }

@@ -200,6 +200,22 @@ struct FeatureParams {
 };
 
 cudaError_t launch_features(const FeatureParams &fp, float *out, cudaStream_t s);
+
+// host.cpp: error reporting (sets the thread's last error, returns the status)
+int fail(int status, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+// host.cpp: the checks and kernel parameters of lrvol_render (scratch
+// pointers left null) and of lrvol_features
+int prepare_render(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                   float *rgba_dev, RenderParams *prm, int *field_out);
+int prepare_features(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                     FeatureParams *fp);
+
+#define CU(call, what)                                        \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return ::lrvol::cuda_fail(_e, what); \
+  } while (0)
 cudaError_t launch_mlp_pack(const float *params, uint16_t *packed, cudaStream_t s);
 cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out, cudaStream_t s);
 cudaError_t launch_mlp_grad(const float *x, const float *target, int64_t n, const float *params, float *grad,

@@ -24,7 +24,13 @@ NONE = 0xFFFFFFFF
 EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
             "lrvol_eval", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
             "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features", "lrvol_mlp_pack", "lrvol_mlp_infer",
-            "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels"]
+            "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels",
+            "lrvol_arena_create", "lrvol_arena_alloc", "lrvol_arena_free", "lrvol_arena_used",
+            "lrvol_arena_largest_free", "lrvol_arena_destroy", "lrvol_server_create", "lrvol_server_set_step_model",
+            "lrvol_server_set_priority_pixels",
+            "lrvol_server_submit", "lrvol_server_progress", "lrvol_server_drain", "lrvol_server_poll", "lrvol_server_info",
+            "lrvol_server_release", "lrvol_server_get_stats", "lrvol_server_clock", "lrvol_server_destroy"]
+REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 MLP_IN, MLP_HIDDEN, MLP_PARAMS, MLP_PACKED = 16, 64, 9473, 10120
 
 
@@ -62,6 +68,27 @@ class Stats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["blocks"] = list(self.blocks)
         return d
+
+
+class FrameInfo(ctypes.Structure):
+    _fields_ = [("state", ctypes.c_int32), ("status", ctypes.c_int32), ("rgba_dev", ctypes.c_void_p),
+                ("t_submit", ctypes.c_double), ("t_admit", ctypes.c_double), ("t_done", ctypes.c_double),
+                ("device_ms", ctypes.c_float), ("dev_start_ms", ctypes.c_float), ("dev_end_ms", ctypes.c_float),
+                ("samples", ctypes.c_int64), ("lookups", ctypes.c_int64), ("rays_hit", ctypes.c_int64),
+                ("bytes", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class ServerStats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("queued", ctypes.c_int64), ("running", ctypes.c_int64),
+                ("done", ctypes.c_int64), ("failed", ctypes.c_int64), ("arena_bytes", ctypes.c_int64),
+                ("arena_used", ctypes.c_int64), ("arena_high_water", ctypes.c_int64), ("slots", ctypes.c_int32),
+                ("max_running", ctypes.c_int32)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
 
 
 _lib = None
@@ -115,6 +142,43 @@ def load(path: str = LIB_PATH):
         L.lrvol_labels.restype = ctypes.c_int
         L.lrvol_labels.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
                                    ctypes.c_double, ctypes.c_double, vp, i32, vp, vp]
+        L.lrvol_arena_create.restype = ctypes.c_int
+        L.lrvol_arena_create.argtypes = [i64, i64, ctypes.POINTER(vp)]
+        L.lrvol_arena_alloc.restype = i64
+        L.lrvol_arena_alloc.argtypes = [vp, i64]
+        L.lrvol_arena_free.restype = ctypes.c_int
+        L.lrvol_arena_free.argtypes = [vp, i64]
+        L.lrvol_arena_used.restype = i64
+        L.lrvol_arena_used.argtypes = [vp]
+        L.lrvol_arena_largest_free.restype = i64
+        L.lrvol_arena_largest_free.argtypes = [vp]
+        L.lrvol_arena_destroy.restype = None
+        L.lrvol_arena_destroy.argtypes = [vp]
+        L.lrvol_server_create.restype = ctypes.c_int
+        L.lrvol_server_create.argtypes = [i32, i64, ctypes.POINTER(vp)]
+        L.lrvol_server_set_step_model.restype = ctypes.c_int
+        L.lrvol_server_set_step_model.argtypes = [vp, vp, ctypes.c_float]
+        L.lrvol_server_set_priority_pixels.restype = ctypes.c_int
+        L.lrvol_server_set_priority_pixels.argtypes = [vp, i64]
+        L.lrvol_server_submit.restype = ctypes.c_int
+        L.lrvol_server_submit.argtypes = [vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
+                                          vp, ctypes.POINTER(i64)]
+        L.lrvol_server_progress.restype = ctypes.c_int
+        L.lrvol_server_progress.argtypes = [vp, ctypes.POINTER(i32)]
+        L.lrvol_server_drain.restype = ctypes.c_int
+        L.lrvol_server_drain.argtypes = [vp]
+        L.lrvol_server_poll.restype = ctypes.c_int
+        L.lrvol_server_poll.argtypes = [vp, vp, i32, ctypes.POINTER(i32)]
+        L.lrvol_server_info.restype = ctypes.c_int
+        L.lrvol_server_info.argtypes = [vp, i64, ctypes.POINTER(FrameInfo)]
+        L.lrvol_server_release.restype = ctypes.c_int
+        L.lrvol_server_release.argtypes = [vp, i64]
+        L.lrvol_server_get_stats.restype = ctypes.c_int
+        L.lrvol_server_get_stats.argtypes = [vp, ctypes.POINTER(ServerStats)]
+        L.lrvol_server_clock.restype = ctypes.c_double
+        L.lrvol_server_clock.argtypes = []
+        L.lrvol_server_destroy.restype = None
+        L.lrvol_server_destroy.argtypes = [vp]
         _lib = L
     return _lib
 
@@ -167,13 +231,15 @@ def make_tf(tf) -> TF:
     return t
 
 
-def make_step(step) -> Step:
+def make_step(step, allow_auto: bool = False) -> Step:
     """From any object with mode ('fixed'|'heuristic'|'learned'), field,
     component, h, xi, alpha_stop and, for learned steps, mult: a CUDA float32
-    tensor of one multiplier per element (kept alive by the caller)."""
+    tensor of one multiplier per element (kept alive by the caller).  With
+    allow_auto, a learned step may leave mult None (the frame server then
+    computes the multipliers with its step model)."""
     s = Step()
     s.mode = {"fixed": STEP_FIXED, "heuristic": STEP_HEURISTIC, "learned": STEP_LEARNED}[step.mode]
-    if step.mode == "learned":
+    if step.mode == "learned" and not (allow_auto and step.mult is None):
         m = step.mult
         if m is None or not getattr(m, "is_cuda", False) or not m.is_contiguous():
             raise ValueError("learned steps need a contiguous CUDA tensor of multipliers")
@@ -349,3 +415,129 @@ def labels(vol: "Volume", cam, tf, step, h_fine: float, tau: float, cand, label=
                                float(tau), _dev(cand_t), len(cand_t), _dev(label), _stream_ptr(stream)),
            "lrvol_labels")
     return label
+
+
+# ---- host arena and frame server ------------------------------------------
+
+class Arena:
+    """Host-side first-fit bookkeeping of offsets (lrvol_arena_*)."""
+
+    def __init__(self, nbytes: int, align: int = 256):
+        h = ctypes.c_void_p()
+        _check(load().lrvol_arena_create(int(nbytes), int(align), ctypes.byref(h)), "lrvol_arena_create")
+        self._h = h
+
+    def alloc(self, nbytes: int) -> int:
+        return int(load().lrvol_arena_alloc(self._h, int(nbytes)))
+
+    def free(self, offset: int) -> None:
+        _check(load().lrvol_arena_free(self._h, int(offset)), "lrvol_arena_free")
+
+    @property
+    def used(self) -> int:
+        return int(load().lrvol_arena_used(self._h))
+
+    @property
+    def largest_free(self) -> int:
+        return int(load().lrvol_arena_largest_free(self._h))
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lrvol_arena_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+class _DeviceArray:
+    """A borrowed device buffer exposed through __cuda_array_interface__."""
+
+    def __init__(self, ptr: int, shape):
+        self.__cuda_array_interface__ = {"shape": tuple(shape), "typestr": "<f4", "data": (int(ptr), False),
+                                         "version": 3, "strides": None}
+
+
+class Server:
+    """Frame server (lrvol_server_*): FIFO admission by free slot and arena
+    memory, frames of several requests in flight on separate streams."""
+
+    def __init__(self, slots: int = 8, arena_bytes: int = 1 << 30):
+        h = ctypes.c_void_p()
+        _check(load().lrvol_server_create(int(slots), int(arena_bytes), ctypes.byref(h)), "lrvol_server_create")
+        self._h = h
+        self._keep = {}   # ticket -> (camera, host buffer) kept alive while the request exists
+
+    def set_step_model(self, packed, ymax: float) -> None:
+        self._model = packed
+        _check(load().lrvol_server_set_step_model(self._h, _dev(packed), float(ymax)), "lrvol_server_set_step_model")
+
+    def set_priority_pixels(self, max_pixels: int) -> None:
+        _check(load().lrvol_server_set_priority_pixels(self._h, int(max_pixels)), "lrvol_server_set_priority_pixels")
+
+    def submit(self, vol: "Volume", cam, tf, step, host_out=None) -> int:
+        c = cam if isinstance(cam, Camera) else make_camera(cam)
+        t = tf if isinstance(tf, TF) else make_tf(tf)
+        s = step if isinstance(step, Step) else make_step(step, allow_auto=True)
+        ticket = ctypes.c_int64()
+        hp = None
+        if host_out is not None:
+            assert (not host_out.is_cuda) and host_out.is_contiguous() and host_out.numel() == c.width * c.height * 4
+            hp = host_out.data_ptr()
+        _check(load().lrvol_server_submit(self._h, vol.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), hp,
+                                          ctypes.byref(ticket)), "lrvol_server_submit")
+        self._keep[ticket.value] = (c.width, c.height, host_out, step)
+        return ticket.value
+
+    def progress(self) -> int:
+        n = ctypes.c_int32()
+        _check(load().lrvol_server_progress(self._h, ctypes.byref(n)), "lrvol_server_progress")
+        return n.value
+
+    def drain(self) -> None:
+        _check(load().lrvol_server_drain(self._h), "lrvol_server_drain")
+
+    def poll(self, max_n: int = 256) -> list:
+        """Tickets retired (done or failed) since the previous poll, in order."""
+        buf = (ctypes.c_int64 * max_n)()
+        n = ctypes.c_int32()
+        out = []
+        while True:
+            _check(load().lrvol_server_poll(self._h, buf, max_n, ctypes.byref(n)), "lrvol_server_poll")
+            out.extend(buf[:n.value])
+            if n.value < max_n:
+                return out
+
+    def info(self, ticket: int) -> dict:
+        fi = FrameInfo()
+        _check(load().lrvol_server_info(self._h, int(ticket), ctypes.byref(fi)), "lrvol_server_info")
+        return fi.as_dict()
+
+    def image(self, ticket: int):
+        """A copy (CUDA tensor, H x W x 4) of a finished frame still in the arena."""
+        import torch
+        d = self.info(ticket)
+        if d["state"] != REQ_DONE or not d["rgba_dev"]:
+            raise LrvolError(ERR_STATE, "image: frame not done or not in the arena")
+        w, h = self._keep[ticket][:2]
+        return torch.as_tensor(_DeviceArray(d["rgba_dev"], (h, w, 4)), device="cuda").clone()
+
+    def release(self, ticket: int) -> None:
+        _check(load().lrvol_server_release(self._h, int(ticket)), "lrvol_server_release")
+        self._keep.pop(ticket, None)
+
+    def stats(self) -> dict:
+        st = ServerStats()
+        _check(load().lrvol_server_get_stats(self._h, ctypes.byref(st)), "lrvol_server_get_stats")
+        return st.as_dict()
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().lrvol_server_destroy(self._h)
+            self._h = None
+
+    __del__ = close
+
+
+def clock() -> float:
+    """The server's host clock (seconds, monotonic)."""
+    return float(load().lrvol_server_clock())

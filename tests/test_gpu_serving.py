@@ -1,0 +1,134 @@
+"""The frame server on the GPU: every frame in a mixed, overlapping batch is
+identical (bit for bit, with the same sample counts) to the same request
+rendered alone by lrvol_render; admission respects the arena and FIFO order;
+frames really overlap on the device; host copies and server-side learned
+steps give the same images as the plain calls."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+from paper_1707_01170_gb300 import learned as LS
+from paper_1707_01170_gb300 import lrvol as lv
+from paper_1707_01170_gb300 import serve
+from paper_1707_01170_gb300.synth import volumes as V
+from paper_1707_01170_gb300.synth.lrgen import Stream
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    lv.load()
+
+
+@pytest.fixture(scope="module")
+def resident():
+    """Three resident volumes of different kinds, with TF and step each."""
+    v1 = V.load_config(1)
+    vec = V.refined_ball((2, 2, 2), (3, 3, 3), centres=((0.3, 0.6, 0.45),), radii=(0.4, 0.2), ncomp=3, seed=4)
+    tp = V.tensor_product((1, 1, 1), (5, 3, 4), seed=2)
+    gvs = [lv.Volume(v1).build_accel((32, 32, 32)).to_bezier(),
+           lv.Volume(vec).build_accel((16, 16, 16)).to_bezier(lv.STORE_F16),
+           lv.Volume(tp).build_accel((8, 8, 8)).to_bezier()]
+    tf1 = V.config1_render()[0]
+    tfv = V.seeded_tf(Stream(31), alpha_max=0.05)
+    tfv.vmin, tfv.vmax = 0.0, 1.6
+    tft = V.seeded_tf(Stream(33), alpha_max=0.1)
+    steps = [V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99),
+             V.StepParams(mode="heuristic", xi=1 / 128, field="magnitude"),
+             V.StepParams(mode="fixed", h=1 / 200, xi=1 / 256)]
+    yield gvs, [tf1, tfv, tft], steps
+    for g in gvs:
+        g.close()
+
+
+SMALL = ((64, 48), (200, 120), (333, 171))
+
+
+def test_mixed_batch_identical_to_alone(resident):
+    gvs, tfs, steps = resident
+    reqs = serve.request_stream(99, 36, 1000.0, 3, sizes=SMALL)
+    srv = lv.Server(slots=6, arena_bytes=64 << 20)
+    tickets = [srv.submit(gvs[r.volume], r.camera, tfs[r.volume], steps[r.volume]) for r in reqs]
+    srv.drain()
+    st = srv.stats()
+    assert st["done"] == len(reqs) and st["failed"] == 0 and st["max_running"] >= 2
+    infos = [srv.info(t) for t in tickets]
+    for r, t, d in zip(reqs, tickets, infos):
+        alone = gvs[r.volume].render(r.camera, tfs[r.volume], steps[r.volume])
+        ast = gvs[r.volume].stats()
+        mixed = srv.image(t)
+        assert torch.equal(mixed, alone), f"ticket {t}"
+        assert (d["samples"], d["lookups"], d["rays_hit"]) == (ast["samples"], ast["lookups"], ast["rays_hit"])
+    # frames overlapped on the device: some pair of [start, end] intervals intersects
+    iv = sorted((d["dev_start_ms"], d["dev_end_ms"]) for d in infos)
+    assert any(iv[k + 1][0] < iv[k][1] for k in range(len(iv) - 1))
+    for t in tickets:
+        srv.release(t)
+    assert srv.stats()["arena_used"] == 0
+    srv.close()
+
+
+def test_admission_by_memory_and_fifo(resident):
+    gvs, tfs, steps = resident
+    img = 512 * 512 * 16                               # 4 MiB per frame
+    srv = lv.Server(slots=8, arena_bytes=2 * img + img // 2)
+    cams = [serve.orbit_view(0, k, 1, 512, 512) for k in range(7)]
+    host = [torch.empty((512, 512, 4), dtype=torch.float32, pin_memory=True) for _ in cams]
+    tickets = [srv.submit(gvs[0], c, tfs[0], steps[0], host_out=h) for c, h in zip(cams, host)]
+    srv.drain()
+    st = srv.stats()
+    assert st["done"] == 7 and st["max_running"] <= 2 and st["arena_high_water"] <= 2 * img
+    assert st["arena_used"] == 0                       # host copies return the memory at retirement
+    admits = [srv.info(t)["t_admit"] for t in tickets]
+    assert admits == sorted(admits)
+    for c, h, t in zip(cams, host, tickets):
+        assert srv.info(t)["rgba_dev"] is None
+        assert torch.equal(h, gvs[0].render(c, tfs[0], steps[0]).cpu())
+        srv.release(t)
+    srv.close()
+
+
+def test_request_larger_than_arena_rejected(resident):
+    gvs, tfs, steps = resident
+    srv = lv.Server(slots=2, arena_bytes=1 << 20)
+    with pytest.raises(lv.LrvolError) as e:
+        srv.submit(gvs[0], serve.orbit_view(0, 0, 1, 512, 512), tfs[0], steps[0])
+    assert e.value.status == lv.ERR_ARG
+    with pytest.raises(lv.LrvolError):
+        srv.submit(gvs[0], serve.orbit_view(0, 0, 1, 64, 64), tfs[0], V.StepParams(mode="learned"))
+    srv.close()
+
+
+def test_server_learned_steps_match_manual(resident, cfg1):
+    gvs, tfs, steps = resident
+    model = LS.StepModel(LS.init_params(5), LS.TrainConfig(margin=-1.5))
+    srv = lv.Server(slots=3, arena_bytes=64 << 20)
+    srv.set_step_model(model.packed, model.cfg.ymax)
+    cams = [serve.orbit_view(0, k, 1, 160, 90) for k in range(5)]
+    lstep = V.StepParams(mode="learned", xi=1 / 256, alpha_stop=0.99)
+    tickets = [srv.submit(gvs[0], c, tfs[0], lstep) for c in cams]
+    srv.drain()
+    for c, t in zip(cams, tickets):
+        mult = model.multipliers(gvs[0], c, tfs[0], steps[0])
+        want = gvs[0].render(c, tfs[0], V.StepParams(mode="learned", xi=1 / 256, alpha_stop=0.99, mult=mult))
+        assert torch.equal(srv.image(t), want)
+        srv.release(t)
+    srv.close()
+
+
+def test_realtime_stream_latencies(resident, capsys):
+    gvs, tfs, steps = resident
+    reqs = serve.request_stream(5, 120, 400.0, 3, sizes=SMALL)
+    srv = lv.Server(slots=4, arena_bytes=64 << 20)
+    recs = serve.run_stream(srv, gvs, tfs, steps, reqs)
+    s = serve.summarize(recs)
+    with capsys.disabled():
+        print(f"\n[serving, small frames at 400 req/s] p50 {s['p50_ms']:.3f} ms, p99 {s['p99_ms']:.3f} ms, "
+              f"{s['frames_per_s']:.0f} frames/s, max in flight {srv.stats()['max_running']}")
+    assert s["frames"] == 120 and s["failed"] == 0
+    assert all(r["latency_ms"] >= 0 and r["done_s"] >= r["admit_s"] >= r["arrival_s"] - 1e-6 for r in recs)
+    srv.close()
