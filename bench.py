@@ -145,25 +145,44 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def cpu_baseline(vol, tf, cam, step, target_s: float = 12.0, seed: int = 11):
+def _core_model() -> str:
+    try:
+        for ln in open("/proc/cpuinfo"):
+            k, _, v = ln.partition(":")
+            if k.strip() in ("model name", "Model name", "CPU part") and v.strip():
+                return v.strip()
+    except OSError:
+        pass
+    import platform
+    return platform.machine()
+
+
+def cpu_baseline(vol, tf, cam, step, samples_per_frame=None, target_s: float = 12.0, seed: int = 11):
     """The FP64 oracle, as it stands, on a seeded pixel subset of the same
-    frame, sized to about target_s seconds of work on all host cores."""
+    frame, sized to about target_s seconds of work on all host cores; plus a
+    short one-thread run and the frame time extrapolated from the rate."""
     from oracle.oracle import Oracle
     rng = np.random.default_rng(seed)
     orc = Oracle(vol)
 
-    def run(n):
+    def run(n, threads=None):
         pix = np.stack([rng.integers(0, cam.width, n), rng.integers(0, cam.height, n)], axis=1).astype(np.int32)
         t0 = time.perf_counter()
-        _, st = orc.render(cam, tf, step, pixels=pix)
+        _, st = orc.render(cam, tf, step, pixels=pix, threads=threads)
         return st["samples"], time.perf_counter() - t0
 
     s0, d0 = run(256)
     n = int(min(40000, max(256, 256 * (target_s - d0) / max(d0, 1e-3))))
     s1, d1 = run(n)
     samples, dt = s0 + s1, d0 + d1
-    return {"value": samples / dt / 1e9, "unit": "Gsamples/s", "cores": orc.threads, "kind": "oracle",
-            "sample": f"{256 + n} seeded pixels of the same 1920x1080 frame ({samples} samples, {dt:.1f} s)"}
+    value = samples / dt / 1e9
+    s2, d2 = run(max(16, n // (4 * orc.threads)), threads=1)
+    out = {"value": value, "unit": "Gsamples/s", "cores": orc.threads, "kind": "oracle",
+           "core_model": _core_model(), "one_thread_value": s2 / d2 / 1e9, "us_per_sample": 1e6 * dt / samples,
+           "sample": f"{256 + n} seeded pixels of the same 1920x1080 frame ({samples} samples, {dt:.1f} s)"}
+    if samples_per_frame:
+        out["extrapolated_ms_per_frame"] = 1e3 * samples_per_frame / (value * 1e9)
+    return out
 
 
 def profiled_traffic():
@@ -213,11 +232,27 @@ def run_reference(args):
     return 0
 
 
-def learned_leg(vol, tf, cam, step, plain, steps: int, storage: str, flush, stream):
+def _timed_frames(fns, steps: int, flush, stream):
+    """Mean CUDA-event time (ms) of each callable in fns, run in order once
+    per frame for `steps` frames, the L2 flushed before each frame."""
+    import torch
+    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(len(fns) + 1)] for _ in range(steps)]
+    for k in range(steps):
+        flush.zero_()
+        evs[k][0].record(stream)
+        for q, fn in enumerate(fns):
+            fn()
+            evs[k][q + 1].record(stream)
+    torch.cuda.synchronize()
+    return [sum(e[q].elapsed_time(e[q + 1]) for e in evs) / steps for q in range(len(fns))]
+
+
+def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream):
     """Learned step sizes with reduced-precision blocks against the plain FP32
-    Eq. 4 renderer on the same frame: both images against the fine-step
-    (1/2048) reference, and the learned frame timed whole (features, BF16
-    network, render), L2 flushed between frames like the main loop."""
+    Eq. 4 renderer on the same frames (1920x1080 and 3840x2160): both images
+    against the fine-step (1/2048) reference, and the learned frame timed
+    whole (features, BF16 network, render), L2 flushed between frames like
+    the main loop."""
     import torch
     from paper_1707_01170_gb300 import learned as LS
     from paper_1707_01170_gb300 import lrvol as lv
@@ -233,45 +268,47 @@ def learned_leg(vol, tf, cam, step, plain, steps: int, storage: str, flush, stre
     train_s = time.perf_counter() - t0
     code = {"f32": lv.STORE_F32, "f16": lv.STORE_F16, "bf16": lv.STORE_BF16}[storage]
     gq = lv.Volume(vol).build_accel(BLOCKS, stream=stream).to_bezier(storage=code, stream=stream)
-    ccam, ctf = lv.make_camera(cam), lv.make_tf(tf)
-    fine = gv32.render(ccam, ctf, V.StepParams(mode="fixed", h=1 / 2048, xi=step.xi, alpha_stop=step.alpha_stop),
-                       stream=stream)
+    ctf = lv.make_tf(tf)
     feat = torch.empty((vol.n_elem, lv.MLP_IN), dtype=torch.float32, device="cuda")
     mult = torch.empty(vol.n_elem, dtype=torch.float32, device="cuda")
     lstep = lv.make_step(V.StepParams(mode="learned", xi=step.xi, alpha_stop=step.alpha_stop, field=step.field,
                                       component=step.component, mult=mult))
-    out = torch.empty_like(fine)
-
-    def frame():
-        model.multipliers(gq, ccam, ctf, step, feat=feat, out=mult, stream=stream)
-        gq.render(ccam, ctf, lstep, out=out, stream=stream)
-
-    for _ in range(3):
-        frame()
-    torch.cuda.synchronize()
-    samples = gq.stats()["samples"]
-    evs = [[torch.cuda.Event(enable_timing=True) for _ in range(3)] for _ in range(steps)]
-    for k in range(steps):
-        flush.zero_()
-        evs[k][0].record(stream)
-        model.multipliers(gq, ccam, ctf, step, feat=feat, out=mult, stream=stream)
-        evs[k][1].record(stream)
-        gq.render(ccam, ctf, lstep, out=out, stream=stream)
-        evs[k][2].record(stream)
-    torch.cuda.synchronize()
-    ms_mult = sum(a.elapsed_time(b) for a, b, _ in evs) / steps
-    ms_render = sum(b.elapsed_time(c) for _, b, c in evs) / steps
+    pstep = lv.make_step(step)
     rmse = lambda a, b: float(torch.sqrt(torch.mean((a.double() - b.double()) ** 2)))
-    res = {"storage": storage, "ms_per_frame": ms_mult + ms_render, "ms_multipliers": ms_mult,
-           "ms_render": ms_render, "samples_per_frame": samples, "rmse_vs_fine": rmse(out, fine),
-           "plain_f32_ms_per_frame": plain["ms"], "plain_f32_samples_per_frame": plain["samples"],
-           "plain_f32_rmse_vs_fine": rmse(plain["img"], fine),
-           "speedup_vs_plain_f32": plain["ms"] / (ms_mult + ms_render),
-           "fine_reference": "fixed step 1/2048, FP32 blocks, same alpha_stop",
-           "gpu_launches_per_frame": 3,
+    res = {"storage": storage, "fine_reference": "fixed step 1/2048, FP32 blocks, same alpha_stop",
+           "gpu_launches_per_frame": 3, "frames_timed": steps,
            "model": {"train_s": train_s, "rows": rows, "loss": losses[-1][1], "tau": model.cfg.tau,
                      "margin": model.cfg.margin, "ymax": model.cfg.ymax, "steps": model.cfg.steps,
-                     "recipe": "16 seeded 320x180 cameras on each of configs 1 and 2"}}
+                     "recipe": "16 seeded 320x180 cameras on each of configs 1 and 2"},
+           "by_resolution": {}}
+    for (w, h) in ((WIDTH, HEIGHT), (3840, 2160)):
+        ccam = lv.make_camera(V.config2_render(w, h, vol)[1])
+        fine = gv32.render(ccam, ctf, V.StepParams(mode="fixed", h=1 / 2048, xi=step.xi, alpha_stop=step.alpha_stop),
+                           stream=stream)
+        out = torch.empty_like(fine)
+        ref_img = torch.empty_like(fine)
+        if (w, h) == (WIDTH, HEIGHT):
+            ms_plain, samples_plain, ref_img = plain["ms"], plain["samples"], plain["img"]
+        else:
+            gv32.render(ccam, ctf, pstep, out=ref_img, stream=stream)
+            ms_plain = _timed_frames([lambda: gv32.render(ccam, ctf, pstep, out=ref_img, stream=stream)],
+                                     steps, flush, stream)[0]
+            samples_plain = gv32.stats()["samples"]
+        mult_fn = lambda: model.multipliers(gq, ccam, ctf, step, feat=feat, out=mult, stream=stream)
+        render_fn = lambda: gq.render(ccam, ctf, lstep, out=out, stream=stream)
+        for _ in range(3):
+            mult_fn()
+            render_fn()
+        torch.cuda.synchronize()
+        samples = gq.stats()["samples"]
+        ms_mult, ms_render = _timed_frames([mult_fn, render_fn], steps, flush, stream)
+        res["by_resolution"][f"{w}x{h}"] = {
+            "ms_per_frame": ms_mult + ms_render, "ms_multipliers": ms_mult, "ms_render": ms_render,
+            "samples_per_frame": samples, "rmse_vs_fine": rmse(out, fine),
+            "plain_f32_ms_per_frame": ms_plain, "plain_f32_samples_per_frame": samples_plain,
+            "plain_f32_rmse_vs_fine": rmse(ref_img, fine), "speedup_vs_plain_f32": ms_plain / (ms_mult + ms_render)}
+        del fine, out
+    res.update(res["by_resolution"][f"{WIDTH}x{HEIGHT}"])
     gq.close()
     res["_model"] = model
     return res
@@ -389,8 +426,7 @@ def run_ours(args):
     if args.learned != "off" and ws == 1 and step.field == "scalar":
         if args.storage == "f32":
             plain = {"gv32": gv, "ms": ms_per_step, "samples": samples_per_frame, "img": out.clone()}
-            learned = learned_leg(vol, tf, cam, step, plain, max(3, min(args.steps, 50)), args.learned, flush,
-                                  stream)
+            learned = learned_leg(vol, tf, step, plain, max(3, min(args.steps, 50)), args.learned, flush, stream)
 
     serving = None
     if args.serve != "off" and ws == 1:
@@ -445,7 +481,7 @@ def run_ours(args):
     if serving is not None:
         line["serving"] = serving
     if not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(vol, tf, cam, step)
+        line["cpu_baseline"] = cpu_baseline(vol, tf, cam, step, samples_per_frame)
     print(json.dumps(line))
     gv.close()
     if dist:

@@ -52,6 +52,7 @@ enum { LRVOL_ORTHO = 0, LRVOL_PERSP = 1 };
 enum { LRVOL_STEP_FIXED = 0, LRVOL_STEP_HEURISTIC = 1, LRVOL_STEP_LEARNED = 2 };
 enum { LRVOL_FIELD_SCALAR = 0, LRVOL_FIELD_MAGNITUDE = 1, LRVOL_FIELD_COMPONENT = 2 };
 enum { LRVOL_STORE_F32 = 0, LRVOL_STORE_F16 = 1, LRVOL_STORE_BF16 = 2 };
+enum { LRVOL_SHADE_NONE = 0, LRVOL_SHADE_GRADIENT = 1 };
 
 /* Camera.  Ray of pixel (i, j), row j = 0 at the top, in FP32 with this exact
  * order of operations (fmaf = fused multiply-add, all other ops IEEE-rounded):
@@ -90,11 +91,16 @@ typedef struct {
  *              d = max(p1,p2,p3), e_k the element holding sample k (Eq. 4)
  *   LEARNED:   t_{k+1} = t_k + ds(e_k) * mult[e_k] (one FP32 product), with
  *              mult a caller-owned device array of one multiplier per element
- *              (e.g. from lrvol_learned_multipliers); Eq. 4 when all are 1
+ *              (e.g. from lrvol_features and lrvol_mlp_infer); Eq. 4 when all are 1
  * Sample k sits at p_k = clamp(fmaf(t_k, d, o), 0, 1); its segment is
  * min(t_{k+1}, t_out) - t_k; T = (1 - alpha_src)^(segment/xi);
  * C += (1-T)(1-alpha) C_src; alpha += (1-T)(1-alpha); the ray stops at
- * t_out or once alpha >= alpha_stop.  Output is premultiplied RGBA. */
+ * t_out or once alpha >= alpha_stop.  Output is premultiplied RGBA.
+ * Gradient shading (Sec. 4.1, scalar fields): C_src is multiplied by
+ * I = max(0.4, |l . n|), with n = grad f / max(|grad f|, eps) at the sample,
+ * eps = 1e-3 (vmax - vmin) (a gradient below eps counts as none, and I
+ * tends to 0.4 continuously), and l the unit vector towards the light:
+ * `light` normalised, or -d (a light at the eye) when `light` is all zero. */
 typedef struct {
   int32_t mode;      /* LRVOL_STEP_FIXED | LRVOL_STEP_HEURISTIC | LRVOL_STEP_LEARNED */
   int32_t field;     /* LRVOL_FIELD_SCALAR | _MAGNITUDE (|v| of a 3-vector) | _COMPONENT */
@@ -103,6 +109,8 @@ typedef struct {
   double xi;         /* reference length xi of Alg. 2 (T = (1 - alpha)^(segment / xi)) */
   double alpha_stop; /* early ray termination threshold; 1.0 = only when fully opaque */
   const float *mult; /* LEARNED: n_elem step multipliers (device), read during the render */
+  int32_t shading;   /* LRVOL_SHADE_NONE | LRVOL_SHADE_GRADIENT (scalar fields only) */
+  double light[3];   /* GRADIENT: direction towards the light (any length); all zero = -ray direction */
 } lrvol_step;
 
 /* Diagnostics; the depth rows match the paper's tables (Sec. 4.3). */
@@ -269,6 +277,14 @@ int lrvol_lookup(lrvol_t vol, const float *pts_dev, int64_t n, uint32_t *elem_de
 /* Field values (Eq. 2 through the Bezier blocks, FP32) at n FP32 points into
  * val_dev (n x ncomp floats, device).  Needs build_accel and to_bezier. */
 int lrvol_eval(lrvol_t vol, const float *pts_dev, int64_t n, float *val_dev, void *stream);
+
+/* Value and gradient of a scalar volume at n points (device, n x 3 floats):
+ * val_grad_dev n x 4 floats (f, df/dx, df/dy, df/dz), evaluated from the
+ * element's render block as the renderer's gradient shading does (the
+ * derivative of the Bezier tensor polynomial, scaled by 1/(hi - lo) per
+ * axis).  Points outside [0,1]^3 give zeros.  LRVOL_ERR_UNSUPPORTED for
+ * vector volumes. */
+int lrvol_eval_grad(lrvol_t vol, const float *pts_dev, int64_t n, float *val_grad_dev, void *stream);
 
 /* Copy the FP64 Bezier blocks to host_out: n_elem x ncomp x (p3+1) x (p2+1)
  * x (p1+1) doubles, x index fastest.  Synchronous. */

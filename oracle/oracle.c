@@ -84,6 +84,18 @@ double orc_bspline(const double *xi, int p, double x) {
   return N[0];
 }
 
+/* Derivative of the B-spline above: the textbook recurrence
+ * B'_p = p (B_{p-1}[xi_0..xi_p] / (xi_p - xi_0) - B_{p-1}[xi_1..xi_{p+1}] / (xi_{p+1} - xi_1)),
+ * a term with a zero denominator dropped.  At a knot it is the derivative
+ * of the piece on the right (half-open intervals, as for the value). */
+double orc_bspline_d1(const double *xi, int p, double x) {
+  if (p == 0) return 0.0;
+  double d = 0.0;
+  if (xi[p] != xi[0]) d += orc_bspline(xi, p - 1, x) / (xi[p] - xi[0]);
+  if (xi[p + 1] != xi[1]) d -= orc_bspline(xi + 1, p - 1, x) / (xi[p + 1] - xi[1]);
+  return (double)p * d;
+}
+
 orc_vol *orc_create(const int *deg, int nc, int64_t n_elem, const double *box, int64_t n_basis,
                     const double *knots, const double *coef, const double *weight) {
   for (int a = 0; a < 3; ++a)
@@ -168,6 +180,46 @@ static void eval_with(const orc_vol *v, const int64_t *inc, int64_t ninc, const 
   }
 }
 
+/* Eq. 2 and its gradient at x: grad[3*c + a] = d f_c / d x_a, each factor
+ * differentiated by orc_bspline_d1 (product rule over the three axes). */
+static void eval_grad_with(const orc_vol *v, const int64_t *inc, int64_t ninc, const double *x, double *val,
+                           double *grad) {
+  for (int c = 0; c < v->nc; ++c) {
+    val[c] = 0.0;
+    grad[3 * c] = grad[3 * c + 1] = grad[3 * c + 2] = 0.0;
+  }
+  for (int64_t q = 0; q < ninc; ++q) {
+    int64_t i = inc[q];
+    double B[3], D[3];
+    for (int a = 0; a < 3; ++a) {
+      B[a] = orc_bspline(knots_of(v, i, a), v->p[a], x[a]);
+      D[a] = orc_bspline_d1(knots_of(v, i, a), v->p[a], x[a]);
+    }
+    const double g = v->weight[i];
+    const double N = g * B[0] * B[1] * B[2];
+    const double dN[3] = {g * D[0] * B[1] * B[2], g * B[0] * D[1] * B[2], g * B[0] * B[1] * D[2]};
+    for (int c = 0; c < v->nc; ++c) {
+      const double cc = v->coef[i * v->nc + c];
+      val[c] += cc * N;
+      for (int a = 0; a < 3; ++a) grad[3 * c + a] += cc * dN[a];
+    }
+  }
+}
+
+/* f(x) and its gradient (grad: 3 x nc, component-major).  Returns the element id. */
+uint32_t orc_eval_grad(const orc_vol *v, const double *x, double *val, double *grad) {
+  uint32_t e = orc_find_element(v, x);
+  if (e == ORC_NONE) {
+    for (int c = 0; c < v->nc; ++c) val[c] = grad[3 * c] = grad[3 * c + 1] = grad[3 * c + 2] = 0.0;
+    return e;
+  }
+  int64_t *inc = (int64_t *)malloc(sizeof(int64_t) * v->n_basis);
+  int64_t n = orc_incidence(v, e, inc);
+  eval_grad_with(v, inc, n, x, val, grad);
+  free(inc);
+  return e;
+}
+
 /* f(x) (Eq. 2).  Returns the element id, ORC_NONE (and zeros) outside the domain. */
 uint32_t orc_eval(const orc_vol *v, const double *x, double *out) {
   uint32_t e = orc_find_element(v, x);
@@ -193,6 +245,7 @@ typedef struct {
   int tid, nth;
   uint32_t *elem;
   double *val;
+  double *grad; /* with val: n x 3 x nc gradients */
 } batch_job;
 
 static void *batch_worker(void *arg) {
@@ -209,13 +262,18 @@ static void *batch_worker(void *arg) {
     if (j->val) {
       if (e == ORC_NONE) {
         for (int c = 0; c < v->nc; ++c) j->val[q * v->nc + c] = 0.0;
+        if (j->grad)
+          for (int c = 0; c < 3 * v->nc; ++c) j->grad[q * 3 * v->nc + c] = 0.0;
         continue;
       }
       if (e != cur) {
         ninc = orc_incidence(v, e, inc);
         cur = e;
       }
-      eval_with(v, inc, ninc, x, j->val + q * v->nc);
+      if (j->grad)
+        eval_grad_with(v, inc, ninc, x, j->val + q * v->nc, j->grad + q * 3 * v->nc);
+      else
+        eval_with(v, inc, ninc, x, j->val + q * v->nc);
     }
   }
   free(inc);
@@ -239,19 +297,31 @@ static void run_batch(batch_job *proto, int nth) {
 
 /* Element ids of n FP32 points (n x 3). */
 void orc_lookup_batch(const orc_vol *v, const float *pts, int64_t n, uint32_t *elem, int nth) {
-  batch_job j = {v, pts, NULL, n, 0, 1, elem, NULL};
+  batch_job j = {v, pts, NULL, n, 0, 1, elem, NULL, NULL};
   run_batch(&j, nth);
 }
 
 /* f at n FP32 points (val: n x nc) and their element ids (may be NULL). */
 void orc_eval_batch_f32(const orc_vol *v, const float *pts, int64_t n, double *val, uint32_t *elem, int nth) {
-  batch_job j = {v, pts, NULL, n, 0, 1, elem, val};
+  batch_job j = {v, pts, NULL, n, 0, 1, elem, val, NULL};
+  run_batch(&j, nth);
+}
+
+/* f and its gradient at n FP32 points (val: n x nc, grad: n x nc x 3). */
+void orc_eval_grad_batch_f32(const orc_vol *v, const float *pts, int64_t n, double *val, double *grad, int nth) {
+  batch_job j = {v, pts, NULL, n, 0, 1, NULL, val, grad};
+  run_batch(&j, nth);
+}
+
+/* f and its gradient at n FP64 points. */
+void orc_eval_grad_batch_f64(const orc_vol *v, const double *pts, int64_t n, double *val, double *grad, int nth) {
+  batch_job j = {v, NULL, pts, n, 0, 1, NULL, val, grad};
   run_batch(&j, nth);
 }
 
 /* f at n FP64 points. */
 void orc_eval_batch_f64(const orc_vol *v, const double *pts, int64_t n, double *val, uint32_t *elem, int nth) {
-  batch_job j = {v, NULL, pts, n, 0, 1, elem, val};
+  batch_job j = {v, NULL, pts, n, 0, 1, elem, val, NULL};
   run_batch(&j, nth);
 }
 
@@ -277,6 +347,8 @@ typedef struct {
   int32_t component;
   double h, xi, alpha_stop;
   const float *mult; /* mode 2: per-element step multipliers (FP32) */
+  int32_t shading;   /* 1: gradient shading of C_src (Sec. 4.1) */
+  double light[3];   /* towards the light; all zero: towards the eye along the ray */
 } orc_step;
 
 typedef struct {
@@ -435,7 +507,35 @@ static void *render_worker(void *arg) {
       }
       if (!(tn > t)) tn = nextafterf(t, INFINITY);
       double seg = (double)fminf(tn, tout) - (double)t;
-      eval_with(v, inc, ninc, x, val);
+      double shade = 1.0;
+      if (J->st->shading) {
+        /* I = max(0.4, |l . n|), l the unit vector towards the light */
+        double g[9];
+        eval_grad_with(v, inc, ninc, x, val, g);
+        double l[3], ll = 0.0, gl = 0.0, gg = 0.0;
+        for (int c = 0; c < 3; ++c) {
+          l[c] = J->st->light[c];
+          ll += l[c] * l[c];
+        }
+        if (ll == 0.0)
+          for (int c = 0; c < 3; ++c) {
+            l[c] = -(double)d[c];
+            ll += l[c] * l[c];
+          }
+        for (int c = 0; c < 3; ++c) {
+          gl += l[c] * g[c];
+          gg += g[c] * g[c];
+        }
+        /* |grad f| below eps = 1e-3 (vmax - vmin) counts as no gradient, continuously:
+           n = grad f / max(|grad f|, eps) */
+        const double eps = 1e-3 * (J->tf->vmax - J->tf->vmin);
+        double gn = sqrt(gg);
+        if (gn < eps) gn = eps;
+        shade = fabs(gl) / (gn * sqrt(ll));
+        if (shade < 0.4) shade = 0.4;
+      } else {
+        eval_with(v, inc, ninc, x, val);
+      }
       double s;
       if (J->st->field == 1)
         s = sqrt(val[0] * val[0] + val[1] * val[1] + val[2] * val[2]);
@@ -448,7 +548,7 @@ static void *render_worker(void *arg) {
       /* Alg. 2 */
       double T = pow(1.0 - src[3], seg / J->st->xi);
       double w = (1.0 - T) * (1.0 - A);
-      for (int c = 0; c < 3; ++c) C[c] += w * src[c];
+      for (int c = 0; c < 3; ++c) C[c] += w * shade * src[c];
       A += w;
       J->stats.samples++;
       ++k;

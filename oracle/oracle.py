@@ -72,7 +72,7 @@ class _TF(ctypes.Structure):
 class _Step(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("field", ctypes.c_int32), ("component", ctypes.c_int32),
                 ("h", ctypes.c_double), ("xi", ctypes.c_double), ("alpha_stop", ctypes.c_double),
-                ("mult", ctypes.c_void_p)]
+                ("mult", ctypes.c_void_p), ("shading", ctypes.c_int32), ("light", ctypes.c_double * 3)]
 
 
 class _Stats(ctypes.Structure):
@@ -100,6 +100,10 @@ def _load():
         L.orc_lookup_batch.argtypes = [vp, vp, i64, vp, i32]
         L.orc_eval_batch_f32.argtypes = [vp, vp, i64, vp, vp, i32]
         L.orc_eval_batch_f64.argtypes = [vp, vp, i64, vp, vp, i32]
+        L.orc_eval_grad_batch_f32.argtypes = [vp, vp, i64, vp, vp, i32]
+        L.orc_eval_grad_batch_f64.argtypes = [vp, vp, i64, vp, vp, i32]
+        L.orc_bspline_d1.restype = ctypes.c_double
+        L.orc_bspline_d1.argtypes = [vp, i32, ctypes.c_double]
         L.orc_heuristic_step.restype = ctypes.c_float
         L.orc_heuristic_step.argtypes = [vp, ctypes.c_uint32]
         L.orc_render.argtypes = [vp, ctypes.POINTER(_Cam), ctypes.POINTER(_TF), ctypes.POINTER(_Step),
@@ -121,6 +125,13 @@ def bspline(knots, p: int, x: float) -> float:
     k = np.ascontiguousarray(knots, dtype=np.float64)
     assert k.shape == (p + 2,)
     return float(_load().orc_bspline(k.ctypes.data, int(p), float(x)))
+
+
+def bspline_d1(knots, p: int, x: float) -> float:
+    """Its derivative (right-hand at knots)."""
+    k = np.ascontiguousarray(knots, dtype=np.float64)
+    assert k.shape == (p + 2,)
+    return float(_load().orc_bspline_d1(k.ctypes.data, int(p), float(x)))
 
 
 def _cam(c) -> _Cam:
@@ -210,6 +221,22 @@ class Oracle:
             L.orc_eval_batch_f64(self._h, p.ctypes.data, len(p), val.ctypes.data, elem.ctypes.data, self.threads)
         return (val, elem) if return_elem else val
 
+    def eval_grad(self, pts):
+        """f and its gradient at points: (val (n, nc), grad (n, nc, 3)), FP64,
+        from Eq. 2 with each univariate factor differentiated (orc_bspline_d1)."""
+        pts = np.asarray(pts)
+        n = pts.reshape(-1, 3).shape[0]
+        val = np.empty((n, self.nc), dtype=np.float64)
+        grad = np.empty((n, self.nc, 3), dtype=np.float64)
+        L = _load()
+        if pts.dtype == np.float32:
+            p = np.ascontiguousarray(pts).reshape(-1, 3)
+            L.orc_eval_grad_batch_f32(self._h, p.ctypes.data, n, val.ctypes.data, grad.ctypes.data, self.threads)
+        else:
+            p = np.ascontiguousarray(pts, dtype=np.float64).reshape(-1, 3)
+            L.orc_eval_grad_batch_f64(self._h, p.ctypes.data, n, val.ctypes.data, grad.ctypes.data, self.threads)
+        return val, grad
+
     def heuristic_step(self, e: int) -> float:
         return float(_load().orc_heuristic_step(self._h, int(e)))
 
@@ -261,6 +288,9 @@ class Oracle:
         s.field = {"scalar": 0, "magnitude": 1, "component": 2}[step.field]
         s.component = int(step.component)
         s.h, s.xi, s.alpha_stop = float(step.h), float(step.xi), float(step.alpha_stop)
+        s.shading = {"none": 0, "gradient": 1}[getattr(step, "shading", "none")]
+        for a, x in enumerate(getattr(step, "light", (0.0, 0.0, 0.0))):
+            s.light[a] = float(x)
         c = _cam(cam)
         st = _Stats()
         if pixels is None:

@@ -19,10 +19,11 @@ ORTHO, PERSP = 0, 1
 STEP_FIXED, STEP_HEURISTIC, STEP_LEARNED = 0, 1, 2
 FIELD_SCALAR, FIELD_MAGNITUDE, FIELD_COMPONENT = 0, 1, 2
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
+SHADE_NONE, SHADE_GRADIENT = 0, 1
 NONE = 0xFFFFFFFF
 
 EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
-            "lrvol_eval", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
+            "lrvol_eval", "lrvol_eval_grad", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
             "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features", "lrvol_mlp_pack", "lrvol_mlp_infer",
             "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels",
             "lrvol_arena_create", "lrvol_arena_alloc", "lrvol_arena_free", "lrvol_arena_used",
@@ -54,7 +55,7 @@ class TF(ctypes.Structure):
 class Step(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("field", ctypes.c_int32), ("component", ctypes.c_int32),
                 ("h", ctypes.c_double), ("xi", ctypes.c_double), ("alpha_stop", ctypes.c_double),
-                ("mult", ctypes.c_void_p)]
+                ("mult", ctypes.c_void_p), ("shading", ctypes.c_int32), ("light", ctypes.c_double * 3)]
 
 
 class Stats(ctypes.Structure):
@@ -117,6 +118,8 @@ def load(path: str = LIB_PATH):
         L.lrvol_lookup.argtypes = [vp, vp, i64, vp, vp]
         L.lrvol_eval.restype = ctypes.c_int
         L.lrvol_eval.argtypes = [vp, vp, i64, vp, vp]
+        L.lrvol_eval_grad.restype = ctypes.c_int
+        L.lrvol_eval_grad.argtypes = [vp, vp, i64, vp, vp]
         L.lrvol_get_bezier.restype = ctypes.c_int
         L.lrvol_get_bezier.argtypes = [vp, vp]
         L.lrvol_stats.restype = ctypes.c_int
@@ -247,6 +250,9 @@ def make_step(step, allow_auto: bool = False) -> Step:
     s.field = {"scalar": FIELD_SCALAR, "magnitude": FIELD_MAGNITUDE, "component": FIELD_COMPONENT}[step.field]
     s.component = int(step.component)
     s.h, s.xi, s.alpha_stop = float(step.h), float(step.xi), float(step.alpha_stop)
+    s.shading = {"none": SHADE_NONE, "gradient": SHADE_GRADIENT}[getattr(step, "shading", "none")]
+    for a, x in enumerate(getattr(step, "light", (0.0, 0.0, 0.0))):
+        s.light[a] = float(x)
     return s
 
 
@@ -319,6 +325,17 @@ class Volume:
         if out is None:
             out = torch.empty((n, self.ncomp), dtype=torch.float32, device=pts.device)
         _check(load().lrvol_eval(self._h, pts.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)), "lrvol_eval")
+        return out
+
+    def eval_grad(self, pts, out=None, stream=None):
+        """(n, 4) float32 CUDA tensor: value and gradient of a scalar volume."""
+        import torch
+        assert pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous() and pts.shape[-1] == 3
+        n = pts.numel() // 3
+        if out is None:
+            out = torch.empty((n, 4), dtype=torch.float32, device=pts.device)
+        _check(load().lrvol_eval_grad(self._h, pts.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)),
+               "lrvol_eval_grad")
         return out
 
     def get_bezier(self) -> np.ndarray:

@@ -59,6 +59,8 @@ class StepParams:
     field: str = "scalar"    # "scalar" | "magnitude" | "component"
     component: int = 0
     mult: object = None      # learned: per-element step multipliers (array or device tensor)
+    shading: str = "none"    # "none" | "gradient" (scalar fields: C_src times max(0.4, |l . n|))
+    light: tuple = (0.0, 0.0, 0.0)   # towards the light; zero = from the eye
 
 
 def seeded_tf(stream: Stream, n_ctrl: int = 8, alpha_max: float = 0.08, bands=()) -> TransferFunction:

@@ -3,8 +3,8 @@
 Each case edits one line of oracle.c (a dropped term, a wrong index or sign,
 a transposed axis, an off-by-one), builds the edited copy on the CPU into a
 temporary directory, points the oracle module at it, and runs the pins of
-test_oracle_pins and the label pins of test_oracle_learned; at least one
-must fail.  The default build is restored
+test_oracle_pins, the label pins of test_oracle_learned and the gradient and
+shading pins of test_oracle_shading; at least one must fail.  The default build is restored
 afterwards.  No GPU is involved.
 """
 import os
@@ -13,6 +13,7 @@ import pytest
 import oracle.oracle as orc
 
 import test_oracle_learned as L
+import test_oracle_shading as S
 import test_oracle_pins as P
 
 SRC = os.path.join(os.path.dirname(orc.__file__), "oracle.c")
@@ -64,6 +65,13 @@ MUTANTS = [
      "if (!(err <= J->tau)) break;"),
     ("labels compare candidates with the Eq. 4 step", "float s = ds * J->cand[c], tc = t;",
      "float s = ds, tc = t;"),
+    ("B-spline derivative without the factor p", "return (double)p * d;", "return d;"),
+    ("B-spline derivative adds the right term",
+     "if (xi[p + 1] != xi[1]) d -= orc_bspline(xi + 1, p - 1, x) / (xi[p + 1] - xi[1]);",
+     "if (xi[p + 1] != xi[1]) d += orc_bspline(xi + 1, p - 1, x) / (xi[p + 1] - xi[1]);"),
+    ("gradient differentiates y for x", "{g * D[0] * B[1] * B[2],", "{g * B[0] * D[1] * B[2],"),
+    ("shading ignores the light vector", "l[c] = J->st->light[c];", "l[c] = 0.0;"),
+    ("shading without the 0.4 floor", "if (shade < 0.4) shade = 0.4;", ""),
 ]
 
 
@@ -93,6 +101,11 @@ def _pins(cfg1):
     yield lambda: L.test_labels_monotone_in_tau(cfg1, O)
     yield lambda: L.test_labels_count_what_the_last_step_skips()
     yield lambda: L.test_labels_weigh_errors_by_front_transmittance()
+    yield lambda: S.test_bspline_derivative_matches_scipy()
+    yield lambda: S.test_gradient_of_reproduced_polynomials((2, 2, 2), ([0.1, -1.0, 2.0], [0.2, 0.5, -0.3],
+                                                                        [1.0, 0.0, 1.0]))
+    yield lambda: S.test_shading_of_a_constant_field_is_0p4(cfg1)
+    yield lambda: S.test_shading_closed_forms_linear_field()
 
 
 def test_unmutated_source_passes_the_same_pins(cfg1):
