@@ -65,6 +65,15 @@ WORKLOADS = {
 }
 
 
+def flop_per_sample_shaded(p: int) -> int:
+    """Gradient-shaded scalar sample: the scalar sample, plus the gradient
+    contraction 2*((p+1)^3 + 2(p+1)^2 + 3(p+1)) reusing the value's partial
+    sums, derivative monomials 3*(2p+1), world scaling 3, I = max(0.4, |l.g|/|g|)
+    15, and the shaded colour weight 1."""
+    n = p + 1
+    return flop_per_sample(p, "scalar") + 2 * (n ** 3 + 2 * n ** 2 + 3 * n) + 3 * (2 * p + 1) + 3 + 15 + 1
+
+
 def flop_per_sample(p: int, field: str) -> int:
     """Algorithmic FP32 flops per composited sample (an FMA counts 2): sample
     position 12, local coordinates 9, monomial basis 3*(2p+1) (p=3: 21),
@@ -428,6 +437,25 @@ def run_ours(args):
             plain = {"gv32": gv, "ms": ms_per_step, "samples": samples_per_frame, "img": out.clone()}
             learned = learned_leg(vol, tf, step, plain, max(3, min(args.steps, 50)), args.learned, flush, stream)
 
+    shading = None
+    if ws == 1 and step.field == "scalar" and args.workload == "cfg2":
+        from paper_1707_01170_gb300.synth import volumes as V
+        sstep = lv.make_step(V.StepParams(mode="heuristic", xi=step.xi, alpha_stop=step.alpha_stop,
+                                          shading="gradient"))
+        for _ in range(3):
+            gv.render(ccam, ctf, sstep, out=out, stream=stream)
+        torch.cuda.synchronize()
+        s_samples = gv.stats()["samples"]
+        n_sh = max(3, min(args.steps, 50))
+        ms_sh = _timed_frames([lambda: gv.render(ccam, ctf, sstep, out=out, stream=stream)], n_sh, flush, stream)[0]
+        fps_sh = flop_per_sample_shaded(int(vol.deg[0]))
+        ach = fps_sh * s_samples / (ms_sh / 1e3) / 1e12
+        shading = {"what": "gradient shading (Sec. 4.1), light at the eye, same frame and storage",
+                   "ms_per_frame": ms_sh, "samples_per_frame": s_samples,
+                   "gsamples_per_s": s_samples / (ms_sh / 1e3) / 1e9, "flop_per_sample": fps_sh,
+                   "achieved_tflops": ach, "frac_of_fp32_peak": ach / FP32_PEAK_TFLOPS, "frames_timed": n_sh,
+                   "kernel": f"k_render<{int(vol.deg[0])},3,{args.storage}>"}
+
     serving = None
     if args.serve != "off" and ws == 1:
         modes = ["plain", "learned"] if args.serve == "both" else [args.serve]
@@ -478,6 +506,8 @@ def run_ours(args):
     if learned is not None:
         learned.pop("_model", None)
         line["learned_step"] = learned
+    if shading is not None:
+        line["shading"] = shading
     if serving is not None:
         line["serving"] = serving
     if not args.no_cpu_baseline:

@@ -327,6 +327,13 @@ int prepare_render(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *tf
   if (field < 0 || field > 2) return fail(LRVOL_ERR_ARG, "bad field");
   if (v->p[0] != v->p[1] || v->p[0] != v->p[2] || v->p[0] > 3)
     return fail(LRVOL_ERR_UNSUPPORTED, "render needs equal degrees 1..3");
+  if (step->shading != LRVOL_SHADE_NONE && step->shading != LRVOL_SHADE_GRADIENT)
+    return fail(LRVOL_ERR_ARG, "bad shading");
+  if (step->shading == LRVOL_SHADE_GRADIENT && field != LRVOL_FIELD_SCALAR)
+    return fail(LRVOL_ERR_UNSUPPORTED, "gradient shading needs a scalar field");
+  const double ll = step->light[0] * step->light[0] + step->light[1] * step->light[1] +
+                    step->light[2] * step->light[2];
+  if (!(ll < INFINITY)) return fail(LRVOL_ERR_ARG, "light must be finite");
   std::memset(prm, 0, sizeof(*prm));
   prm->elem = v->d_elem;
   prm->n_elem = v->n_elem;
@@ -350,6 +357,12 @@ int prepare_render(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *tf
   prm->tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
   prm->tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
   for (int q = 0; q < 256; ++q) prm->tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
+  if (step->shading == LRVOL_SHADE_GRADIENT) {
+    field = kFieldShaded;
+    prm->light_set = ll > 0.0;
+    for (int a = 0; a < 3; ++a) prm->light[a] = ll > 0.0 ? (float)(step->light[a] / std::sqrt(ll)) : 0.f;
+    prm->grad_eps = (float)(1e-3 * (tf->vmax - tf->vmin));
+  }
   *field_out = field;
   return LRVOL_OK;
 }
@@ -564,51 +577,12 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
 // static device array instead of memory of the handle, and nothing is allocated.
 int lrvol_render_noalloc(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
                          float *rgba_dev, uint64_t *counters_dev, void *stream) {
-  if (!v || !cam || !tf || !step || !rgba_dev) return fail(LRVOL_ERR_ARG, "null pointer");
-  if (!v->have_bezier || !v->have_accel) return fail(LRVOL_ERR_STATE, "render needs to_bezier and build_accel");
-  if (cam->width < 1 || cam->height < 1 || cam->width > kMaxImageSide || cam->height > kMaxImageSide)
+  if (cam && (cam->width > kMaxImageSide || cam->height > kMaxImageSide))
     return fail(LRVOL_ERR_ARG, "image size outside 1..32768 x 1..32768, the maximum of lrvol_render_noalloc");
-  if (cam->projection != LRVOL_ORTHO && cam->projection != LRVOL_PERSP) return fail(LRVOL_ERR_ARG, "bad projection");
-  int r0 = cam->row_begin, r1 = cam->row_end;
-  if (r0 == 0 && r1 == 0) r1 = cam->height;
-  if (r0 < 0 || r1 > cam->height || r0 > r1) return fail(LRVOL_ERR_ARG, "bad row range");
-  if (step->mode != LRVOL_STEP_FIXED && step->mode != LRVOL_STEP_HEURISTIC && step->mode != LRVOL_STEP_LEARNED)
-    return fail(LRVOL_ERR_ARG, "bad step mode");
-  if (step->mode == LRVOL_STEP_LEARNED && !step->mult) return fail(LRVOL_ERR_ARG, "learned steps need multipliers");
-  if (step->mode == LRVOL_STEP_FIXED && !(step->h > 0)) return fail(LRVOL_ERR_ARG, "fixed step must be > 0");
-  if (!(step->xi > 0) || !(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "xi and vmax - vmin must be > 0");
-  const int field = step->field;
-  if (field < 0 || field > 2) return fail(LRVOL_ERR_ARG, "bad field");
-  if (field == LRVOL_FIELD_SCALAR && v->nc != 1) return fail(LRVOL_ERR_ARG, "scalar field needs ncomp = 1");
-  if (field == LRVOL_FIELD_MAGNITUDE && v->nc != 3) return fail(LRVOL_ERR_ARG, "magnitude needs ncomp = 3");
-  if (field == LRVOL_FIELD_COMPONENT && (step->component < 0 || step->component >= v->nc))
-    return fail(LRVOL_ERR_ARG, "bad component");
-  if (v->p[0] != v->p[1] || v->p[0] != v->p[2] || v->p[0] > 3)
-    return fail(LRVOL_ERR_UNSUPPORTED, "render needs equal degrees 1..3");
   RenderParams prm;
-  std::memset(&prm, 0, sizeof(prm));
-  prm.elem = v->d_elem;
-  prm.n_elem = v->n_elem;
-  prm.bez = v->d_bez;
-  prm.elem_bytes = v->elem_bytes;
-  prm.bezc = v->d_bezc;
-  prm.elemc_bytes = v->elemc_bytes;
-  prm.comp = field == LRVOL_FIELD_COMPONENT ? step->component : 0;
-  prm.forest = forest_view(v);
-  prm.out = rgba_dev;
-  prm.width = cam->width;
-  prm.height = cam->height;
-  prm.row_begin = r0;
-  prm.row_end = r1;
-  camera_consts(cam, &prm.ray);
-  prm.mode = step->mode;
-  prm.mult = step->mult;
-  prm.h = (float)step->h;
-  prm.inv_xi = (float)(1.0 / step->xi);
-  prm.alpha_stop = (float)step->alpha_stop;
-  prm.tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
-  prm.tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
-  for (int q = 0; q < 256; ++q) prm.tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
+  int field = 0;
+  int rc = prepare_render(v, cam, tf, step, rgba_dev, &prm, &field);
+  if (rc) return rc;
   cudaError_t e = launch_render_static(prm, v->p[0], field, v->storage, (cudaStream_t)stream,
                                        reinterpret_cast<unsigned long long *>(counters_dev));
   if (e != cudaSuccess) return cuda_fail(e, "render_noalloc");
@@ -718,6 +692,15 @@ int lrvol_eval(lrvol_t v, const float *pts, int64_t n, float *val, void *stream)
   if (!v->have_accel || !v->have_bezier) return fail(LRVOL_ERR_STATE, "eval needs build_accel and to_bezier");
   if (n == 0) return LRVOL_OK;
   CU(launch_eval(v, pts, n, val, (cudaStream_t)stream), "eval kernel");
+  return LRVOL_OK;
+}
+
+int lrvol_eval_grad(lrvol_t v, const float *pts, int64_t n, float *out, void *stream) {
+  if (!v || (n > 0 && (!pts || !out)) || n < 0) return fail(LRVOL_ERR_ARG, "bad arguments");
+  if (!v->have_bezier || !v->have_accel) return fail(LRVOL_ERR_STATE, "eval_grad needs to_bezier and build_accel");
+  if (v->nc != 1) return fail(LRVOL_ERR_UNSUPPORTED, "eval_grad needs a scalar volume");
+  if (n == 0) return LRVOL_OK;
+  CU(launch_eval_grad(v, pts, n, out, (cudaStream_t)stream), "eval_grad kernel");
   return LRVOL_OK;
 }
 

@@ -259,6 +259,26 @@ __device__ __forceinline__ void monomials(float u, float *m) {
   }
 }
 
+// Derivatives d m_i / du = i u^(i-1) (1-u)^(p-i) - (p-i) u^i (1-u)^(p-i-1).
+template <int P>
+__device__ __forceinline__ void dmonomials(float u, float *d) {
+  const float v = 1.f - u;
+  if constexpr (P == 1) {
+    d[0] = -1.f;
+    d[1] = 1.f;
+  } else if constexpr (P == 2) {
+    d[0] = -2.f * v;
+    d[1] = v - u;
+    d[2] = 2.f * u;
+  } else {
+    const float uv = u * v;
+    d[0] = -3.f * (v * v);
+    d[1] = fmaf(-2.f, uv, v * v);
+    d[2] = fmaf(2.f, uv, -(u * u));
+    d[3] = 3.f * (u * u);
+  }
+}
+
 // sum_{k,j,i} c[k][j][i] bx[i] by[j] bz[k], x fastest
 template <int P>
 __device__ __forceinline__ float contract(const float *c, const float *bx, const float *by, const float *bz) {
@@ -309,6 +329,57 @@ __device__ float eval_generic(const float *c, const int *deg, float ux, float uy
   return f;
 }
 
+// Value and derivatives in local coordinates (d/du, d/dv, d/dw) of the same block.
+__device__ float eval_generic_grad(const float *c, const int *deg, float ux, float uy, float uz, float *g) {
+  float b[3][kMaxDeg + 1], db[3][kMaxDeg + 1];
+  const float u[3] = {ux, uy, uz};
+  for (int a = 0; a < 3; ++a) {
+    const int p = deg[a];
+    const float v = 1.f - u[a];
+    for (int i = 0; i <= p; ++i) {
+      float m = 1.f, d1 = 0.f, d2 = 0.f;
+      for (int q = 0; q < i; ++q) m *= u[a];
+      for (int q = i; q < p; ++q) m *= v;
+      if (i > 0) {  // i u^(i-1) v^(p-i)
+        d1 = (float)i;
+        for (int q = 0; q < i - 1; ++q) d1 *= u[a];
+        for (int q = i; q < p; ++q) d1 *= v;
+      }
+      if (i < p) {  // (p-i) u^i v^(p-i-1)
+        d2 = (float)(p - i);
+        for (int q = 0; q < i; ++q) d2 *= u[a];
+        for (int q = i + 1; q < p; ++q) d2 *= v;
+      }
+      b[a][i] = m;
+      db[a][i] = d1 - d2;
+    }
+  }
+  const int n0 = deg[0] + 1, n1 = deg[1] + 1, n2 = deg[2] + 1;
+  float f = 0.f, gx = 0.f, gy = 0.f, gz = 0.f;
+  for (int k = 0; k < n2; ++k) {
+    float t = 0.f, tx = 0.f, ty = 0.f;
+    for (int j = 0; j < n1; ++j) {
+      float s = 0.f, sx = 0.f;
+      for (int i = 0; i < n0; ++i) {
+        const float cc = c[(k * n1 + j) * n0 + i];
+        s = fmaf(cc, b[0][i], s);
+        sx = fmaf(cc, db[0][i], sx);
+      }
+      t = fmaf(s, b[1][j], t);
+      tx = fmaf(sx, b[1][j], tx);
+      ty = fmaf(s, db[1][j], ty);
+    }
+    f = fmaf(t, b[2][k], f);
+    gx = fmaf(tx, b[2][k], gx);
+    gy = fmaf(ty, b[2][k], gy);
+    gz = fmaf(t, db[2][k], gz);
+  }
+  g[0] = gx;
+  g[1] = gy;
+  g[2] = gz;
+  return f;
+}
+
 __device__ __forceinline__ float load_slot(const unsigned char *eb, int storage, int slot) {
   if (storage == LRVOL_STORE_F32) return __ldg(reinterpret_cast<const float *>(eb) + slot);
   const unsigned short h = __ldg(reinterpret_cast<const unsigned short *>(eb + kHeaderBytes) + slot);
@@ -346,6 +417,38 @@ __global__ void k_eval(ForestView f, const ElemRec *__restrict__ elem, int64_t n
       out[q * nc + c] = fmaf(__ldg(hdr + 3 + c), v, __ldg(hdr + c));
     }
   }
+}
+
+// Value and world-space gradient of a scalar volume at points (n x 4 out).
+__global__ void k_eval_grad(ForestView f, const ElemRec *__restrict__ elem, int64_t n_elem,
+                            const unsigned char *__restrict__ bez, int ebytes, int storage, int p0, int p1, int p2,
+                            const float *__restrict__ pts, int64_t n, float *__restrict__ out, uint32_t *status) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const float x = pts[3 * q], y = pts[3 * q + 1], z = pts[3 * q + 2];
+  uint32_t e = kNone;
+  if (x >= 0.f && x <= 1.f && y >= 0.f && y <= 1.f && z >= 0.f && z <= 1.f) e = forest_lookup(f, x, y, z, status);
+  float4 *o = reinterpret_cast<float4 *>(out) + q;
+  if (e == kNone || (int64_t)e >= n_elem) {
+    *o = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const ElemRec r = elem[e];
+  const int deg[3] = {p0, p1, p2};
+  const int n0 = p0 + 1, nb = n0 * (p1 + 1) * (p2 + 1);
+  const unsigned char *eb = bez + (int64_t)e * ebytes;
+  float cl[(kMaxDeg + 1) * (kMaxDeg + 1) * (kMaxDeg + 1)];
+  for (int t = 0; t < nb; ++t) cl[t] = load_slot(eb, storage, render_slot(1, n0, nb, t / n0, t % n0, 0));
+  float g[3];
+  float v = eval_generic_grad(cl, deg, local_u(x, r.a.x, r.c.x, r.d.x), local_u(y, r.a.y, r.c.y, r.d.y),
+                              local_u(z, r.a.z, r.c.z, r.d.z), g);
+  float sc = 1.f;
+  if (storage != LRVOL_STORE_F32) {
+    const float *hdr = reinterpret_cast<const float *>(eb);
+    sc = __ldg(hdr + 3);
+    v = fmaf(sc, v, __ldg(hdr));
+  }
+  *o = make_float4(v, sc * g[0] * r.d.x, sc * g[1] * r.d.y, sc * g[2] * r.d.z);
 }
 
 // ----------------------------------------------------------------------------
@@ -419,6 +522,23 @@ __device__ __forceinline__ void composite(const float4 *tfb, const float4 *tfd, 
   const float sa = fmaf(fr, de.w, e0.w);
   const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (seg * prm.inv_xi));
   const float w = fmaf(-Tr, T, Tr);
+  C0 = fmaf(w, fmaf(fr, de.x, e0.x), C0);
+  C1 = fmaf(w, fmaf(fr, de.y, e0.y), C1);
+  C2 = fmaf(w, fmaf(fr, de.z, e0.z), C2);
+  Tr *= T;
+}
+
+// Alg. 2 with C_src multiplied by the shading intensity sh (Sec. 4.1).
+__device__ __forceinline__ void composite_shaded(const float4 *tfb, const float4 *tfd, float v, float seg, float sh,
+                                                 const RenderParams &prm, float &C0, float &C1, float &C2,
+                                                 float &Tr) {
+  const float x = fminf(fmaxf(fmaf(v, prm.tf_scale, prm.tf_bias), 0.f), 255.f);
+  const int q = min((int)x, 254);
+  const float fr = x - (float)q;
+  const float4 e0 = tfb[q], de = tfd[q];
+  const float sa = fmaf(fr, de.w, e0.w);
+  const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (seg * prm.inv_xi));
+  const float w = fmaf(-Tr, T, Tr) * sh;
   C0 = fmaf(w, fmaf(fr, de.x, e0.x), C0);
   C1 = fmaf(w, fmaf(fr, de.y, e0.y), C1);
   C2 = fmaf(w, fmaf(fr, de.z, e0.z), C2);
@@ -607,6 +727,76 @@ struct Block {
     }
   }
 
+  // Scalar blocks: value and derivatives in local coordinates (d/du, d/dv, d/dw)
+  // at monomials b* and their derivatives d*, reusing the partial sums of the value.
+  __device__ __forceinline__ float eval_grad(const float *bx, const float *by, const float *bz, const float *dx,
+                                             const float *dy, const float *dz, float &gu, float &gv,
+                                             float &gw) const {
+    static_assert(FIELD == 0, "gradients of scalar blocks only");
+    if constexpr (ROWPAIR) {
+      const f2 X0 = f2_pack(bx[0], bx[0]), X1 = f2_pack(bx[1], bx[1]);
+      const f2 X2 = f2_pack(bx[2], bx[2]), X3 = f2_pack(bx[3], bx[3]);
+      const f2 D0 = f2_pack(dx[0], dx[0]), D1 = f2_pack(dx[1], dx[1]);
+      const f2 D2 = f2_pack(dx[2], dx[2]), D3 = f2_pack(dx[3], dx[3]);
+      const f2 Y01 = f2_pack(by[0], by[1]), Y23 = f2_pack(by[2], by[3]);
+      const f2 E01 = f2_pack(dy[0], dy[1]), E23 = f2_pack(dy[2], dy[3]);
+      f2 F = 0, FX = 0, FY = 0, FZ = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const f2 *a = rp[2 * k], *b = rp[2 * k + 1];
+        const f2 S0 = f2_fma(a[3], X3, f2_fma(a[2], X2, f2_fma(a[1], X1, f2_mul(a[0], X0))));
+        const f2 S1 = f2_fma(b[3], X3, f2_fma(b[2], X2, f2_fma(b[1], X1, f2_mul(b[0], X0))));
+        const f2 R0 = f2_fma(a[3], D3, f2_fma(a[2], D2, f2_fma(a[1], D1, f2_mul(a[0], D0))));
+        const f2 R1 = f2_fma(b[3], D3, f2_fma(b[2], D2, f2_fma(b[1], D1, f2_mul(b[0], D0))));
+        const f2 T = f2_fma(S1, Y23, f2_mul(S0, Y01));
+        const f2 TX = f2_fma(R1, Y23, f2_mul(R0, Y01));
+        const f2 TY = f2_fma(S1, E23, f2_mul(S0, E01));
+        const f2 Z = f2_pack(bz[k], bz[k]), DZ = f2_pack(dz[k], dz[k]);
+        F = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, F);
+        FX = k == 0 ? f2_mul(TX, Z) : f2_fma(TX, Z, FX);
+        FY = k == 0 ? f2_mul(TY, Z) : f2_fma(TY, Z, FY);
+        FZ = k == 0 ? f2_mul(T, DZ) : f2_fma(T, DZ, FZ);
+      }
+      float lo, hi;
+      f2_unpack(FX, lo, hi);
+      gu = F32 ? lo + hi : sa * (lo + hi);
+      f2_unpack(FY, lo, hi);
+      gv = F32 ? lo + hi : sa * (lo + hi);
+      f2_unpack(FZ, lo, hi);
+      gw = F32 ? lo + hi : sa * (lo + hi);
+      f2_unpack(F, lo, hi);
+      return F32 ? lo + hi : fmaf(sa, lo + hi, oa);
+    } else {
+      float f = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        float t = 0.f, tx = 0.f, ty = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const int r = k * N + j;
+          float sx = 0.f, rx = 0.f;
+#pragma unroll
+          for (int i = 0; i < N; ++i) {
+            const float c = sg[(r >> 1) * 2 * N + 2 * i + (r & 1)];
+            sx = fmaf(c, bx[i], sx);
+            rx = fmaf(c, dx[i], rx);
+          }
+          t = fmaf(sx, by[j], t);
+          tx = fmaf(rx, by[j], tx);
+          ty = fmaf(sx, dy[j], ty);
+        }
+        f = fmaf(t, bz[k], f);
+        fx = fmaf(tx, bz[k], fx);
+        fy = fmaf(ty, bz[k], fy);
+        fz = fmaf(t, dz[k], fz);
+      }
+      gu = F32 ? fx : sa * fx;
+      gv = F32 ? fy : sa * fy;
+      gw = F32 ? fz : sa * fz;
+      return F32 ? f : fmaf(sa, f, oa);
+    }
+  }
+
   __device__ __forceinline__ float eval(const float *bx, const float *by, const float *bz) const {
     if constexpr (ROWPAIR) {
       // rows r = k*4 + j; pair m = 2k + (j >> 1) holds (row 2m, row 2m+1)
@@ -703,9 +893,15 @@ struct Block {
 // the evaluation of sample k+1 (they are independent), so the scheduler can
 // overlap their latencies; a ray that terminates after sample k discards the
 // already evaluated sample k+1.
+//
+// FIELD 3 renders a scalar volume with gradient shading (Sec. 4.1): each
+// sample also evaluates the block's gradient, and C_src is scaled by
+// I = max(0.4, |l . g| / max(|g|, eps)).
 template <int P, int FIELD, int STORE>
-__global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ RenderParams prm) {
+__global__ void __launch_bounds__(128, (FIELD == 3 && P == 3) ? 3 : 4) k_render(const __grid_constant__ RenderParams prm) {
   constexpr int N = P + 1;
+  constexpr bool SHADE = FIELD == 3;
+  constexpr int BF = SHADE ? 0 : FIELD;
   __shared__ float4 tfb[256], tfd[256];
   for (int q = threadIdx.x; q < 256; q += blockDim.x) {
     const float4 e0 = prm.tf[q], e1 = prm.tf[q < 255 ? q + 1 : 255];
@@ -728,15 +924,24 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
       const float tr_stop = 1.f - prm.alpha_stop;
       float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
       float dsv = 0.f;       // step inside the current element (Eq. 4, or Eq. 4 x learned multiplier)
-      Block<P, FIELD, STORE> blk;
+      Block<P, BF, STORE> blk;
       float t = ray.tin;
       int k = 0;
       bool pend = false;     // a sample evaluated but not yet composited
-      float pv = 0.f, pseg = 0.f;
+      float pv = 0.f, pseg = 0.f, psh = 1.f;
+      float lx = 0.f, ly = 0.f, lz = 0.f;   // towards the light (shading)
+      if constexpr (SHADE) {
+        lx = prm.light_set ? prm.light[0] : -ray.d[0];
+        ly = prm.light_set ? prm.light[1] : -ray.d[1];
+        lz = prm.light_set ? prm.light[2] : -ray.d[2];
+      }
       for (;;) {
         if (!(t < ray.tout)) {
           if (pend) {
-            composite(tfb, tfd, pv, pseg, prm, C0, C1, C2, Tr);
+            if constexpr (SHADE)
+              composite_shaded(tfb, tfd, pv, pseg, psh, prm, C0, C1, C2, Tr);
+            else
+              composite(tfb, tfd, pv, pseg, prm, C0, C1, C2, Tr);
             ++nsamp;
           }
           break;
@@ -754,7 +959,7 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
           ++nlook;
           load_record(prm.elem + cur, ra, rb, rc, rd);
           dsv = prm.mode == LRVOL_STEP_LEARNED ? __fmul_rn(ra.w, __ldg(prm.mult + cur)) : ra.w;
-          if constexpr (FIELD == 2)
+          if constexpr (BF == 2)
             blk.load(prm.bezc + (int64_t)cur * prm.elemc_bytes, prm.comp);
           else
             blk.load(prm.bez + (int64_t)cur * prm.elem_bytes, 0);
@@ -764,18 +969,38 @@ __global__ void __launch_bounds__(128, 4) k_render(const __grid_constant__ Rende
         const float seg = __fsub_rn(fminf(tn, ray.tout), t);
         // evaluate sample k ...
         float bx[N], by[N], bz[N];
-        monomials<P>(local_u(px, ra.x, rc.x, rd.x), bx);
-        monomials<P>(local_u(py, ra.y, rc.y, rd.y), by);
-        monomials<P>(local_u(pz, ra.z, rc.z, rd.z), bz);
-        const float v = blk.eval(bx, by, bz);
+        const float ux = local_u(px, ra.x, rc.x, rd.x);
+        const float uy = local_u(py, ra.y, rc.y, rd.y);
+        const float uz = local_u(pz, ra.z, rc.z, rd.z);
+        monomials<P>(ux, bx);
+        monomials<P>(uy, by);
+        monomials<P>(uz, bz);
+        float v, sh = 1.f;
+        if constexpr (SHADE) {
+          float dx[N], dy[N], dz[N], gu, gv, gw;
+          dmonomials<P>(ux, dx);
+          dmonomials<P>(uy, dy);
+          dmonomials<P>(uz, dz);
+          v = blk.eval_grad(bx, by, bz, dx, dy, dz, gu, gv, gw);
+          const float gx = gu * rd.x, gy = gv * rd.y, gz = gw * rd.z;   // world gradient: d/dx = iw d/du
+          const float gl = fmaf(gx, lx, fmaf(gy, ly, gz * lz));
+          const float gn = fmaxf(sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz))), prm.grad_eps);
+          sh = fmaxf(0.4f, fabsf(gl) / gn);
+        } else {
+          v = blk.eval(bx, by, bz);
+        }
         // ... while compositing sample k-1
         if (pend) {
-          composite(tfb, tfd, pv, pseg, prm, C0, C1, C2, Tr);
+          if constexpr (SHADE)
+            composite_shaded(tfb, tfd, pv, pseg, psh, prm, C0, C1, C2, Tr);
+          else
+            composite(tfb, tfd, pv, pseg, prm, C0, C1, C2, Tr);
           ++nsamp;
           if (Tr <= tr_stop) break;
         }
         pend = true;
         pv = v;
+        psh = sh;
         pseg = seg;
         t = tn;
         if (++k >= kMaxSamplesPerRay) {
@@ -838,6 +1063,13 @@ cudaError_t launch_eval(const lrvol_s *v, const float *pts, int64_t n, float *ou
   return cudaGetLastError();
 }
 
+cudaError_t launch_eval_grad(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s) {
+  k_eval_grad<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(forest_view(v), v->d_elem, v->n_elem, v->d_bez,
+                                                         v->elem_bytes, v->storage, v->p[0], v->p[1], v->p[2], pts,
+                                                         n, out, v->d_status);
+  return cudaGetLastError();
+}
+
 template <int P, int FIELD, int STORE>
 cudaError_t launch_render_t(const RenderParams &prm, cudaStream_t s) {
   const dim3 grid((unsigned)((prm.width + 15) / 16), (unsigned)((prm.row_end - prm.row_begin + 7) / 8));
@@ -847,6 +1079,14 @@ cudaError_t launch_render_t(const RenderParams &prm, cudaStream_t s) {
 
 template <int STORE>
 cudaError_t launch_render_s(const RenderParams &prm, int degree, int f, cudaStream_t s) {
+  if (f == 3) {  // scalar with gradient shading
+    switch (degree) {
+      case 1: return launch_render_t<1, 3, STORE>(prm, s);
+      case 2: return launch_render_t<2, 3, STORE>(prm, s);
+      case 3: return launch_render_t<3, 3, STORE>(prm, s);
+      default: return cudaErrorInvalidValue;
+    }
+  }
   switch (degree * 3 + f) {
     case 3: return launch_render_t<1, 0, STORE>(prm, s);
     case 4: return launch_render_t<1, 1, STORE>(prm, s);
@@ -862,7 +1102,7 @@ cudaError_t launch_render_s(const RenderParams &prm, int degree, int f, cudaStre
 }
 
 cudaError_t launch_render(const RenderParams &prm, int degree, int field, int storage, cudaStream_t s) {
-  const int f = field == LRVOL_FIELD_MAGNITUDE ? 1 : (field == LRVOL_FIELD_COMPONENT ? 2 : 0);
+  const int f = field == kFieldShaded ? 3 : (field == LRVOL_FIELD_MAGNITUDE ? 1 : (field == LRVOL_FIELD_COMPONENT ? 2 : 0));
   switch (storage) {
     case LRVOL_STORE_F32: return launch_render_s<LRVOL_STORE_F32>(prm, degree, f, s);
     case LRVOL_STORE_F16: return launch_render_s<LRVOL_STORE_F16>(prm, degree, f, s);

@@ -96,6 +96,10 @@ __host__ __device__ inline int elem_bytes(int storage, int slots) {
   return roundup32(header_bytes(storage) + slot_bytes(storage) * slots);
 }
 
+// Field code of launch_render for a scalar volume rendered with gradient
+// shading (the public LRVOL_FIELD_* codes are 0..2).
+constexpr int kFieldShaded = 3;
+
 struct RenderParams {
   const ElemRec *elem;
   int64_t n_elem;
@@ -112,6 +116,9 @@ struct RenderParams {
   const float *mult;      // LEARNED: per-element step multipliers
   float h, inv_xi, alpha_stop;
   float tf_scale, tf_bias; // x = v * tf_scale + tf_bias, clamped to [0, 255]
+  int light_set;          // shading: 1 = light[] (unit), 0 = towards the eye along the ray
+  float light[3];
+  float grad_eps;         // shading: gradients below this count as none (1e-3 (vmax - vmin))
   unsigned long long *counters;
   uint32_t *status;
   float4 tf[256];
@@ -164,6 +171,7 @@ cudaError_t launch_to_bezier(const lrvol_s *v, cudaStream_t s);
 cudaError_t launch_pack(const lrvol_s *v, cudaStream_t s);
 cudaError_t launch_elem_records(const lrvol_s *v, cudaStream_t s);
 cudaError_t launch_lookup(const lrvol_s *v, const float *pts, int64_t n, uint32_t *out, cudaStream_t s);
+cudaError_t launch_eval_grad(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s);
 cudaError_t launch_eval(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s);
 cudaError_t launch_render(const RenderParams &prm, int degree, int field, int storage, cudaStream_t s);
 cudaError_t launch_render_static(RenderParams prm, int degree, int field, int storage, cudaStream_t s,
