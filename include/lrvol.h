@@ -314,13 +314,16 @@ void lrvol_arena_destroy(lrvol_arena_t a);
  * A server owns `slots` slots (each three CUDA streams of different
  * priority, two events and statistics counters) and one device arena of `arena_bytes`
  * for output images (and, for learned steps, per-frame features and
- * multipliers).  lrvol_server_submit queues a request (FIFO) and returns at
- * once.  lrvol_server_progress, called from the host loop, first retires the
- * frames whose work has finished, then admits waiting requests in order
- * while a slot is free and the arena holds the request's memory, launching
- * each on its slot's stream: frames of different requests run concurrently
- * on the device.  A request whose memory does not fit waits at the head of
- * the queue (no overtaking) until retired frames free enough.  Results are
+ * multipliers).  lrvol_server_submit queues a request and returns at once.
+ * lrvol_server_progress, called from the host loop, first retires the
+ * frames whose work has finished, then admits waiting requests while a slot
+ * is free and the arena holds the request's memory, launching each on its
+ * slot's stream: frames of different requests run concurrently on the
+ * device.  Admission is FIFO.  With size tiers on (see
+ * lrvol_server_set_priority_pixels) it is FIFO within each tier, smaller
+ * tiers are served first, and the tier of the largest frames holds at most
+ * slots - max(1, slots/4) slots; a request that does not fit waits at the
+ * head of its tier while smaller tiers may go ahead.  Results are
  * identical to lrvol_render of the same request alone: the same kernel with
  * the same parameters, and statistics counters of its own.
  *

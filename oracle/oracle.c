@@ -740,3 +740,213 @@ void orc_labels(const orc_vol *v, const orc_camera *cam, const orc_tf *tf, const
   free(th);
   free(jobs);
 }
+
+/* ------------------------------------------------------------------------ */
+/* Streamlines (Sec. 5): dx/dt = f(x) by explicit Runge-Kutta methods (Eq. 5) */
+/* in FP64, f evaluated by Eq. 2.  Butcher tableaus of the published         */
+/* methods; the step is fixed, the Eq. 4 step of the element holding x_n     */
+/* times a base factor (Sec. 5.2), or chosen by the embedded error estimate. */
+/* Element decisions (the Eq. 4 step, leaving the domain) are taken on the   */
+/* FP32 rounding of the point, as for ray samples.                           */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+  int32_t method;    /* 0 RK1 .. 8 RKF45 (order of the list in lrvol.h) */
+  int32_t step_rule; /* 0 fixed, 1 Eq. 4 times h, 2 adaptive (embedded methods) */
+  double h, t_end, tol;
+  int32_t max_samples;
+} orc_sl_params;
+
+typedef struct {
+  int s;            /* stages */
+  double c[6], a[6][6], b[6], bh[6];
+  int embedded, q_low; /* bh: the other solution of an embedded pair, q_low its order */
+} orc_tableau;
+
+static void tableau_of(int m, orc_tableau *T) {
+  memset(T, 0, sizeof(*T));
+  switch (m) {
+    case 0: /* explicit Euler */
+      T->s = 1; T->b[0] = 1.0;
+      break;
+    case 1: /* explicit midpoint */
+      T->s = 2; T->c[1] = 0.5; T->a[1][0] = 0.5; T->b[1] = 1.0;
+      break;
+    case 2: /* Kutta's third-order method */
+      T->s = 3; T->c[1] = 0.5; T->c[2] = 1.0;
+      T->a[1][0] = 0.5; T->a[2][0] = -1.0; T->a[2][1] = 2.0;
+      T->b[0] = 1.0 / 6; T->b[1] = 2.0 / 3; T->b[2] = 1.0 / 6;
+      break;
+    case 3: /* classic fourth order */
+      T->s = 4; T->c[1] = 0.5; T->c[2] = 0.5; T->c[3] = 1.0;
+      T->a[1][0] = 0.5; T->a[2][1] = 0.5; T->a[3][2] = 1.0;
+      T->b[0] = 1.0 / 6; T->b[1] = 1.0 / 3; T->b[2] = 1.0 / 3; T->b[3] = 1.0 / 6;
+      break;
+    case 4: /* 3/8 rule */
+      T->s = 4; T->c[1] = 1.0 / 3; T->c[2] = 2.0 / 3; T->c[3] = 1.0;
+      T->a[1][0] = 1.0 / 3; T->a[2][0] = -1.0 / 3; T->a[2][1] = 1.0;
+      T->a[3][0] = 1.0; T->a[3][1] = -1.0; T->a[3][2] = 1.0;
+      T->b[0] = 1.0 / 8; T->b[1] = 3.0 / 8; T->b[2] = 3.0 / 8; T->b[3] = 1.0 / 8;
+      break;
+    case 5: /* Fehlberg, fifth-order solution */
+    case 8: /* Fehlberg 4(5), fifth order propagated, fourth order for the estimate */
+      T->s = 6;
+      T->c[1] = 0.25; T->c[2] = 3.0 / 8; T->c[3] = 12.0 / 13; T->c[4] = 1.0; T->c[5] = 0.5;
+      T->a[1][0] = 0.25;
+      T->a[2][0] = 3.0 / 32; T->a[2][1] = 9.0 / 32;
+      T->a[3][0] = 1932.0 / 2197; T->a[3][1] = -7200.0 / 2197; T->a[3][2] = 7296.0 / 2197;
+      T->a[4][0] = 439.0 / 216; T->a[4][1] = -8.0; T->a[4][2] = 3680.0 / 513; T->a[4][3] = -845.0 / 4104;
+      T->a[5][0] = -8.0 / 27; T->a[5][1] = 2.0; T->a[5][2] = -3544.0 / 2565; T->a[5][3] = 1859.0 / 4104;
+      T->a[5][4] = -11.0 / 40;
+      T->b[0] = 16.0 / 135; T->b[2] = 6656.0 / 12825; T->b[3] = 28561.0 / 56430; T->b[4] = -9.0 / 50;
+      T->b[5] = 2.0 / 55;
+      T->bh[0] = 25.0 / 216; T->bh[2] = 1408.0 / 2565; T->bh[3] = 2197.0 / 4104; T->bh[4] = -1.0 / 5;
+      T->embedded = m == 8; T->q_low = 4;
+      break;
+    case 6: /* Heun-Euler 2(1) */
+      T->s = 2; T->c[1] = 1.0; T->a[1][0] = 1.0;
+      T->b[0] = 0.5; T->b[1] = 0.5;
+      T->bh[0] = 1.0;
+      T->embedded = 1; T->q_low = 1;
+      break;
+    case 7: /* Bogacki-Shampine 3(2) */
+      T->s = 4; T->c[1] = 0.5; T->c[2] = 0.75; T->c[3] = 1.0;
+      T->a[1][0] = 0.5; T->a[2][1] = 0.75;
+      T->a[3][0] = 2.0 / 9; T->a[3][1] = 1.0 / 3; T->a[3][2] = 4.0 / 9;
+      T->b[0] = 2.0 / 9; T->b[1] = 1.0 / 3; T->b[2] = 4.0 / 9;
+      T->bh[0] = 7.0 / 24; T->bh[1] = 0.25; T->bh[2] = 1.0 / 3; T->bh[3] = 0.125;
+      T->embedded = 1; T->q_low = 2;
+      break;
+  }
+}
+
+/* inside [0,1]^3 as an FP32 point; its element through e (cached) */
+static int sl_point(const orc_vol *v, const double *x, uint32_t *e, double xf[3]) {
+  for (int a = 0; a < 3; ++a) {
+    xf[a] = (double)(float)x[a];
+    if (!(xf[a] >= 0.0 && xf[a] <= 1.0)) return 0;
+  }
+  if (*e == ORC_NONE || !in_element(v, *e, xf)) *e = orc_find_element(v, xf);
+  return *e != ORC_NONE;
+}
+
+typedef struct {
+  const orc_vol *v;
+  const orc_sl_params *P;
+  const double *seeds;
+  int64_t n;
+  double *out;
+  int32_t *count, *status;
+  int tid, nth;
+} sl_job;
+
+static void *sl_worker(void *arg) {
+  sl_job *J = (sl_job *)arg;
+  const orc_vol *v = J->v;
+  const orc_sl_params *P = J->P;
+  orc_tableau T;
+  tableau_of(P->method, &T);
+  int64_t *inc = (int64_t *)malloc(sizeof(int64_t) * v->n_basis);
+  for (int64_t q = J->tid; q < J->n; q += J->nth) {
+    double x[3] = {J->seeds[3 * q], J->seeds[3 * q + 1], J->seeds[3 * q + 2]};
+    double *o = J->out + q * (int64_t)P->max_samples * 4;
+    double t = 0.0, xf[3];
+    uint32_t e = ORC_NONE, ei = ORC_NONE;
+    int64_t ninc = 0;
+    int n = 0, st = 0;
+    if (!sl_point(v, x, &e, xf)) {
+      J->count[q] = 0;
+      J->status[q] = 1;
+      continue;
+    }
+    o[0] = x[0]; o[1] = x[1]; o[2] = x[2]; o[3] = 0.0;
+    n = 1;
+    double h = P->step_rule == 0 ? P->h : (P->step_rule == 1 ? P->h * (double)orc_heuristic_step(v, e)
+                                                             : (P->h > 0 ? P->h : (double)orc_heuristic_step(v, e)));
+    for (;;) {
+      if (!(t < P->t_end)) { st = 0; break; }
+      if (n >= P->max_samples) { st = 2; break; }
+      if (P->step_rule == 1) h = P->h * (double)orc_heuristic_step(v, e);
+      if (P->step_rule == 0) h = P->h;
+      int tries = 0, taken = 0, out = 0;
+      double xn[3];
+      while (!taken) {
+        double hs = h, last = 0;
+        if (t + hs > P->t_end) { hs = P->t_end - t; last = 1; }
+        double k[6][3];
+        for (int i = 0; i < T.s && !out; ++i) {
+          double y[3];
+          for (int a = 0; a < 3; ++a) {
+            double acc = 0.0;
+            for (int j = 0; j < i; ++j) acc += T.a[i][j] * k[j][a];
+            y[a] = x[a] + hs * acc;
+          }
+          uint32_t es = e;
+          if (!sl_point(v, y, &es, xf)) { out = 1; break; }
+          if (es != ei) { ninc = orc_incidence(v, es, inc); ei = es; }
+          /* the field is evaluated at the FP32 point (single-precision spline
+             evaluation under a double-precision outer loop, Sec. 5.5) */
+          double val[3];
+          eval_with(v, inc, ninc, xf, val);
+          for (int a = 0; a < 3; ++a) k[i][a] = val[a];
+        }
+        if (out) break;
+        double dx[3], err2 = 0.0;
+        for (int a = 0; a < 3; ++a) {
+          double acc = 0.0, ea = 0.0;
+          for (int i = 0; i < T.s; ++i) {
+            acc += T.b[i] * k[i][a];
+            ea += (T.b[i] - T.bh[i]) * k[i][a];
+          }
+          dx[a] = hs * acc;
+          err2 += (hs * ea) * (hs * ea);
+        }
+        if (P->step_rule == 2) {
+          double err = sqrt(err2);
+          double fac = err > 0.0 ? 0.9 * pow(P->tol / err, 1.0 / (T.q_low + 1)) : 5.0;
+          if (fac < 0.2) fac = 0.2;
+          if (fac > 5.0) fac = 5.0;
+          if (err > P->tol) {
+            h = hs * fac;
+            if (++tries >= 64) break;
+            continue;
+          }
+          if (!last) h = hs * fac;
+        }
+        for (int a = 0; a < 3; ++a) xn[a] = x[a] + dx[a];
+        uint32_t en = e;
+        if (!sl_point(v, xn, &en, xf)) { out = 1; break; }
+        e = en;
+        t = last ? P->t_end : t + hs;
+        taken = 1;
+      }
+      if (out) { st = 1; break; }
+      if (!taken) { st = 3; break; }
+      for (int a = 0; a < 3; ++a) x[a] = xn[a];
+      double *w = o + 4 * n;
+      w[0] = x[0]; w[1] = x[1]; w[2] = x[2]; w[3] = t;
+      ++n;
+    }
+    J->count[q] = n;
+    J->status[q] = st;
+  }
+  free(inc);
+  return NULL;
+}
+
+/* n streamlines from seeds (n x 3); out n x max_samples x 4 (x, y, z, t),
+ * count[n] samples written (the seed first), status[n]: 0 reached t_end,
+ * 1 left the domain, 2 max_samples, 3 step control failed. */
+void orc_streamlines(const orc_vol *v, const orc_sl_params *P, const double *seeds, int64_t n, double *out,
+                     int32_t *count, int32_t *status, int nth) {
+  if (nth < 1) nth = 1;
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nth);
+  sl_job *jobs = (sl_job *)malloc(sizeof(sl_job) * nth);
+  for (int t = 0; t < nth; ++t) {
+    sl_job J = {v, P, seeds, n, out, count, status, t, nth};
+    jobs[t] = J;
+    pthread_create(&th[t], NULL, sl_worker, &jobs[t]);
+  }
+  for (int t = 0; t < nth; ++t) pthread_join(th[t], NULL);
+  free(th);
+  free(jobs);
+}

@@ -75,6 +75,15 @@ class _Step(ctypes.Structure):
                 ("mult", ctypes.c_void_p), ("shading", ctypes.c_int32), ("light", ctypes.c_double * 3)]
 
 
+class _SLParams(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("step_rule", ctypes.c_int32), ("h", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("tol", ctypes.c_double), ("max_samples", ctypes.c_int32)]
+
+
+SL_METHODS = ["RK1", "RK2", "RK3", "RK4", "RK38", "RKF5", "HE", "BS", "RKF45"]
+SL_RULES = ["fixed", "heuristic", "adaptive"]
+
+
 class _Stats(ctypes.Structure):
     _fields_ = [("samples", ctypes.c_int64), ("lookups", ctypes.c_int64), ("rays_hit", ctypes.c_int64)]
 
@@ -110,6 +119,7 @@ def _load():
                                  vp, i64, vp, i32, ctypes.POINTER(_Stats)]
         L.orc_labels.argtypes = [vp, ctypes.POINTER(_Cam), ctypes.POINTER(_TF), ctypes.POINTER(_Step),
                                  ctypes.c_double, ctypes.c_double, vp, i32, vp, i32]
+        L.orc_streamlines.argtypes = [vp, ctypes.POINTER(_SLParams), vp, i64, vp, vp, vp, i32]
         L.orc_ray.restype = i32
         L.orc_ray.argtypes = [ctypes.POINTER(_Cam), i32, i32, vp, vp, vp, vp]
         _lib = L
@@ -237,6 +247,22 @@ class Oracle:
             L.orc_eval_grad_batch_f64(self._h, p.ctypes.data, n, val.ctypes.data, grad.ctypes.data, self.threads)
         return val, grad
 
+    def streamlines(self, seeds, method: str, rule: str, h: float, t_end: float, tol: float = 1e-6,
+                    max_samples: int = 4096, threads: int | None = None):
+        """Streamlines (Sec. 5) in FP64: (samples (n, max, 4) of x, y, z, t;
+        count (n,); status (n,): 0 reached t_end, 1 left the domain,
+        2 max_samples, 3 step control failed)."""
+        seeds = np.ascontiguousarray(seeds, dtype=np.float64).reshape(-1, 3)
+        n = len(seeds)
+        P = _SLParams(SL_METHODS.index(method), SL_RULES.index(rule), float(h), float(t_end), float(tol),
+                      int(max_samples))
+        out = np.zeros((n, max_samples, 4), dtype=np.float64)
+        count = np.zeros(n, dtype=np.int32)
+        status = np.zeros(n, dtype=np.int32)
+        _load().orc_streamlines(self._h, ctypes.byref(P), seeds.ctypes.data, n, out.ctypes.data, count.ctypes.data,
+                                status.ctypes.data, _threads(threads or self.threads))
+        return out, count, status
+
     def heuristic_step(self, e: int) -> float:
         return float(_load().orc_heuristic_step(self._h, int(e)))
 
@@ -321,3 +347,25 @@ class Oracle:
         _load().orc_labels(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), float(h_fine), float(tau),
                            cand.ctypes.data, len(cand), lab.ctypes.data, _threads(threads or self.threads))
         return lab
+
+
+def streamline_error(ref, ref_count, approx, approx_count):
+    """Eq. 7: for each streamline j, sum over the approximation's samples
+    i >= 1 of (t^i - t^{i-1}) * ||x_j(t^i) - y_j(t^i)||_2, the reference x_j
+    linearly interpolated between its samples at t^i (samples past the
+    reference's last time are left out).  Returns (per-line sums, max)."""
+    ref = np.asarray(ref, dtype=np.float64)
+    approx = np.asarray(approx, dtype=np.float64)
+    sums = np.zeros(len(approx))
+    for j in range(len(approx)):
+        r = ref[j, :int(ref_count[j])]
+        a = approx[j, :int(approx_count[j])]
+        if len(r) < 2 or len(a) < 2:
+            continue
+        t = a[1:, 3]
+        keep = t <= r[-1, 3]
+        t = t[keep]
+        dt = np.diff(a[:, 3])[keep]
+        x = np.stack([np.interp(t, r[:, 3], r[:, c]) for c in range(3)], axis=1)
+        sums[j] = float(np.sum(dt * np.linalg.norm(x - a[1:, :3][keep], axis=1)))
+    return sums, float(sums.max()) if len(sums) else 0.0

@@ -1,5 +1,6 @@
 // liblrvol frame server: continuous batching of frame requests over volumes
-// that stay resident on the device.  Requests queue in FIFO order; each call
+// that stay resident on the device.  Requests queue in FIFO order per size
+// tier; each call
 // of lrvol_server_progress retires frames whose work has finished (one event
 // query per busy slot, never a wait) and admits waiting requests while a slot
 // stream is free and the output arena has room, so the frames of several
@@ -132,12 +133,13 @@ struct lrvol_server_s {
   unsigned char *h_scratch = nullptr;
   cudaEvent_t base = nullptr;
   lrvol_arena_s arena;
-  std::deque<int64_t> queue;
+  std::deque<int64_t> queue[kTiers];  // FIFO per tier (one tier while priorities are off)
   std::deque<int64_t> finished;  // retired since the last lrvol_server_poll
   std::unordered_map<int64_t, Request> req;
   int64_t next_ticket = 1;
   int64_t submitted = 0, done = 0, failed = 0, high_water = 0;
   int running = 0, max_running = 0;
+  int running_tier[kTiers] = {0, 0, 0};
   const uint16_t *packed = nullptr;
   float ymax = 0.f;
   int64_t priority_pixels = 0;  // tier 0 up to this many pixels, tier 1 up to 4 times as many, else tier 2
@@ -225,6 +227,7 @@ int retire(lrvol_server_s *s, int32_t *n_retired) {
     Request &r = s->req[sl.ticket];
     sl.ticket = -1;
     --s->running;
+    --s->running_tier[r.tier];
     ++n;
     if (e != cudaSuccess) {
       finish(s, r, LRVOL_REQ_FAILED, cuda_fail(e, "server: frame"));
@@ -247,31 +250,48 @@ int retire(lrvol_server_s *s, int32_t *n_retired) {
   return LRVOL_OK;
 }
 
+// Admission.  Each tier's queue is served in arrival order.  With
+// priorities on, tiers are tried from the smallest frames up, and the
+// largest tier may hold at most slots - max(1, slots / 4) slots, so small
+// and medium frames always find a slot; a request that does not fit (slot
+// or memory) waits at the head of its tier while smaller tiers go ahead.
+// With priorities off every request is in the last tier: plain FIFO.
 void admit(lrvol_server_s *s) {
-  while (!s->queue.empty()) {
-    int k = -1;
-    for (size_t q = 0; q < s->slots.size(); ++q)
-      if (s->slots[q].ticket < 0) {
-        k = (int)q;
+  const int nslots = (int)s->slots.size();
+  const int reserve = s->priority_pixels > 0 ? (nslots / 4 > 1 ? nslots / 4 : 1) : 0;
+  const int cap_large = nslots - reserve > 1 ? nslots - reserve : 1;
+  for (bool progress = true; progress;) {
+    progress = false;
+    for (int tier = 0; tier < kTiers; ++tier) {
+      if (s->queue[tier].empty()) continue;
+      if (tier == kTiers - 1 && s->running_tier[tier] >= cap_large) continue;
+      int k = -1;
+      for (int q = 0; q < nslots; ++q)
+        if (s->slots[q].ticket < 0) {
+          k = q;
+          break;
+        }
+      if (k < 0) return;  // no slot for anyone
+      Request &r = s->req[s->queue[tier].front()];
+      const int64_t off = s->arena.alloc(r.bytes);
+      if (off < 0) continue;  // this tier's head waits for memory
+      s->queue[tier].pop_front();
+      r.off = off;
+      r.slot = k;
+      r.t_admit = now_s();
+      if (s->arena.in_use > s->high_water) s->high_water = s->arena.in_use;
+      progress = true;
+      int rc = launch_request(s, r, k);
+      if (rc) {
+        finish(s, r, LRVOL_REQ_FAILED, rc);
         break;
       }
-    if (k < 0) return;
-    Request &r = s->req[s->queue.front()];
-    const int64_t off = s->arena.alloc(r.bytes);
-    if (off < 0) return;  // the head waits for memory; nothing overtakes it
-    s->queue.pop_front();
-    r.off = off;
-    r.slot = k;
-    r.t_admit = now_s();
-    if (s->arena.in_use > s->high_water) s->high_water = s->arena.in_use;
-    int rc = launch_request(s, r, k);
-    if (rc) {
-      finish(s, r, LRVOL_REQ_FAILED, rc);
-      continue;
+      r.state = LRVOL_REQ_RUNNING;
+      s->slots[k].ticket = r.ticket;
+      ++s->running_tier[r.tier];
+      if (++s->running > s->max_running) s->max_running = s->running;
+      break;  // start again from the smallest tier
     }
-    r.state = LRVOL_REQ_RUNNING;
-    s->slots[k].ticket = r.ticket;
-    if (++s->running > s->max_running) s->max_running = s->running;
   }
 }
 
@@ -391,7 +411,7 @@ int lrvol_server_submit(lrvol_server_t s, lrvol_t vol, const lrvol_camera *cam, 
   r.ticket = s->next_ticket++;
   r.t_submit = now_s();
   s->req[r.ticket] = r;
-  s->queue.push_back(r.ticket);
+  s->queue[r.tier].push_back(r.ticket);
   ++s->submitted;
   *ticket = r.ticket;
   return LRVOL_OK;
@@ -410,7 +430,9 @@ int lrvol_server_drain(lrvol_server_t s) {
     retire(s, nullptr);
     admit(s);
     if (s->running == 0) {
-      if (s->queue.empty()) return LRVOL_OK;
+      bool empty = true;
+      for (int t = 0; t < kTiers; ++t) empty = empty && s->queue[t].empty();
+      if (empty) return LRVOL_OK;
       return fail(LRVOL_ERR_OOM, "server: queued requests do not fit beside unreleased frames");
     }
     // wait for the oldest running frame
@@ -475,7 +497,7 @@ int lrvol_server_get_stats(lrvol_server_t s, lrvol_server_stats *out) {
   if (!s || !out) return fail(LRVOL_ERR_ARG, "null pointer");
   std::memset(out, 0, sizeof(*out));
   out->submitted = s->submitted;
-  out->queued = (int64_t)s->queue.size();
+  for (int t = 0; t < kTiers; ++t) out->queued += (int64_t)s->queue[t].size();
   out->running = s->running;
   out->done = s->done;
   out->failed = s->failed;

@@ -132,3 +132,30 @@ def test_realtime_stream_latencies(resident, capsys):
     assert s["frames"] == 120 and s["failed"] == 0
     assert all(r["latency_ms"] >= 0 and r["done_s"] >= r["admit_s"] >= r["arrival_s"] - 1e-6 for r in recs)
     srv.close()
+
+
+def test_size_tiers_let_small_frames_overtake(resident):
+    """With tiers on, small frames submitted behind large ones that fill the
+    arena are admitted first; within a tier admission stays FIFO."""
+    gvs, tfs, steps = resident
+    big = 1024 * 1024 * 16                                 # 16 MiB per large frame
+    srv = lv.Server(slots=8, arena_bytes=2 * big + (4 << 20))
+    srv.set_priority_pixels(64 * 64)
+    hl = [torch.empty((1024, 1024, 4), pin_memory=True) for _ in range(5)]
+    hs = [torch.empty((48, 64, 4), pin_memory=True) for _ in range(5)]
+    large = [srv.submit(gvs[0], serve.orbit_view(0, k, 1, 1024, 1024), tfs[0], steps[0], host_out=h)
+             for k, h in enumerate(hl)]
+    assert srv.progress() == 0                             # two large frames fill the arena
+    small = [srv.submit(gvs[0], serve.orbit_view(0, k, 1, 64, 48), tfs[0], steps[0], host_out=h)
+             for k, h in enumerate(hs)]
+    srv.drain()
+    st = srv.stats()
+    assert st["done"] == 10 and st["arena_high_water"] <= 2 * big + (4 << 20)
+    adm_l = [srv.info(t)["t_admit"] for t in large]
+    adm_s = [srv.info(t)["t_admit"] for t in small]
+    assert adm_l == sorted(adm_l) and adm_s == sorted(adm_s)
+    assert max(adm_s) < adm_l[2]                           # every small frame before the third large one
+    assert min(adm_s) > adm_l[1]
+    for t in large + small:
+        srv.release(t)
+    srv.close()

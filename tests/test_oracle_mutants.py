@@ -4,7 +4,8 @@ Each case edits one line of oracle.c (a dropped term, a wrong index or sign,
 a transposed axis, an off-by-one), builds the edited copy on the CPU into a
 temporary directory, points the oracle module at it, and runs the pins of
 test_oracle_pins, the label pins of test_oracle_learned and the gradient and
-shading pins of test_oracle_shading; at least one must fail.  The default build is restored
+shading pins of test_oracle_shading and the streamline pins of
+test_oracle_streamlines; at least one must fail.  The default build is restored
 afterwards.  No GPU is involved.
 """
 import os
@@ -14,6 +15,7 @@ import oracle.oracle as orc
 
 import test_oracle_learned as L
 import test_oracle_shading as S
+import test_oracle_streamlines as SL
 import test_oracle_pins as P
 
 SRC = os.path.join(os.path.dirname(orc.__file__), "oracle.c")
@@ -72,6 +74,17 @@ MUTANTS = [
     ("gradient differentiates y for x", "{g * D[0] * B[1] * B[2],", "{g * B[0] * D[1] * B[2],"),
     ("shading ignores the light vector", "l[c] = J->st->light[c];", "l[c] = 0.0;"),
     ("shading without the 0.4 floor", "if (shade < 0.4) shade = 0.4;", ""),
+    ("RK4 weight 1/6 for the second stage",
+     "T->b[0] = 1.0 / 6; T->b[1] = 1.0 / 3; T->b[2] = 1.0 / 3; T->b[3] = 1.0 / 6;",
+     "T->b[0] = 1.0 / 6; T->b[1] = 1.0 / 6; T->b[2] = 1.0 / 3; T->b[3] = 1.0 / 6;"),
+    ("Kutta's method with a31 = +1", "T->a[1][0] = 0.5; T->a[2][0] = -1.0; T->a[2][1] = 2.0;",
+     "T->a[1][0] = 0.5; T->a[2][0] = 1.0; T->a[2][1] = 2.0;"),
+    ("3/8 rule with a42 = +1", "T->a[3][0] = 1.0; T->a[3][1] = -1.0; T->a[3][2] = 1.0;",
+     "T->a[3][0] = 1.0; T->a[3][1] = 1.0; T->a[3][2] = 1.0;"),
+    ("Fehlberg fifth-order weight sign", "T->b[4] = -9.0 / 50;", "T->b[4] = 9.0 / 50;"),
+    ("stages evaluated at x_n", "y[a] = x[a] + hs * acc;", "y[a] = x[a];"),
+    ("streamline Eq. 4 step without the element", "if (P->step_rule == 1) h = P->h * (double)orc_heuristic_step(v, e);",
+     "if (P->step_rule == 1) h = P->h;"),
 ]
 
 
@@ -106,6 +119,13 @@ def _pins(cfg1):
                                                                         [1.0, 0.0, 1.0]))
     yield lambda: S.test_shading_of_a_constant_field_is_0p4(cfg1)
     yield lambda: S.test_shading_closed_forms_linear_field()
+    H = orc.Oracle(SL.helix_volume())
+    for m in sorted(SL.ORDERS):
+        yield lambda m=m: SL.test_fixed_step_order(H, m)
+    yield lambda: SL.test_constant_field_is_exact_and_heuristic_step_closed_form("RK4")
+    yield lambda: SL.test_domain_exit_and_sample_cap()
+    for m in ("HE", "BS", "RKF45"):
+        yield lambda m=m: SL.test_adaptive_meets_tolerance(H, m)
 
 
 def test_unmutated_source_passes_the_same_pins(cfg1):
