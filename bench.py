@@ -323,6 +323,60 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream):
     return res
 
 
+SL_RUNS = (("RK2", "heuristic", 1.0, 0.0), ("RK4", "heuristic", 1.0, 0.0), ("RKF5", "heuristic", 1.0, 0.0),
+           ("RK4", "heuristic", 0.5, 0.0), ("RKF45", "adaptive", 0.0, 1e-6), ("BS", "adaptive", 0.0, 1e-6))
+SL_STAGES = {"RK1": 1, "RK2": 2, "RK3": 3, "RK4": 4, "RK38": 4, "RKF5": 6, "HE": 2, "BS": 4, "RKF45": 6}
+
+
+def streamline_leg(stream, n_seeds: int = 65536, n_err: int = 4096, t_end: float = 1.2, reps: int = 3):
+    """Streamlines through config 3's wind field (Sec. 5): a seeded rake of
+    n_seeds upstream of the obstacle, integrated to t_end or until the line
+    leaves the domain, by several methods and step rules.  Each run is timed
+    with CUDA events (mean of reps); the Eq. 7 error is taken on the first
+    n_err lines against Fehlberg's fifth-order solution with the fixed step
+    2^-12 (the paper's reference)."""
+    import torch
+    from paper_1707_01170_gb300 import lrvol as lv
+    from paper_1707_01170_gb300.synth import volumes as V
+    vol = V.load_config(3)
+    g = lv.Volume(vol).build_accel(BLOCKS, stream=stream).to_bezier(stream=stream)
+    seeds = torch.from_numpy(V.config3_seeds(n_seeds)).cuda()
+    href = 2.0 ** -12
+    nref = int(t_end / href) + 2
+    ref = lv.streamlines(g, seeds[:n_err].contiguous(), "RKF5", "fixed", href, t_end, max_samples=nref, stream=stream)
+    torch.cuda.synchronize()
+    out = {"volume": "config 3 (388,016 elements, triquadratic 3-vector wind flow)", "seeds": n_seeds,
+           "t_end": t_end, "reference": f"RKF5 fixed step 2^-12 on the first {n_err} seeds",
+           "precision": "outer loop in float pairs (about 48 bits) and FP64 time, field evaluation in FP32",
+           "runs": []}
+    max_samples = 4096
+    buf = (torch.empty((n_seeds, max_samples, 4), dtype=torch.float64, device="cuda"),
+           torch.empty(n_seeds, dtype=torch.int32, device="cuda"), torch.empty(n_seeds, dtype=torch.int32, device="cuda"))
+    for method, rule, h, tol in SL_RUNS:
+        run = lambda: lv.streamlines(g, seeds, method, rule, h, t_end, tol, max_samples, out=buf, stream=stream)
+        run()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(reps):
+            run()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+        samples, count, status = buf
+        steps = int((count.to(torch.int64) - 1).clamp(min=0).sum())
+        sums = lv.streamline_error(ref[0], ref[1], samples[:n_err].contiguous(), count[:n_err].contiguous(),
+                                   stream=stream)
+        st = torch.bincount(status.to(torch.int64), minlength=4).tolist()
+        evals = steps * SL_STAGES[method]
+        out["runs"].append({"method": method, "rule": rule, "h": h, "tol": tol, "ms": ms, "accepted_steps": steps,
+                            "steps_per_s": steps / (ms / 1e3), "evals_per_s_accepted": evals / (ms / 1e3),
+                            "eq7_max": float(sums.max()), "eq7_mean": float(sums.mean()),
+                            "status_counts": {"t_end": st[0], "left": st[1], "cap": st[2], "control": st[3]}})
+    g.close()
+    return out
+
+
 SERVE_PLAN = ((60.0, 500), (120.0, 1000), (240.0, 2000))   # (requests/s, requests): about 8 s each
 
 
@@ -456,6 +510,10 @@ def run_ours(args):
                    "achieved_tflops": ach, "frac_of_fp32_peak": ach / FP32_PEAK_TFLOPS, "frames_timed": n_sh,
                    "kernel": f"k_render<{int(vol.deg[0])},3,{args.storage}>"}
 
+    sl = None
+    if args.streamlines and ws == 1:
+        sl = streamline_leg(stream)
+
     serving = None
     if args.serve != "off" and ws == 1:
         modes = ["plain", "learned"] if args.serve == "both" else [args.serve]
@@ -508,6 +566,8 @@ def run_ours(args):
         line["learned_step"] = learned
     if shading is not None:
         line["shading"] = shading
+    if sl is not None:
+        line["streamlines"] = sl
     if serving is not None:
         line["serving"] = serving
     if not args.no_cpu_baseline:
@@ -533,6 +593,8 @@ def main():
                     help="also time learned step sizes with this block storage against plain FP32 Eq. 4")
     ap.add_argument("--serve", default="both", choices=["off", "plain", "learned", "both"],
                     help="frame-server runs over three resident volumes (learned needs --learned)")
+    ap.add_argument("--no-streamlines", dest="streamlines", action="store_false",
+                    help="skip the streamline runs on config 3")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up frames
     if args.impl == "reference":

@@ -291,6 +291,61 @@ int lrvol_eval_grad(lrvol_t vol, const float *pts_dev, int64_t n, float *val_gra
 int lrvol_get_bezier(lrvol_t vol, double *host_out);
 
 /* ---------------------------------------------------------------------------
+ * Streamlines of a 3-vector volume (Sec. 5): dx/dt = f(x) from each seed by
+ * an explicit Runge-Kutta method (Eq. 5).  The outer loop accumulates x in
+ * more than FP32 precision (an unevaluated pair of floats, about 48
+ * significant bits) and t in FP64; f is evaluated in FP32 at the FP32
+ * rounding of each stage point (the paper's mixed precision, Sec. 5.5).
+ * Steps: FIXED h; HEURISTIC h times the Eq. 4 step of the element holding
+ * the FP32 rounding of x_n (Sec. 5.2; h is the base factor); ADAPTIVE (the
+ * embedded pairs only): the step after an accepted or rejected attempt is
+ * h * clamp(0.9 (tol/err)^(1/(q+1)), 0.2, 5), err = |h sum (b_i - b^_i) k_i|,
+ * q the lower order, accept when err <= tol, first step h (0 = Eq. 4), at
+ * most 64 attempts per step.  The last step is clipped to end at t_end.
+ * A streamline stops at t_end (status 0), when a stage point or the next
+ * point leaves [0,1]^3 (status 1; the point before is the last sample),
+ * after max_samples samples (2), or when the step control gives up (3).
+ * ------------------------------------------------------------------------- */
+enum {
+  LRVOL_RK1 = 0,   /* explicit Euler */
+  LRVOL_RK2 = 1,   /* explicit midpoint */
+  LRVOL_RK3 = 2,   /* Kutta's third-order method */
+  LRVOL_RK4 = 3,   /* classic fourth order */
+  LRVOL_RK38 = 4,  /* 3/8 rule */
+  LRVOL_RKF5 = 5,  /* Fehlberg's fifth-order solution */
+  LRVOL_HE = 6,    /* Heun-Euler 2(1), second order propagated */
+  LRVOL_BS = 7,    /* Bogacki-Shampine 3(2), third order propagated */
+  LRVOL_RKF45 = 8  /* Fehlberg 4(5), fifth order propagated */
+};
+enum { LRVOL_SL_FIXED = 0, LRVOL_SL_HEURISTIC = 1, LRVOL_SL_ADAPTIVE = 2 };
+
+typedef struct {
+  int32_t method;      /* LRVOL_RK1 .. LRVOL_RKF45 */
+  int32_t step_rule;   /* LRVOL_SL_* */
+  double h;            /* FIXED: step (> 0); HEURISTIC: factor on Eq. 4 (> 0); ADAPTIVE: first step, 0 = Eq. 4 */
+  double t_end;        /* > 0 */
+  double tol;          /* ADAPTIVE: local error tolerance (> 0, parameter-space units) */
+  int32_t max_samples; /* >= 1, per streamline, the seed included */
+} lrvol_streamline_params;
+
+/* n seeds (device, n x 3 doubles) -> samples_dev (n x max_samples x 4
+ * doubles: x, y, z, t; the seed first at t = 0), count_dev (n int32:
+ * samples written), status_dev (n int32).  Needs build_accel and to_bezier,
+ * ncomp 3, equal degrees 1..3; any block storage.  Seeds outside [0,1]^3
+ * give count 0 and status 1. */
+int lrvol_streamlines(lrvol_t vol, const lrvol_streamline_params *params, const double *seeds_dev, int64_t n,
+                      double *samples_dev, int32_t *count_dev, int32_t *status_dev, void *stream);
+
+/* Eq. 7 per streamline (device): sums_dev[j] = sum over the approximation's
+ * samples i >= 1 of (t_i - t_{i-1}) |x_j(t_i) - y_j(t_i)|_2, the reference
+ * x_j linear between its samples; samples past the reference's last time
+ * are left out.  Layouts as lrvol_streamlines writes them (ref_max and
+ * app_max samples per line).  The metric E is the maximum of the sums. */
+int lrvol_streamline_error(const double *ref_dev, const int32_t *ref_count_dev, int32_t ref_max,
+                           const double *app_dev, const int32_t *app_count_dev, int32_t app_max, int64_t n,
+                           double *sums_dev, void *stream);
+
+/* ---------------------------------------------------------------------------
  * Host-side arena bookkeeping (first fit, coalescing): offsets into a range
  * of `bytes`, every block aligned to `align` (a power of two).  The frame
  * server below carves its output images from one device allocation with it;

@@ -704,6 +704,50 @@ int lrvol_eval_grad(lrvol_t v, const float *pts, int64_t n, float *out, void *st
   return LRVOL_OK;
 }
 
+int lrvol_streamlines(lrvol_t v, const lrvol_streamline_params *P, const double *seeds, int64_t n, double *out,
+                      int32_t *count, int32_t *status, void *stream) {
+  if (!v || !P || n < 0 || (n > 0 && (!seeds || !out || !count || !status))) return fail(LRVOL_ERR_ARG, "bad arguments");
+  if (!v->have_bezier || !v->have_accel) return fail(LRVOL_ERR_STATE, "streamlines need to_bezier and build_accel");
+  if (v->nc != 3) return fail(LRVOL_ERR_UNSUPPORTED, "streamlines need a 3-vector volume");
+  if (v->p[0] != v->p[1] || v->p[0] != v->p[2] || v->p[0] > 3)
+    return fail(LRVOL_ERR_UNSUPPORTED, "streamlines need equal degrees 1..3");
+  if (P->method < LRVOL_RK1 || P->method > LRVOL_RKF45) return fail(LRVOL_ERR_ARG, "bad method");
+  if (P->step_rule < LRVOL_SL_FIXED || P->step_rule > LRVOL_SL_ADAPTIVE) return fail(LRVOL_ERR_ARG, "bad step rule");
+  if (P->step_rule == LRVOL_SL_ADAPTIVE && P->method < LRVOL_HE)
+    return fail(LRVOL_ERR_ARG, "adaptive steps need an embedded pair (HE, BS, RKF45)");
+  if (P->step_rule != LRVOL_SL_ADAPTIVE ? !(P->h > 0) : !(P->h >= 0)) return fail(LRVOL_ERR_ARG, "bad step");
+  if (!(P->t_end > 0 && P->t_end < INFINITY)) return fail(LRVOL_ERR_ARG, "t_end must be positive and finite");
+  if (P->step_rule == LRVOL_SL_ADAPTIVE && !(P->tol > 0)) return fail(LRVOL_ERR_ARG, "tol must be > 0");
+  if (P->max_samples < 1) return fail(LRVOL_ERR_ARG, "max_samples must be >= 1");
+  if (n == 0) return LRVOL_OK;
+  SLParams sp;
+  std::memset(&sp, 0, sizeof(sp));
+  sp.elem = v->d_elem;
+  sp.n_elem = v->n_elem;
+  sp.bez = v->d_bez;
+  sp.elem_bytes = v->elem_bytes;
+  sp.forest = forest_view(v);
+  sp.status = v->d_status;
+  sp.method = P->method;
+  sp.rule = P->step_rule;
+  sp.max_samples = P->max_samples;
+  sp.h = P->h;
+  sp.t_end = P->t_end;
+  sp.tol_f = (float)P->tol;
+  CU(launch_streamlines(sp, v->p[0], v->storage, seeds, n, out, count, status, (cudaStream_t)stream),
+     "streamline kernel");
+  return LRVOL_OK;
+}
+
+int lrvol_streamline_error(const double *ref, const int32_t *rc, int32_t rmax, const double *app, const int32_t *ac,
+                           int32_t amax, int64_t n, double *sums, void *stream) {
+  if (n < 0 || rmax < 1 || amax < 1 || (n > 0 && (!ref || !rc || !app || !ac || !sums)))
+    return fail(LRVOL_ERR_ARG, "bad arguments");
+  if (n == 0) return LRVOL_OK;
+  CU(launch_streamline_error(ref, rc, rmax, app, ac, amax, n, sums, (cudaStream_t)stream), "streamline error kernel");
+  return LRVOL_OK;
+}
+
 int lrvol_get_bezier(lrvol_t v, double *host_out) {
   if (!v || !host_out) return fail(LRVOL_ERR_ARG, "null pointer");
   if (!v->have_bezier) return fail(LRVOL_ERR_STATE, "get_bezier needs to_bezier");

@@ -833,52 +833,62 @@ struct Block {
       }
       return F32 ? f : fmaf(sa, f, oa);
     } else {
-      float v0 = 0.f, v1 = 0.f, v2 = 0.f;
-      if constexpr (PAIRS) {
-        f2 X[N], Y[N];
-#pragma unroll
-        for (int i = 0; i < N; ++i) {
-          X[i] = f2_pack(bx[i], bx[i]);
-          Y[i] = f2_pack(by[i], by[i]);
-        }
-        f2 V = 0;
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          f2 T = 0;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            const f2 *c = &cp[(k * N + j) * N];
-            f2 S = f2_mul(c[0], X[0]);
-#pragma unroll
-            for (int i = 1; i < N; ++i) S = f2_fma(c[i], X[i], S);
-            T = j == 0 ? f2_mul(S, Y[0]) : f2_fma(S, Y[j], T);
-          }
-          const f2 Z = f2_pack(bz[k], bz[k]);
-          V = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, V);
-        }
-        f2_unpack(V, v0, v1);
-        if constexpr (!F32) {
-          v0 = fmaf(sa, v0, oa);
-          v1 = fmaf(sb, v1, ob);
-        }
-      }
-      if constexpr (COMP2) {
-#pragma unroll
-        for (int k = 0; k < N; ++k) {
-          float t = 0.f;
-#pragma unroll
-          for (int j = 0; j < N; ++j) {
-            float sx = 0.f;
-#pragma unroll
-            for (int i = 0; i < N; ++i) sx = fmaf(c2[(k * N + j) * N + i], bx[i], sx);
-            t = fmaf(sx, by[j], t);
-          }
-          v2 = fmaf(t, bz[k], v2);
-        }
-        if constexpr (!F32) v2 = fmaf(sc, v2, oc);
-      }
+      float v0, v1, v2;
+      components(bx, by, bz, v0, v1, v2);
       if constexpr (FIELD == 1) return sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
       return v2;
+    }
+  }
+
+  // Vector blocks: the components as evaluated (FIELD 1: all three; FIELD 2:
+  // the chosen component in v2).
+  __device__ __forceinline__ void components(const float *bx, const float *by, const float *bz, float &v0,
+                                             float &v1, float &v2) const {
+    v0 = 0.f;
+    v1 = 0.f;
+    v2 = 0.f;
+    if constexpr (PAIRS) {
+      f2 X[N], Y[N];
+#pragma unroll
+      for (int i = 0; i < N; ++i) {
+        X[i] = f2_pack(bx[i], bx[i]);
+        Y[i] = f2_pack(by[i], by[i]);
+      }
+      f2 V = 0;
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        f2 T = 0;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          const f2 *c = &cp[(k * N + j) * N];
+          f2 S = f2_mul(c[0], X[0]);
+#pragma unroll
+          for (int i = 1; i < N; ++i) S = f2_fma(c[i], X[i], S);
+          T = j == 0 ? f2_mul(S, Y[0]) : f2_fma(S, Y[j], T);
+        }
+        const f2 Z = f2_pack(bz[k], bz[k]);
+        V = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, V);
+      }
+      f2_unpack(V, v0, v1);
+      if constexpr (!F32) {
+        v0 = fmaf(sa, v0, oa);
+        v1 = fmaf(sb, v1, ob);
+      }
+    }
+    if constexpr (COMP2) {
+#pragma unroll
+      for (int k = 0; k < N; ++k) {
+        float t = 0.f;
+#pragma unroll
+        for (int j = 0; j < N; ++j) {
+          float sx = 0.f;
+#pragma unroll
+          for (int i = 0; i < N; ++i) sx = fmaf(c2[(k * N + j) * N + i], bx[i], sx);
+          t = fmaf(sx, by[j], t);
+        }
+        v2 = fmaf(t, bz[k], v2);
+      }
+      if constexpr (!F32) v2 = fmaf(sc, v2, oc);
     }
   }
 };
@@ -1204,11 +1214,11 @@ __global__ void k_mlp_pack(const float *__restrict__ p, uint16_t *__restrict__ o
   if (q >= kPacked) return;
   float w = 0.f;
   bool weight = false;
-  int K = 0, N = 0, base = 0, woff = 0;
-  if (q < kPkL2) { K = kIn; N = kHid; base = kPkL1; woff = kOffW1; weight = true; }
-  else if (q < kPkL3) { K = kHid; N = kHid; base = kPkL2; woff = kOffW2; weight = true; }
-  else if (q < kPkL4) { K = kHid; N = kHid; base = kPkL3; woff = kOffW3; weight = true; }
-  else if (q < kPkBias) { K = kHid; N = 8; base = kPkL4; woff = kOffW4; weight = true; }
+  int N = 0, base = 0, woff = 0;
+  if (q < kPkL2) { N = kHid; base = kPkL1; woff = kOffW1; weight = true; }
+  else if (q < kPkL3) { N = kHid; base = kPkL2; woff = kOffW2; weight = true; }
+  else if (q < kPkL4) { N = kHid; base = kPkL3; woff = kOffW3; weight = true; }
+  else if (q < kPkBias) { N = 8; base = kPkL4; woff = kOffW4; weight = true; }
   if (weight) {
     const int r = q - base;
     const int j = r & 3, lane = (r >> 2) & 31, tile = r >> 7;
@@ -1554,6 +1564,298 @@ cudaError_t launch_labels(const RenderParams &prm, int degree, float h_fine, flo
     case 3: k_labels<3><<<grid, 128, 0, s>>>(prm, h_fine, tau, cand, n_cand, label); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Streamlines (Sec. 5): dx/dt = f(x) by explicit Runge-Kutta methods (Eq. 5),
+// one thread per seed.  The outer loop keeps x as an unevaluated float pair
+// (hi + lo, about 48 significant bits) and t in FP64: on this GPU FP64
+// arithmetic runs at a small fraction of the FP32 rate, and compensated
+// FP32 sums keep the accumulation exact enough that the steps are not lost
+// to rounding (the reason for the paper's double-precision outer loop,
+// Sec. 5.5).  Stage increments h * sum a_ij k_j are formed in FP32 (they
+// are small against x) and added exactly; the field is evaluated in FP32
+// at the FP32 rounding of the stage point, reusing the element (box and
+// block in registers) while consecutive points stay in it.
+// ----------------------------------------------------------------------------
+namespace {
+
+struct __align__(32) SLSample {
+  double x, y, z, t;
+};
+
+struct SLTab {
+  int s, embedded, q_low;
+  float a[6][6], b[6], bh[6];
+};
+
+// Butcher tableaus in the order of LRVOL_RK1 .. LRVOL_RKF45 (coefficients in FP32).
+__constant__ SLTab c_sl_tab[9] = {
+    {1, 0, 0, {}, {1.f}, {}},
+    {2, 0, 0, {{0.f}, {0.5f}}, {0.f, 1.f}, {}},
+    {3, 0, 0, {{0.f}, {0.5f}, {-1.f, 2.f}}, {1.f / 6, 2.f / 3, 1.f / 6}, {}},
+    {4, 0, 0, {{0.f}, {0.5f}, {0.f, 0.5f}, {0.f, 0.f, 1.f}}, {1.f / 6, 1.f / 3, 1.f / 3, 1.f / 6}, {}},
+    {4, 0, 0, {{0.f}, {1.f / 3}, {-1.f / 3, 1.f}, {1.f, -1.f, 1.f}}, {0.125f, 0.375f, 0.375f, 0.125f}, {}},
+    {6, 0, 4,
+     {{0.f},
+      {0.25f},
+      {3.f / 32, 9.f / 32},
+      {1932.f / 2197, -7200.f / 2197, 7296.f / 2197},
+      {439.f / 216, -8.f, 3680.f / 513, -845.f / 4104},
+      {-8.f / 27, 2.f, -3544.f / 2565, 1859.f / 4104, -11.f / 40}},
+     {16.f / 135, 0.f, 6656.f / 12825, 28561.f / 56430, -9.f / 50, 2.f / 55},
+     {25.f / 216, 0.f, 1408.f / 2565, 2197.f / 4104, -0.2f, 0.f}},
+    {2, 1, 1, {{0.f}, {1.f}}, {0.5f, 0.5f}, {1.f, 0.f}},
+    {4, 1, 2, {{0.f}, {0.5f}, {0.f, 0.75f}, {2.f / 9, 1.f / 3, 4.f / 9}}, {2.f / 9, 1.f / 3, 4.f / 9, 0.f},
+     {7.f / 24, 0.25f, 1.f / 3, 0.125f}},
+    {6, 1, 4,
+     {{0.f},
+      {0.25f},
+      {3.f / 32, 9.f / 32},
+      {1932.f / 2197, -7200.f / 2197, 7296.f / 2197},
+      {439.f / 216, -8.f, 3680.f / 513, -845.f / 4104},
+      {-8.f / 27, 2.f, -3544.f / 2565, 1859.f / 4104, -11.f / 40}},
+     {16.f / 135, 0.f, 6656.f / 12825, 28561.f / 56430, -9.f / 50, 2.f / 55},
+     {25.f / 216, 0.f, 1408.f / 2565, 2197.f / 4104, -0.2f, 0.f}},
+};
+
+// x + d for x = hi + lo and a float d, renormalised (two-sum, then fast two-sum)
+__device__ __forceinline__ void ff_add(float &hi, float &lo, float d) {
+  const float s = __fadd_rn(hi, d);
+  const float bb = __fsub_rn(s, hi);
+  const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(d, bb));
+  const float t = __fadd_rn(e, lo);
+  hi = __fadd_rn(s, t);
+  lo = __fsub_rn(t, __fsub_rn(hi, s));
+}
+
+template <int P, int STORE>
+struct SLField {
+  static constexpr int N = P + 1;
+  float4 ra, rb, rc, rd;
+  uint32_t cur;
+  Block<P, 1, STORE> blk;
+
+  // f at the FP32 point p; false outside [0,1]^3 (or on a failed look-up)
+  __device__ __forceinline__ bool eval(const SLParams &sp, float px, float py, float pz, float &v0, float &v1,
+                                       float &v2) {
+    if (!(px >= 0.f && px <= 1.f && py >= 0.f && py <= 1.f && pz >= 0.f && pz <= 1.f)) return false;
+    if (!locate(sp, px, py, pz)) return false;
+    float bx[N], by[N], bz[N];
+    monomials<P>(local_u(px, ra.x, rc.x, rd.x), bx);
+    monomials<P>(local_u(py, ra.y, rc.y, rd.y), by);
+    monomials<P>(local_u(pz, ra.z, rc.z, rd.z), bz);
+    blk.components(bx, by, bz, v0, v1, v2);
+    return true;
+  }
+
+  __device__ __forceinline__ bool locate(const SLParams &sp, float px, float py, float pz) {
+    if (cur != kNone && px >= ra.x && py >= ra.y && pz >= ra.z && px < rb.x && py < rb.y && pz < rb.z) return true;
+    const uint32_t e = forest_lookup(sp.forest, px, py, pz, sp.status);
+    if (e == kNone || (int64_t)e >= sp.n_elem) {
+      set_status(sp.status, kStatusBounds);
+      return false;
+    }
+    cur = e;
+    load_record(sp.elem + e, ra, rb, rc, rd);
+    blk.load(sp.bez + (int64_t)e * sp.elem_bytes, 0);
+    return true;
+  }
+};
+
+template <int P, int STORE>
+__global__ void __launch_bounds__(128) k_streamlines(const __grid_constant__ SLParams sp,
+                                                     const double *__restrict__ seeds, int64_t n,
+                                                     SLSample *__restrict__ out, int32_t *__restrict__ count,
+                                                     int32_t *__restrict__ status) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const SLTab &T = c_sl_tab[sp.method];
+  SLField<P, STORE> F;
+  F.cur = kNone;
+  float xh[3], xl[3];
+  for (int a = 0; a < 3; ++a) {
+    const double s = seeds[3 * q + a];
+    xh[a] = __double2float_rn(s);
+    xl[a] = __double2float_rn(s - (double)xh[a]);
+  }
+  SLSample *o = out + q * (int64_t)sp.max_samples;
+  int nout = 0, st = 0;
+  float v0, v1, v2;
+  if (!(xh[0] >= 0.f && xh[0] <= 1.f && xh[1] >= 0.f && xh[1] <= 1.f && xh[2] >= 0.f && xh[2] <= 1.f) ||
+      !F.locate(sp, xh[0], xh[1], xh[2])) {
+    count[q] = 0;
+    status[q] = 1;
+    return;
+  }
+  o[0] = SLSample{(double)xh[0] + (double)xl[0], (double)xh[1] + (double)xl[1], (double)xh[2] + (double)xl[2],
+                  0.0};
+  nout = 1;
+  double t = 0.0;
+  float dsn = F.ra.w;  // Eq. 4 step of the element holding x_n
+  double h = sp.rule == 0 ? sp.h : (sp.rule == 1 ? sp.h * (double)dsn : (sp.h > 0.0 ? sp.h : (double)dsn));
+  for (;;) {
+    if (!(t < sp.t_end)) {
+      st = 0;
+      break;
+    }
+    if (nout >= sp.max_samples) {
+      st = 2;
+      break;
+    }
+    if (sp.rule == 1) h = sp.h * (double)dsn;
+    if (sp.rule == 0) h = sp.h;
+    bool taken = false, left = false;
+    float nh[3], nl[3];
+    for (int tries = 0; tries < 64 && !taken; ++tries) {
+      double hs = h;
+      bool last = false;
+      if (t + hs > sp.t_end) {
+        hs = sp.t_end - t;
+        last = true;
+      }
+      const float hf = __double2float_rn(hs);
+      float k[6][3];
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        if (i < T.s) {
+          float d0 = 0.f, d1 = 0.f, d2 = 0.f;
+#pragma unroll
+          for (int j = 0; j < i; ++j) {
+            const float a = T.a[i][j];
+            d0 = fmaf(a, k[j][0], d0);
+            d1 = fmaf(a, k[j][1], d1);
+            d2 = fmaf(a, k[j][2], d2);
+          }
+          float yh0 = xh[0], yl0 = xl[0], yh1 = xh[1], yl1 = xl[1], yh2 = xh[2], yl2 = xl[2];
+          if (i > 0) {
+            ff_add(yh0, yl0, hf * d0);
+            ff_add(yh1, yl1, hf * d1);
+            ff_add(yh2, yl2, hf * d2);
+          }
+          if (!left && !F.eval(sp, yh0, yh1, yh2, v0, v1, v2)) left = true;
+          k[i][0] = v0;
+          k[i][1] = v1;
+          k[i][2] = v2;
+        }
+      }
+      if (left) break;
+      float D0 = 0.f, D1 = 0.f, D2 = 0.f, E0 = 0.f, E1 = 0.f, E2 = 0.f;
+#pragma unroll
+      for (int i = 0; i < 6; ++i) {
+        if (i < T.s) {
+          const float b = T.b[i], e = T.b[i] - T.bh[i];
+          D0 = fmaf(b, k[i][0], D0);
+          D1 = fmaf(b, k[i][1], D1);
+          D2 = fmaf(b, k[i][2], D2);
+          E0 = fmaf(e, k[i][0], E0);
+          E1 = fmaf(e, k[i][1], E1);
+          E2 = fmaf(e, k[i][2], E2);
+        }
+      }
+      if (sp.rule == 2) {
+        const float err = hf * sqrtf(fmaf(E0, E0, fmaf(E1, E1, E2 * E2)));
+        float fac = err > 0.f ? 0.9f * powf(sp.tol_f / err, 1.f / (float)(T.q_low + 1)) : 5.f;
+        fac = fminf(fmaxf(fac, 0.2f), 5.f);
+        if (err > sp.tol_f) {
+          h = hs * (double)fac;
+          continue;
+        }
+        if (!last) h = hs * (double)fac;
+      }
+      for (int a = 0; a < 3; ++a) {
+        nh[a] = xh[a];
+        nl[a] = xl[a];
+      }
+      ff_add(nh[0], nl[0], hf * D0);
+      ff_add(nh[1], nl[1], hf * D1);
+      ff_add(nh[2], nl[2], hf * D2);
+      if (!(nh[0] >= 0.f && nh[0] <= 1.f && nh[1] >= 0.f && nh[1] <= 1.f && nh[2] >= 0.f && nh[2] <= 1.f) ||
+          !F.locate(sp, nh[0], nh[1], nh[2])) {
+        left = true;
+        break;
+      }
+      dsn = F.ra.w;
+      t = last ? sp.t_end : t + hs;
+      taken = true;
+    }
+    if (left) {
+      st = 1;
+      break;
+    }
+    if (!taken) {
+      st = 3;
+      break;
+    }
+    for (int a = 0; a < 3; ++a) {
+      xh[a] = nh[a];
+      xl[a] = nl[a];
+    }
+    o[nout++] = SLSample{(double)xh[0] + (double)xl[0], (double)xh[1] + (double)xl[1],
+                         (double)xh[2] + (double)xl[2], t};
+  }
+  count[q] = nout;
+  status[q] = st;
+}
+
+// Eq. 7 per streamline: sum over the approximation's samples i >= 1 of
+// (t_i - t_{i-1}) * |x_ref(t_i) - y_i|, x_ref linear between its samples.
+__global__ void k_streamline_error(const SLSample *__restrict__ ref, const int32_t *__restrict__ rc, int rmax,
+                                   const SLSample *__restrict__ app, const int32_t *__restrict__ ac, int amax,
+                                   int64_t n, double *__restrict__ sums) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n) return;
+  const SLSample *r = ref + q * (int64_t)rmax, *y = app + q * (int64_t)amax;
+  const int nr = rc[q], na = ac[q];
+  double acc = 0.0;
+  if (nr >= 2 && na >= 2) {
+    int j = 0;
+    const double tlast = r[nr - 1].t;
+    for (int i = 1; i < na; ++i) {
+      const SLSample p = y[i];
+      if (!(p.t <= tlast)) break;
+      while (j + 2 < nr && r[j + 1].t < p.t) ++j;
+      const SLSample r0 = r[j], r1 = r[j + 1];
+      const double dt = r1.t - r0.t;
+      const double f = dt > 0.0 ? (p.t - r0.t) / dt : 0.0;
+      const double ex = fma(f, r1.x - r0.x, r0.x) - p.x;
+      const double ey = fma(f, r1.y - r0.y, r0.y) - p.y;
+      const double ez = fma(f, r1.z - r0.z, r0.z) - p.z;
+      acc = fma(p.t - y[i - 1].t, sqrt(fma(ex, ex, fma(ey, ey, ez * ez))), acc);
+    }
+  }
+  sums[q] = acc;
+}
+
+}  // namespace
+
+cudaError_t launch_streamlines(const SLParams &sp, int degree, int storage, const double *seeds, int64_t n,
+                               double *out, int32_t *count, int32_t *status, cudaStream_t s) {
+  const unsigned blocks = (unsigned)((n + 127) / 128);
+  SLSample *o = reinterpret_cast<SLSample *>(out);
+#define LRVOL_SL_CASE(P_, S_) k_streamlines<P_, S_><<<blocks, 128, 0, s>>>(sp, seeds, n, o, count, status)
+  switch (degree * 3 + storage) {
+    case 3: LRVOL_SL_CASE(1, LRVOL_STORE_F32); break;
+    case 4: LRVOL_SL_CASE(1, LRVOL_STORE_F16); break;
+    case 5: LRVOL_SL_CASE(1, LRVOL_STORE_BF16); break;
+    case 6: LRVOL_SL_CASE(2, LRVOL_STORE_F32); break;
+    case 7: LRVOL_SL_CASE(2, LRVOL_STORE_F16); break;
+    case 8: LRVOL_SL_CASE(2, LRVOL_STORE_BF16); break;
+    case 9: LRVOL_SL_CASE(3, LRVOL_STORE_F32); break;
+    case 10: LRVOL_SL_CASE(3, LRVOL_STORE_F16); break;
+    case 11: LRVOL_SL_CASE(3, LRVOL_STORE_BF16); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef LRVOL_SL_CASE
+  return cudaGetLastError();
+}
+
+cudaError_t launch_streamline_error(const double *ref, const int32_t *rc, int rmax, const double *app,
+                                    const int32_t *ac, int amax, int64_t n, double *sums, cudaStream_t s) {
+  k_streamline_error<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(reinterpret_cast<const SLSample *>(ref), rc, rmax,
+                                                                 reinterpret_cast<const SLSample *>(app), ac, amax, n,
+                                                                 sums);
   return cudaGetLastError();
 }
 

@@ -209,6 +209,23 @@ struct FeatureParams {
 
 cudaError_t launch_features(const FeatureParams &fp, float *out, cudaStream_t s);
 
+// Streamlines (Sec. 5)
+struct SLParams {
+  const ElemRec *elem;
+  int64_t n_elem;
+  const unsigned char *bez;
+  int elem_bytes;
+  ForestView forest;
+  uint32_t *status;   // device status word (bounds)
+  int method, rule, max_samples;
+  double h, t_end;
+  float tol_f;
+};
+cudaError_t launch_streamlines(const SLParams &sp, int degree, int storage, const double *seeds, int64_t n,
+                               double *out, int32_t *count, int32_t *status, cudaStream_t s);
+cudaError_t launch_streamline_error(const double *ref, const int32_t *rc, int rmax, const double *app,
+                                    const int32_t *ac, int amax, int64_t n, double *sums, cudaStream_t s);
+
 // host.cpp: error reporting (sets the thread's last error, returns the status)
 int fail(int status, const std::string &msg);
 int cuda_fail(cudaError_t e, const char *what);

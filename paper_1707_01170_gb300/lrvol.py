@@ -30,8 +30,11 @@ EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_rende
             "lrvol_arena_largest_free", "lrvol_arena_destroy", "lrvol_server_create", "lrvol_server_set_step_model",
             "lrvol_server_set_priority_pixels",
             "lrvol_server_submit", "lrvol_server_progress", "lrvol_server_drain", "lrvol_server_poll", "lrvol_server_info",
-            "lrvol_server_release", "lrvol_server_get_stats", "lrvol_server_clock", "lrvol_server_destroy"]
+            "lrvol_server_release", "lrvol_server_get_stats", "lrvol_server_clock", "lrvol_server_destroy",
+            "lrvol_streamlines", "lrvol_streamline_error"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
+SL_METHODS = ["RK1", "RK2", "RK3", "RK4", "RK38", "RKF5", "HE", "BS", "RKF45"]
+SL_RULES = ["fixed", "heuristic", "adaptive"]
 MLP_IN, MLP_HIDDEN, MLP_PARAMS, MLP_PACKED = 16, 64, 9473, 10120
 
 
@@ -69,6 +72,11 @@ class Stats(ctypes.Structure):
         d = {k: getattr(self, k) for k, _ in self._fields_}
         d["blocks"] = list(self.blocks)
         return d
+
+
+class SLParams(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int32), ("step_rule", ctypes.c_int32), ("h", ctypes.c_double),
+                ("t_end", ctypes.c_double), ("tol", ctypes.c_double), ("max_samples", ctypes.c_int32)]
 
 
 class FrameInfo(ctypes.Structure):
@@ -145,6 +153,10 @@ def load(path: str = LIB_PATH):
         L.lrvol_labels.restype = ctypes.c_int
         L.lrvol_labels.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
                                    ctypes.c_double, ctypes.c_double, vp, i32, vp, vp]
+        L.lrvol_streamlines.restype = ctypes.c_int
+        L.lrvol_streamlines.argtypes = [vp, ctypes.POINTER(SLParams), vp, i64, vp, vp, vp, vp]
+        L.lrvol_streamline_error.restype = ctypes.c_int
+        L.lrvol_streamline_error.argtypes = [vp, vp, i32, vp, vp, i32, i64, vp, vp]
         L.lrvol_arena_create.restype = ctypes.c_int
         L.lrvol_arena_create.argtypes = [i64, i64, ctypes.POINTER(vp)]
         L.lrvol_arena_alloc.restype = i64
@@ -558,3 +570,33 @@ class Server:
 def clock() -> float:
     """The server's host clock (seconds, monotonic)."""
     return float(load().lrvol_server_clock())
+
+
+# ---- streamlines (Sec. 5) ----------------------------------------------------
+
+def streamlines(vol: "Volume", seeds, method: str, rule: str, h: float, t_end: float, tol: float = 0.0,
+                max_samples: int = 1024, out=None, stream=None):
+    """Streamlines from seeds (CUDA float64 tensor, n x 3): (samples n x max x 4
+    float64 (x, y, z, t), count n int32, status n int32), CUDA tensors."""
+    import torch
+    n = seeds.shape[0]
+    P = SLParams(SL_METHODS.index(method), SL_RULES.index(rule), float(h), float(t_end), float(tol),
+                 int(max_samples))
+    if out is None:
+        out = (torch.empty((n, max_samples, 4), dtype=torch.float64, device="cuda"),
+               torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.int32, device="cuda"))
+    samples, count, status = out
+    _check(load().lrvol_streamlines(vol.handle, ctypes.byref(P), _dev(seeds, torch.float64), n, _dev(samples),
+                                    _dev(count), _dev(status), _stream_ptr(stream)), "lrvol_streamlines")
+    return samples, count, status
+
+
+def streamline_error(ref, ref_count, app, app_count, stream=None):
+    """Eq. 7 per streamline (CUDA float64 tensor of n sums); E is their max."""
+    import torch
+    n = ref.shape[0]
+    sums = torch.empty(n, dtype=torch.float64, device="cuda")
+    _check(load().lrvol_streamline_error(_dev(ref, torch.float64), _dev(ref_count), ref.shape[1],
+                                         _dev(app, torch.float64), _dev(app_count), app.shape[1], n, _dev(sums),
+                                         _stream_ptr(stream)), "lrvol_streamline_error")
+    return sums

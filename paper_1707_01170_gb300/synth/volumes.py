@@ -387,6 +387,14 @@ def config3_render(width: int = 1920, height: int = 1080):
     return tf, cam
 
 
+def config3_seeds(n: int) -> np.ndarray:
+    """Streamline seeds for config 3: a seeded rake upstream of the obstacle,
+    x in [0.02, 0.10], y in [0.05, 0.95], z in [0.02, 0.60] (n x 3, FP64)."""
+    u = Stream(SEED_BASE + 3 + 2000, 3 * n + 8).take(3 * n).reshape(n, 3)
+    lo, hi = np.array([0.02, 0.05, 0.02]), np.array([0.10, 0.95, 0.60])
+    return lo + (hi - lo) * u
+
+
 # ----------------------------------------------------------------------------
 
 _BUILDERS = {1: config1, 2: config2, 3: config3}
