@@ -256,7 +256,7 @@ def _timed_frames(fns, steps: int, flush, stream):
     return [sum(e[q].elapsed_time(e[q + 1]) for e in evs) / steps for q in range(len(fns))]
 
 
-def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream):
+def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, model_path=None, save_path=None):
     """Learned step sizes with reduced-precision blocks against the plain FP32
     Eq. 4 renderer on the same frames (1920x1080 and 3840x2160): both images
     against the fine-step (1/2048) reference, and the learned frame timed
@@ -268,12 +268,17 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream):
     from paper_1707_01170_gb300.synth import volumes as V
     t0 = time.perf_counter()
     gv32 = plain["gv32"]
-    v1 = V.load_config(1)
-    tf1 = V.config1_render()[0]
-    g1 = lv.Volume(v1).build_accel(BLOCKS, stream=stream).to_bezier(stream=stream)
-    model, losses, rows = LS.fit([(g1, tf1), (gv32, tf)], step)
-    torch.cuda.synchronize()
-    g1.close()
+    if model_path:
+        model, losses, rows = LS.StepModel.load(model_path), [(0, None)], 0
+    else:
+        v1 = V.load_config(1)
+        tf1 = V.config1_render()[0]
+        g1 = lv.Volume(v1).build_accel(BLOCKS, stream=stream).to_bezier(stream=stream)
+        model, losses, rows = LS.fit([(g1, tf1), (gv32, tf)], step)
+        torch.cuda.synchronize()
+        g1.close()
+    if save_path:
+        model.save(save_path)
     train_s = time.perf_counter() - t0
     code = {"f32": lv.STORE_F32, "f16": lv.STORE_F16, "bf16": lv.STORE_BF16}[storage]
     gq = lv.Volume(vol).build_accel(BLOCKS, stream=stream).to_bezier(storage=code, stream=stream)
@@ -288,7 +293,8 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream):
            "gpu_launches_per_frame": 3, "frames_timed": steps,
            "model": {"train_s": train_s, "rows": rows, "loss": losses[-1][1], "tau": model.cfg.tau,
                      "margin": model.cfg.margin, "ymax": model.cfg.ymax, "steps": model.cfg.steps,
-                     "recipe": "16 seeded 320x180 cameras on each of configs 1 and 2"},
+                     "recipe": ("loaded from " + model_path) if model_path else
+                     "16 seeded 320x180 cameras on each of configs 1 and 2"},
            "by_resolution": {}}
     for (w, h) in ((WIDTH, HEIGHT), (3840, 2160)):
         ccam = lv.make_camera(V.config2_render(w, h, vol)[1])
@@ -489,7 +495,8 @@ def run_ours(args):
     if args.learned != "off" and ws == 1 and step.field == "scalar":
         if args.storage == "f32":
             plain = {"gv32": gv, "ms": ms_per_step, "samples": samples_per_frame, "img": out.clone()}
-            learned = learned_leg(vol, tf, step, plain, max(3, min(args.steps, 50)), args.learned, flush, stream)
+            learned = learned_leg(vol, tf, step, plain, max(3, min(args.steps, 50)), args.learned, flush, stream,
+                                  args.learned_model, args.save_learned_model)
 
     shading = None
     if ws == 1 and step.field == "scalar" and args.workload == "cfg2":
@@ -591,6 +598,8 @@ def main():
                     help="Bezier block storage (FP32 accumulation in every case)")
     ap.add_argument("--learned", default="f16", choices=["off", "f32", "f16", "bf16"],
                     help="also time learned step sizes with this block storage against plain FP32 Eq. 4")
+    ap.add_argument("--learned-model", default=None, help="load step-model weights instead of training")
+    ap.add_argument("--save-learned-model", default=None, help="write the trained step-model weights here")
     ap.add_argument("--serve", default="both", choices=["off", "plain", "learned", "both"],
                     help="frame-server runs over three resident volumes (learned needs --learned)")
     ap.add_argument("--no-streamlines", dest="streamlines", action="store_false",

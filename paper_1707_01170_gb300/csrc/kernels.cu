@@ -1149,6 +1149,10 @@ __device__ __forceinline__ void field_range(const FeatureParams &fp, int64_t e, 
 }
 
 __global__ void k_features(const __grid_constant__ FeatureParams fp, float *__restrict__ out) {
+  // the TF in shared memory: the bin scans below index it per lane
+  __shared__ float4 tfs[256];
+  for (int q = threadIdx.x; q < 256; q += blockDim.x) tfs[q] = fp.tf[q];
+  __syncthreads();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= fp.n_elem) return;
   const double *b = fp.box + 6 * e;
@@ -1167,10 +1171,10 @@ __global__ void k_features(const __grid_constant__ FeatureParams fp, float *__re
   float amax = 0.f, asum = 0.f, slope = 0.f;
   float cmin[3] = {1e30f, 1e30f, 1e30f}, cmax[3] = {-1e30f, -1e30f, -1e30f};
   for (int i = i0; i <= i1; ++i) {
-    const float4 t = fp.tf[i];
+    const float4 t = tfs[i];
     amax = fmaxf(amax, t.w);
     asum += t.w;
-    if (i < i1) slope = fmaxf(slope, fabsf(fp.tf[i + 1].w - t.w));
+    if (i < i1) slope = fmaxf(slope, fabsf(tfs[i + 1].w - t.w));
     cmin[0] = fminf(cmin[0], t.x); cmax[0] = fmaxf(cmax[0], t.x);
     cmin[1] = fminf(cmin[1], t.y); cmax[1] = fmaxf(cmax[1], t.y);
     cmin[2] = fminf(cmin[2], t.z); cmax[2] = fmaxf(cmax[2], t.z);
