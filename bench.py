@@ -194,9 +194,9 @@ def cpu_baseline(vol, tf, cam, step, samples_per_frame=None, target_s: float = 1
     return out
 
 
-def profiled_traffic():
-    """DRAM bytes per k_render launch from the committed ncu summary, if the
-    kernel source is unchanged since that capture; else None."""
+def profiled_counters():
+    """DRAM and L2 bytes per k_render launch from the committed ncu summary,
+    if the kernel source is unchanged since that capture; else None."""
     import hashlib
     try:
         prof = open(os.path.join(ROOT, "profiles", "k_render_cfg2_1080p.md")).read()
@@ -205,10 +205,17 @@ def profiled_traffic():
         return None
     sha = hashlib.sha256(src).hexdigest()[:16]
     fields = dict(ln.strip().split(": ", 1) for ln in prof.splitlines() if ln.strip().startswith(
-        ("kernels_cu_sha256_16:", "traffic_bytes_per_launch:")))
+        ("kernels_cu_sha256_16:", "traffic_bytes_per_launch:", "l2_bytes_per_launch:")))
     if fields.get("kernels_cu_sha256_16") != sha:
         return None
-    return int(fields["traffic_bytes_per_launch"])
+    return {"traffic": int(fields["traffic_bytes_per_launch"]), "l2": int(fields.get("l2_bytes_per_launch", 0)) or None}
+
+
+def measured_hbm_gbs():
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def run_reference(args):
@@ -551,10 +558,19 @@ def run_ours(args):
     fps = flop_per_sample(int(vol.deg[0]), step.field)
     flop = fps * samples_per_frame
     achieved = flop / (ms_per_step / 1e3) / 1e12
+    prof = profiled_counters() if (args.workload == "cfg2" and args.storage == "f32") else None
+    fcode = {"scalar": 0, "magnitude": 1, "component": 2}[step.field]
     roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": profiled_traffic() if args.workload == "cfg2" else None,
-            "kernel": f"k_render<{int(vol.deg[0])},{1 if step.field == 'magnitude' else 0}>", "flop_per_sample": fps,
+            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": prof["traffic"] if prof else None,
+            "kernel": f"k_render<{int(vol.deg[0])},{fcode},{args.storage}>", "flop_per_sample": fps,
             "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no FP32 figure measured)"}
+    hbm = measured_hbm_gbs()
+    if prof:
+        dram_gbs = prof["traffic"] / (ms_per_step / 1e3) / 1e9
+        roof["memory_side"] = {"dram_gbs": dram_gbs, "hbm_peak_gbs": hbm,
+                               "dram_frac": dram_gbs / hbm if hbm else None,
+                               "l2_gbs": prof["l2"] / (ms_per_step / 1e3) / 1e9 if prof["l2"] else None,
+                               "source": "ncu bytes per launch (profiles/k_render_cfg2_1080p.md) / event time"}
     line = {"metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
