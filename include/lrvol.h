@@ -428,6 +428,11 @@ int lrvol_server_set_step_model(lrvol_server_t s, const uint16_t *packed_dev, fl
  * (at most 32) before its CUDA context exists, or streams share hardware
  * queues and a small frame can wait behind a large one. */
 int lrvol_server_set_priority_pixels(lrvol_server_t s, int64_t max_pixels);
+/* With size tiers on: at most max_in_flight frames of the largest tier run at
+ * once (0, the default: slots - max(1, slots/4)).  Large frames each fill
+ * the GPU; running fewer of them side by side shortens each one's latency
+ * without lowering throughput. */
+int lrvol_server_set_large_cap(lrvol_server_t s, int32_t max_in_flight);
 /* Queue one frame.  cam, tf and step are copied.  host_out: NULL, or a host
  * buffer (pinned for an asynchronous copy) of height x width x 4 floats that
  * receives the image as part of the frame's work; the arena memory is then

@@ -143,6 +143,7 @@ struct lrvol_server_s {
   const uint16_t *packed = nullptr;
   float ymax = 0.f;
   int64_t priority_pixels = 0;  // tier 0 up to this many pixels, tier 1 up to 4 times as many, else tier 2
+  int large_cap = 0;            // most frames of the last tier in flight (0: slots - max(1, slots/4))
 };
 
 namespace {
@@ -259,7 +260,8 @@ int retire(lrvol_server_s *s, int32_t *n_retired) {
 void admit(lrvol_server_s *s) {
   const int nslots = (int)s->slots.size();
   const int reserve = s->priority_pixels > 0 ? (nslots / 4 > 1 ? nslots / 4 : 1) : 0;
-  const int cap_large = nslots - reserve > 1 ? nslots - reserve : 1;
+  int cap_large = nslots - reserve > 1 ? nslots - reserve : 1;
+  if (s->priority_pixels > 0 && s->large_cap > 0 && s->large_cap < cap_large) cap_large = s->large_cap;
   for (bool progress = true; progress;) {
     progress = false;
     for (int tier = 0; tier < kTiers; ++tier) {
@@ -377,6 +379,12 @@ int lrvol_server_set_step_model(lrvol_server_t s, const uint16_t *packed_dev, fl
 int lrvol_server_set_priority_pixels(lrvol_server_t s, int64_t max_pixels) {
   if (!s || max_pixels < 0) return fail(LRVOL_ERR_ARG, "bad arguments");
   s->priority_pixels = max_pixels;
+  return LRVOL_OK;
+}
+
+int lrvol_server_set_large_cap(lrvol_server_t s, int32_t max_in_flight) {
+  if (!s || max_in_flight < 0) return fail(LRVOL_ERR_ARG, "bad arguments");
+  s->large_cap = max_in_flight;
   return LRVOL_OK;
 }
 

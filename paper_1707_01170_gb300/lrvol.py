@@ -28,7 +28,7 @@ EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_rende
             "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels",
             "lrvol_arena_create", "lrvol_arena_alloc", "lrvol_arena_free", "lrvol_arena_used",
             "lrvol_arena_largest_free", "lrvol_arena_destroy", "lrvol_server_create", "lrvol_server_set_step_model",
-            "lrvol_server_set_priority_pixels",
+            "lrvol_server_set_priority_pixels", "lrvol_server_set_large_cap",
             "lrvol_server_submit", "lrvol_server_progress", "lrvol_server_drain", "lrvol_server_poll", "lrvol_server_info",
             "lrvol_server_release", "lrvol_server_get_stats", "lrvol_server_clock", "lrvol_server_destroy",
             "lrvol_streamlines", "lrvol_streamline_error"]
@@ -175,6 +175,8 @@ def load(path: str = LIB_PATH):
         L.lrvol_server_set_step_model.argtypes = [vp, vp, ctypes.c_float]
         L.lrvol_server_set_priority_pixels.restype = ctypes.c_int
         L.lrvol_server_set_priority_pixels.argtypes = [vp, i64]
+        L.lrvol_server_set_large_cap.restype = ctypes.c_int
+        L.lrvol_server_set_large_cap.argtypes = [vp, i32]
         L.lrvol_server_submit.restype = ctypes.c_int
         L.lrvol_server_submit.argtypes = [vp, vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
                                           vp, ctypes.POINTER(i64)]
@@ -502,6 +504,9 @@ class Server:
 
     def set_priority_pixels(self, max_pixels: int) -> None:
         _check(load().lrvol_server_set_priority_pixels(self._h, int(max_pixels)), "lrvol_server_set_priority_pixels")
+
+    def set_large_cap(self, max_in_flight: int) -> None:
+        _check(load().lrvol_server_set_large_cap(self._h, int(max_in_flight)), "lrvol_server_set_large_cap")
 
     def submit(self, vol: "Volume", cam, tf, step, host_out=None) -> int:
         c = cam if isinstance(cam, Camera) else make_camera(cam)
