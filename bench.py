@@ -390,6 +390,44 @@ def streamline_leg(stream, n_seeds: int = 65536, n_err: int = 4096, t_end: float
     return out
 
 
+FOREST_SWEEP = (1, 4, 16, 64, 256)
+
+
+def forest_leg(stream, frames: int = 20):
+    """The paper's look-up comparison (Sec. 4.3 tables) on the synthetic
+    volumes: for each forest resolution (trees per axis), the build time on
+    the host, the tree depth statistics and the 1080p frame time (cfg2
+    scalar and cfg3 |v|, Eq. 4 steps, L2 flushed between frames)."""
+    import torch
+    from paper_1707_01170_gb300 import lrvol as lv
+    from paper_1707_01170_gb300.synth import volumes as V
+    flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
+    out = []
+    for name in ("cfg2", "cfg3mag"):
+        vol, tf, cam, step = _workload(name)
+        ccam, ctf, cstep = lv.make_camera(cam), lv.make_tf(tf), lv.make_step(step)
+        img = torch.empty((HEIGHT, WIDTH, 4), dtype=torch.float32, device="cuda")
+        for b in FOREST_SWEEP:
+            gv = lv.Volume(vol)
+            t0 = time.perf_counter()
+            gv.build_accel((b, b, b), stream=stream)
+            torch.cuda.synchronize()
+            build_s = time.perf_counter() - t0
+            gv.to_bezier(stream=stream)
+            for _ in range(3):
+                gv.render(ccam, ctf, cstep, out=img, stream=stream)
+            torch.cuda.synchronize()
+            st = gv.stats()
+            ms = _timed_frames([lambda: gv.render(ccam, ctf, cstep, out=img, stream=stream)], frames, flush, stream)[0]
+            out.append({"workload": name, "trees_per_axis": b, "build_s": build_s, "nodes": st["n_nodes"],
+                        "depth": {"min": st["depth_min"], "max": st["depth_max"], "mean": st["depth_mean"],
+                                  "var": st["depth_var"]},
+                        "ms_per_frame": ms, "lookups_per_frame": st["lookups"],
+                        "gsamples_per_s": st["samples"] / (ms / 1e3) / 1e9})
+            gv.close()
+    return out
+
+
 SERVE_PLAN = ((60.0, 500), (120.0, 1000), (240.0, 2000))   # (requests/s, requests): about 8 s each
 
 
@@ -528,6 +566,8 @@ def run_ours(args):
     if args.streamlines and ws == 1:
         sl = streamline_leg(stream)
 
+    forest = forest_leg(stream) if (args.forest_sweep and ws == 1) else None
+
     serving = None
     if args.serve != "off" and ws == 1:
         modes = ["plain", "learned"] if args.serve == "both" else [args.serve]
@@ -591,6 +631,8 @@ def run_ours(args):
         line["shading"] = shading
     if sl is not None:
         line["streamlines"] = sl
+    if forest is not None:
+        line["forest_sweep"] = forest
     if serving is not None:
         line["serving"] = serving
     if not args.no_cpu_baseline:
@@ -618,6 +660,8 @@ def main():
     ap.add_argument("--save-learned-model", default=None, help="write the trained step-model weights here")
     ap.add_argument("--serve", default="both", choices=["off", "plain", "learned", "both"],
                     help="frame-server runs over three resident volumes (learned needs --learned)")
+    ap.add_argument("--forest-sweep", action="store_true",
+                    help="also time the frame for 1^3 .. 256^3 trees (the paper's look-up comparison)")
     ap.add_argument("--no-streamlines", dest="streamlines", action="store_false",
                     help="skip the streamline runs on config 3")
     args = ap.parse_args()
