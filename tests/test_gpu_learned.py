@@ -303,3 +303,23 @@ def test_step_model_save_load(trained, tmp_path):
     assert torch.equal(again.params, model.params)
     assert again.cfg.tau == model.cfg.tau and again.cfg.margin == model.cfg.margin and again.cfg.cand == model.cfg.cand
     assert torch.equal(again.packed, model.packed)
+
+
+@pytest.mark.slow
+def test_learned_render_full_size_sampled(trained):
+    """The learned benchmark frame (cfg2, 1920x1080, trained multipliers,
+    alpha_stop 0.99) on sampled pixels: the oracle steps with the same FP32
+    multipliers."""
+    model, losses, gvs, tfs, step = trained
+    vol = V.load_config(2)
+    tf = _f32_tf(V.config2_render(vol=vol)[0])
+    cam = V.config2_render(vol=vol)[1]
+    mult = model.multipliers(gvs[2], cam, tf, step)
+    lstep = V.StepParams(mode="learned", xi=1 / 256, alpha_stop=0.99, mult=mult)
+    img = gvs[2].render(cam, tf, lstep).cpu().numpy()
+    rng = np.random.default_rng(8)
+    pix = np.stack([rng.integers(0, cam.width, 48), rng.integers(0, cam.height, 48)], axis=1).astype(np.int32)
+    ostep = V.StepParams(mode="learned", xi=1 / 256, alpha_stop=0.99, mult=mult.cpu().numpy())
+    ref, _ = Oracle(vol).render(cam, tf, ostep, pixels=pix)
+    assert _rmse(img[pix[:, 1], pix[:, 0]], ref) <= 1e-4
+    assert float(mult.min()) >= 1.0 and float(mult.max()) <= 8.0 and float(mult.mean()) > 1.5

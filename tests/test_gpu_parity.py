@@ -300,6 +300,51 @@ def test_render_cfg2_full_size_sampled():
     assert st["samples"] > 0 and st["rays_hit"] > 0
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("field", ["magnitude", "component"])
+def test_render_cfg3_full_size_sampled(field):
+    """The vector benchmark configurations (388,016 elements, knots not FP32
+    exact, 1920x1080, |v| or v_x, 64^3 forest) on sampled pixels."""
+    vol = V.load_config(3)
+    tf, cam = V.config3_render()
+    tf = _f32_tf(tf)
+    if field == "magnitude":
+        tf.vmin, tf.vmax = 0.0, 1.5
+        step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, field="magnitude")
+    else:
+        tf.vmin, tf.vmax = -0.5, 1.5
+        step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, field="component", component=0)
+    pix = _sample_pixels(cam, 40, 4)
+    img, ref, st, ost = _render_pair(vol, Oracle(vol), cam, tf, step, blocks=(64, 64, 64), pixels=pix)
+    assert _rmse(img, ref) <= RMSE_TOL
+    assert np.abs(ref[:, 3]).max() > 0.05              # the sampled rays see the field
+
+
+@pytest.mark.parametrize("mode", ["fixed", "heuristic"])
+def test_render_eye_inside_volume(vols, oracles, mode):
+    """A perspective eye inside [0,1]^3: rays start at t = 0, not at a face."""
+    tf, _ = V.config1_render()
+    tf = _f32_tf(tf)
+    cam = V.Camera("persp", 48, 40, eye=(0.47, 0.52, 0.55), target=(0.9, 0.2, 0.1), up=(0.0, 0.0, 1.0),
+                   fovy=np.deg2rad(70.0))
+    step = V.StepParams(mode=mode, h=1 / 300, xi=1 / 256, alpha_stop=1.0)
+    img, ref, st, ost = _render_pair(vols["cfg1"], oracles["cfg1"], cam, tf, step, blocks=(32, 32, 32))
+    assert _rmse(img, ref) <= RMSE_TOL
+    assert st["rays_hit"] == ost["rays_hit"] == 48 * 40
+    assert abs(st["samples"] - ost["samples"]) <= 0.001 * ost["samples"]
+
+
+def test_render_one_pixel_and_extreme_aspect(vols, oracles):
+    tf, _ = V.config1_render()
+    tf = _f32_tf(tf)
+    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
+    for w, h in ((1, 1), (257, 1), (1, 129)):
+        cam = V.orbit_camera(V.Stream(70 + w + h), w, h)
+        img, ref, st, ost = _render_pair(vols["cfg1"], oracles["cfg1"], cam, tf, step, blocks=(16, 16, 16))
+        assert img.shape == (h, w, 4)
+        assert _rmse(img, ref) <= RMSE_TOL
+
+
 def test_render_shards_reassemble(vols):
     """Screen-space shards (row ranges of 3 ranks, rendered here in turn) give
     the full frame bitwise."""
