@@ -191,6 +191,15 @@ def cpu_baseline(vol, tf, cam, step, samples_per_frame=None, target_s: float = 1
            "sample": f"{256 + n} seeded pixels of the same 1920x1080 frame ({samples} samples, {dt:.1f} s)"}
     if samples_per_frame:
         out["extrapolated_ms_per_frame"] = 1e3 * samples_per_frame / (value * 1e9)
+    # a whole frame the oracle finishes: config 1, 128x128, Eq. 4 steps
+    from paper_1707_01170_gb300.synth import volumes as V
+    v1 = V.load_config(1)
+    tf1, cams1 = V.config1_render()
+    o1 = Oracle(v1)
+    t0 = time.perf_counter()
+    _, st1 = o1.render(cams1[1], tf1, V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99))
+    out["config1_full_frame"] = {"frame": "128x128 oblique view, Eq. 4 steps", "s": time.perf_counter() - t0,
+                                 "samples": st1["samples"], "cores": o1.threads}
     return out
 
 
