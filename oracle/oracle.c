@@ -349,6 +349,7 @@ typedef struct {
   const float *mult; /* mode 2: per-element step multipliers (FP32) */
   int32_t shading;   /* 1: gradient shading of C_src (Sec. 4.1) */
   double light[3];   /* towards the light; all zero: towards the eye along the ray */
+  const float *trim; /* NULL, or per pixel (t_front, t_back) of a trimming mesh (orc_trim) */
 } orc_step;
 
 typedef struct {
@@ -422,6 +423,113 @@ static int ray_setup(const ray_consts *k, int i, int j, float o[3], float d[3], 
   return t0 < t1;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Trimming (Sec. 4.1): the ray interval is cut to the first front face and  */
+/* the last back face of a closed triangle mesh, the two depth buffers of a  */
+/* z-prepass.  Hits use the watertight ray/triangle test of Woop, Benthin    */
+/* and Wald (JCGT 2013) in FP32 with the kernel's order of operations (hits  */
+/* are decisions), falling back to FP64 for an edge function that is        */
+/* exactly 0.  Front faces are those wound counter-clockwise seen from the   */
+/* ray's origin side (det > 0).                                              */
+/* ------------------------------------------------------------------------ */
+static int tri_hit(const float o[3], const float d[3], const float *v, float *t, int *front) {
+  int kz = 0;
+  if (fabsf(d[1]) > fabsf(d[kz])) kz = 1;
+  if (fabsf(d[2]) > fabsf(d[kz])) kz = 2;
+  int kx = kz == 2 ? 0 : kz + 1, ky = kx == 2 ? 0 : kx + 1;
+  if (d[kz] < 0.0f) {
+    int w = kx;
+    kx = ky;
+    ky = w;
+  }
+  const float Sx = d[kx] / d[kz], Sy = d[ky] / d[kz], Sz = 1.0f / d[kz];
+  float A[3], B[3], C[3];
+  for (int c = 0; c < 3; ++c) {
+    A[c] = v[c] - o[c];
+    B[c] = v[3 + c] - o[c];
+    C[c] = v[6 + c] - o[c];
+  }
+  const float Ax = A[kx] - Sx * A[kz], Ay = A[ky] - Sy * A[kz];
+  const float Bx = B[kx] - Sx * B[kz], By = B[ky] - Sy * B[kz];
+  const float Cx = C[kx] - Sx * C[kz], Cy = C[ky] - Sy * C[kz];
+  float U = Cx * By - Cy * Bx, V = Ax * Cy - Ay * Cx, W = Bx * Ay - By * Ax;
+  if (U == 0.0f || V == 0.0f || W == 0.0f) {
+    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+    V = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+  }
+  if ((U < 0.0f || V < 0.0f || W < 0.0f) && (U > 0.0f || V > 0.0f || W > 0.0f)) return 0;
+  const float det = U + V + W;
+  if (det == 0.0f) return 0;
+  const float Az = Sz * A[kz], Bz = Sz * B[kz], Cz = Sz * C[kz];
+  const float T = U * Az + V * Bz + W * Cz;
+  if (det > 0.0f ? !(T > 0.0f) : !(T < 0.0f)) return 0; /* hits at t <= 0 do not count */
+  *t = T / det;
+  *front = det > 0.0f;
+  return 1;
+}
+
+typedef struct {
+  const orc_camera *cam;
+  const float *tri;
+  int64_t n_tri;
+  float *out;
+  int tid, nth;
+} trim_job;
+
+static void *trim_worker(void *arg) {
+  trim_job *J = (trim_job *)arg;
+  ray_consts K;
+  camera_consts(J->cam, &K);
+  const int64_t npix = (int64_t)J->cam->width * J->cam->height;
+  for (int64_t q = J->tid; q < npix; q += J->nth) {
+    const int i = (int)(q % J->cam->width), j = (int)(q / J->cam->width);
+    float o[3], d[3], tin, tout;
+    ray_setup(&K, i, j, o, d, &tin, &tout);
+    float tf = INFINITY, tb = 0.0f;
+    for (int64_t k = 0; k < J->n_tri; ++k) {
+      float t;
+      int front;
+      if (!tri_hit(o, d, J->tri + 9 * k, &t, &front)) continue;
+      if (front) {
+        if (t < tf) tf = t;
+      } else if (t > tb) {
+        tb = t;
+      }
+    }
+    J->out[2 * q] = tf;
+    J->out[2 * q + 1] = tb;
+  }
+  return NULL;
+}
+
+/* Per pixel (t_front, t_back): the nearest front-face hit (+inf if none) and
+ * the farthest back-face hit (0 if none) of n_tri triangles (n x 9 floats). */
+void orc_trim(const orc_camera *cam, const float *tri, int64_t n_tri, float *out, int nth) {
+  if (nth < 1) nth = 1;
+  pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nth);
+  trim_job *jobs = (trim_job *)malloc(sizeof(trim_job) * nth);
+  for (int t = 0; t < nth; ++t) {
+    trim_job J = {cam, tri, n_tri, out, t, nth};
+    jobs[t] = J;
+    pthread_create(&th[t], NULL, trim_worker, &jobs[t]);
+  }
+  for (int t = 0; t < nth; ++t) pthread_join(th[t], NULL);
+  free(th);
+  free(jobs);
+}
+
+/* The ray interval [tin, tout] cut by a pixel's trimming interval: no hit
+ * hides the pixel; only back faces (the eye inside the mesh) keep [tin,
+ * t_back]; only front faces (an open mesh) keep [t_front, tout]. */
+static int trim_interval(const float *tr, float *tin, float *tout) {
+  const float tf = tr[0], tb = tr[1];
+  if (tf == INFINITY && tb == 0.0f) return 0;
+  if (tf != INFINITY && tf > *tin) *tin = tf;
+  if (tb != 0.0f && tb < *tout) *tout = tb;
+  return *tin < *tout;
+}
+
 /* Eq. 4: 2^-d times the shortest side of element e, d = max degree, rounded once to FP32. */
 float orc_heuristic_step(const orc_vol *v, uint32_t e) {
   const double *b = v->box + 6 * (int64_t)e;
@@ -478,6 +586,7 @@ static void *render_worker(void *arg) {
     out[0] = out[1] = out[2] = out[3] = 0.0;
     float o[3], d[3], tin, tout;
     if (!ray_setup(&K, i, j, o, d, &tin, &tout)) continue;
+    if (J->st->trim && !trim_interval(J->st->trim + 2 * ((int64_t)j * J->cam->width + i), &tin, &tout)) continue;
     J->stats.rays_hit++;
     double C[3] = {0, 0, 0}, A = 0.0;
     uint32_t cur = ORC_NONE;

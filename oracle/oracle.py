@@ -72,7 +72,8 @@ class _TF(ctypes.Structure):
 class _Step(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("field", ctypes.c_int32), ("component", ctypes.c_int32),
                 ("h", ctypes.c_double), ("xi", ctypes.c_double), ("alpha_stop", ctypes.c_double),
-                ("mult", ctypes.c_void_p), ("shading", ctypes.c_int32), ("light", ctypes.c_double * 3)]
+                ("mult", ctypes.c_void_p), ("shading", ctypes.c_int32), ("light", ctypes.c_double * 3),
+                ("trim", ctypes.c_void_p)]
 
 
 class _SLParams(ctypes.Structure):
@@ -120,6 +121,7 @@ def _load():
         L.orc_labels.argtypes = [vp, ctypes.POINTER(_Cam), ctypes.POINTER(_TF), ctypes.POINTER(_Step),
                                  ctypes.c_double, ctypes.c_double, vp, i32, vp, i32]
         L.orc_streamlines.argtypes = [vp, ctypes.POINTER(_SLParams), vp, i64, vp, vp, vp, i32]
+        L.orc_trim.argtypes = [ctypes.POINTER(_Cam), vp, i64, vp, i32]
         L.orc_ray.restype = i32
         L.orc_ray.argtypes = [ctypes.POINTER(_Cam), i32, i32, vp, vp, vp, vp]
         _lib = L
@@ -315,6 +317,11 @@ class Oracle:
         s.component = int(step.component)
         s.h, s.xi, s.alpha_stop = float(step.h), float(step.xi), float(step.alpha_stop)
         s.shading = {"none": 0, "gradient": 1}[getattr(step, "shading", "none")]
+        trim = getattr(step, "trim", None)
+        if trim is not None:
+            trim = np.ascontiguousarray(trim, dtype=np.float32)
+            assert trim.shape == (cam.height, cam.width, 2)
+            s.trim = trim.ctypes.data
         for a, x in enumerate(getattr(step, "light", (0.0, 0.0, 0.0))):
             s.light[a] = float(x)
         c = _cam(cam)
@@ -369,3 +376,14 @@ def streamline_error(ref, ref_count, approx, approx_count):
         x = np.stack([np.interp(t, r[:, 3], r[:, c]) for c in range(3)], axis=1)
         sums[j] = float(np.sum(dt * np.linalg.norm(x - a[1:, :3][keep], axis=1)))
     return sums, float(sums.max()) if len(sums) else 0.0
+
+
+def trim(cam, tris, threads: int | None = None):
+    """Per-pixel trimming interval (H, W, 2) float32: nearest front-face hit
+    (+inf if none) and farthest back-face hit (0 if none) of the triangles
+    (n x 3 x 3 FP32 vertices, counter-clockwise seen from outside)."""
+    tri = np.ascontiguousarray(tris, dtype=np.float32).reshape(-1, 9)
+    out = np.zeros((cam.height, cam.width, 2), dtype=np.float32)
+    _load().orc_trim(ctypes.byref(_cam(cam)), tri.ctypes.data, len(tri), out.ctypes.data,
+                     _threads(threads or 0))
+    return out

@@ -61,6 +61,7 @@ class StepParams:
     mult: object = None      # learned: per-element step multipliers (array or device tensor)
     shading: str = "none"    # "none" | "gradient" (scalar fields: C_src times max(0.4, |l . n|))
     light: tuple = (0.0, 0.0, 0.0)   # towards the light; zero = from the eye
+    trim: object = None      # per-pixel (t_front, t_back) of a trimming mesh (array or device tensor)
 
 
 def seeded_tf(stream: Stream, n_ctrl: int = 8, alpha_max: float = 0.08, bands=()) -> TransferFunction:
@@ -393,6 +394,51 @@ def config3_seeds(n: int) -> np.ndarray:
     u = Stream(SEED_BASE + 3 + 2000, 3 * n + 8).take(3 * n).reshape(n, 3)
     lo, hi = np.array([0.02, 0.05, 0.02]), np.array([0.10, 0.95, 0.60])
     return lo + (hi - lo) * u
+
+
+# ----------------------------------------------------------------------------
+# trimming meshes (closed, counter-clockwise seen from outside)
+# ----------------------------------------------------------------------------
+
+def box_mesh(lo, hi) -> np.ndarray:
+    """The 12 triangles of an axis-aligned box, (12, 3, 3)."""
+    lo, hi = np.asarray(lo, dtype=np.float64), np.asarray(hi, dtype=np.float64)
+    c = np.array([[lo[0] if (k & 1) == 0 else hi[0], lo[1] if (k & 2) == 0 else hi[1],
+                   lo[2] if (k & 4) == 0 else hi[2]] for k in range(8)])
+    quads = [(0, 2, 3, 1), (4, 5, 7, 6), (0, 1, 5, 4), (2, 6, 7, 3), (0, 4, 6, 2), (1, 3, 7, 5)]
+    tris = []
+    for a, b, cc, d in quads:        # each face counter-clockwise seen from outside
+        tris.append([c[a], c[b], c[cc]])
+        tris.append([c[a], c[cc], c[d]])
+    return np.array(tris)
+
+
+def icosphere(centre=(0.5, 0.5, 0.5), radius: float = 0.3, subdiv: int = 3) -> np.ndarray:
+    """A sphere tessellated from an icosahedron by subdiv 4-way splits,
+    20 * 4^subdiv triangles, (n, 3, 3)."""
+    t = (1 + 5 ** 0.5) / 2
+    v = [(-1, t, 0), (1, t, 0), (-1, -t, 0), (1, -t, 0), (0, -1, t), (0, 1, t), (0, -1, -t), (0, 1, -t),
+         (t, 0, -1), (t, 0, 1), (-t, 0, -1), (-t, 0, 1)]
+    v = [np.array(p, dtype=np.float64) / np.linalg.norm(p) for p in v]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4), (11, 10, 2), (10, 7, 6),
+         (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8), (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10),
+         (8, 6, 7), (9, 8, 1)]
+    for _ in range(subdiv):
+        cache, nf = {}, []
+
+        def mid(a, b):
+            key = (min(a, b), max(a, b))
+            if key not in cache:
+                m = v[a] + v[b]
+                v.append(m / np.linalg.norm(m))
+                cache[key] = len(v) - 1
+            return cache[key]
+        for a, b, c in f:
+            ab, bc, ca = mid(a, b), mid(b, c), mid(c, a)
+            nf += [(a, ab, ca), (b, bc, ab), (c, ca, bc), (ab, bc, ca)]
+        f = nf
+    V_ = np.asarray(v) * radius + np.asarray(centre, dtype=np.float64)
+    return V_[np.asarray(f)]
 
 
 # ----------------------------------------------------------------------------

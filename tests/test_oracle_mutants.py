@@ -4,8 +4,9 @@ Each case edits one line of oracle.c (a dropped term, a wrong index or sign,
 a transposed axis, an off-by-one), builds the edited copy on the CPU into a
 temporary directory, points the oracle module at it, and runs the pins of
 test_oracle_pins, the label pins of test_oracle_learned and the gradient and
-shading pins of test_oracle_shading and the streamline pins of
-test_oracle_streamlines; at least one must fail.  The default build is restored
+shading pins of test_oracle_shading, the streamline pins of
+test_oracle_streamlines and the trimming pins of test_oracle_trim; at least
+one must fail.  The default build is restored
 afterwards.  No GPU is involved.
 """
 import os
@@ -16,6 +17,7 @@ import oracle.oracle as orc
 import test_oracle_learned as L
 import test_oracle_shading as S
 import test_oracle_streamlines as SL
+import test_oracle_trim as T
 import test_oracle_pins as P
 
 SRC = os.path.join(os.path.dirname(orc.__file__), "oracle.c")
@@ -83,6 +85,8 @@ MUTANTS = [
      "T->a[3][0] = 1.0; T->a[3][1] = 1.0; T->a[3][2] = 1.0;"),
     ("Fehlberg fifth-order weight sign", "T->b[4] = -9.0 / 50;", "T->b[4] = 9.0 / 50;"),
     ("stages evaluated at x_n", "y[a] = x[a] + hs * acc;", "y[a] = x[a];"),
+    ("trimming takes back faces for front faces", "*front = det > 0.0f;", "*front = det < 0.0f;"),
+    ("trimming ignores the back faces", "if (tb != 0.0f && tb < *tout) *tout = tb;", ""),
     ("streamline Eq. 4 step without the element", "if (P->step_rule == 1) h = P->h * (double)orc_heuristic_step(v, e);",
      "if (P->step_rule == 1) h = P->h;"),
 ]
@@ -119,6 +123,10 @@ def _pins(cfg1):
                                                                         [1.0, 0.0, 1.0]))
     yield lambda: S.test_shading_of_a_constant_field_is_0p4(cfg1)
     yield lambda: S.test_shading_closed_forms_linear_field()
+    yield lambda: T.test_box_intervals_along_z()
+    yield lambda: T.test_sphere_is_watertight()
+    yield lambda: T.test_trimmed_constant_field_closed_form(cfg1, "outside")
+    yield lambda: T.test_trimmed_constant_field_closed_form(cfg1, "inside")
     H = orc.Oracle(SL.helix_volume())
     for m in sorted(SL.ORDERS):
         yield lambda m=m: SL.test_fixed_step_order(H, m)
