@@ -399,6 +399,30 @@ def streamline_leg(stream, n_seeds: int = 65536, n_err: int = 4096, t_end: float
     return out
 
 
+def trim_leg(gv, vol, tf, cam, step, flush, stream, reps: int = 10):
+    """Trimming (Sec. 4.1) at 1920x1080: the per-pixel interval of a
+    2.4M-triangle sphere (latitude-longitude tessellation) inside the cfg2
+    volume, computed by lrvol_trim (timed), and the trimmed frame."""
+    import torch
+    from paper_1707_01170_gb300 import lrvol as lv
+    from paper_1707_01170_gb300.synth import volumes as V
+    mesh = torch.from_numpy(np.ascontiguousarray(V.uv_sphere((0.5, 0.5, 0.5), 0.35, 1000, 1200),
+                                                 dtype=np.float32)).cuda()
+    ccam = lv.make_camera(cam)
+    tr = torch.empty((cam.height, cam.width, 2), dtype=torch.float32, device="cuda")
+    lv.trim(ccam, mesh, out=tr, stream=stream)
+    ms_trim = _timed_frames([lambda: lv.trim(ccam, mesh, out=tr, stream=stream)], reps, flush, stream)[0]
+    tstep = lv.make_step(V.StepParams(mode=step.mode, xi=step.xi, alpha_stop=step.alpha_stop, trim=tr))
+    ctf = lv.make_tf(tf)
+    out = torch.empty((cam.height, cam.width, 4), dtype=torch.float32, device="cuda")
+    gv.render(ccam, ctf, tstep, out=out, stream=stream)
+    ms_render = _timed_frames([lambda: gv.render(ccam, ctf, tstep, out=out, stream=stream)], reps, flush, stream)[0]
+    st = gv.stats()
+    return {"mesh": "latitude-longitude sphere, radius 0.35, 2,400,000 triangles", "ms_trim": ms_trim,
+            "ms_trimmed_frame": ms_render, "samples_per_frame": st["samples"], "rays_kept": st["rays_hit"],
+            "reps": reps}
+
+
 FOREST_SWEEP = (1, 4, 16, 64, 256)
 
 
@@ -575,6 +599,10 @@ def run_ours(args):
     if args.streamlines and ws == 1:
         sl = streamline_leg(stream)
 
+    trimming = None
+    if ws == 1 and args.workload == "cfg2":
+        trimming = trim_leg(gv, vol, tf, cam, step, flush, stream)
+
     forest = forest_leg(stream) if (args.forest_sweep and ws == 1) else None
 
     serving = None
@@ -642,6 +670,8 @@ def run_ours(args):
         line["streamlines"] = sl
     if forest is not None:
         line["forest_sweep"] = forest
+    if trimming is not None:
+        line["trimming"] = trimming
     if serving is not None:
         line["serving"] = serving
     if not args.no_cpu_baseline:

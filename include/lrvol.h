@@ -100,7 +100,11 @@ typedef struct {
  * I = max(0.4, |l . n|), with n = grad f / max(|grad f|, eps) at the sample,
  * eps = 1e-3 (vmax - vmin) (a gradient below eps counts as none, and I
  * tends to 0.4 continuously), and l the unit vector towards the light:
- * `light` normalised, or -d (a light at the eye) when `light` is all zero. */
+ * `light` normalised, or -d (a light at the eye) when `light` is all zero.
+ * Trimming (Sec. 4.1): with `trim` set, a pixel's [t_in, t_out] is cut to
+ * [t_front, t_back]; a pixel with neither hit is transparent, one with only
+ * back-face hits (the eye inside the mesh) keeps [t_in, t_back], one with
+ * only front-face hits (an open mesh) keeps [t_front, t_out]. */
 typedef struct {
   int32_t mode;      /* LRVOL_STEP_FIXED | LRVOL_STEP_HEURISTIC | LRVOL_STEP_LEARNED */
   int32_t field;     /* LRVOL_FIELD_SCALAR | _MAGNITUDE (|v| of a 3-vector) | _COMPONENT */
@@ -111,6 +115,8 @@ typedef struct {
   const float *mult; /* LEARNED: n_elem step multipliers (device), read during the render */
   int32_t shading;   /* LRVOL_SHADE_NONE | LRVOL_SHADE_GRADIENT (scalar fields only) */
   double light[3];   /* GRADIENT: direction towards the light (any length); all zero = -ray direction */
+  const float *trim; /* NULL, or per pixel (t_front, t_back) from lrvol_trim (device, height x width x 2
+                        floats, row major), read during the render */
 } lrvol_step;
 
 /* Diagnostics; the depth rows match the paper's tables (Sec. 4.3). */
@@ -289,6 +295,22 @@ int lrvol_eval_grad(lrvol_t vol, const float *pts_dev, int64_t n, float *val_gra
 /* Copy the FP64 Bezier blocks to host_out: n_elem x ncomp x (p3+1) x (p2+1)
  * x (p1+1) doubles, x index fastest.  Synchronous. */
 int lrvol_get_bezier(lrvol_t vol, double *host_out);
+
+/* ---------------------------------------------------------------------------
+ * Trimming by a boundary mesh (Sec. 4.1), the two depth buffers of a
+ * z-prepass computed by ray casting: for every pixel ray (as lrvol_render
+ * generates it), t_front = the nearest hit on a front face (+inf if none)
+ * and t_back = the farthest hit on a back face (0 if none), hits at t <= 0
+ * ignored.  Triangles are counter-clockwise seen from outside; a face is
+ * front-facing when the ray sees that winding.  Hits are decided by the
+ * watertight ray/triangle test of Woop, Benthin and Wald (JCGT 2013) in FP32,
+ * retrying an edge function that is exactly 0 in FP64, so rays through
+ * shared edges and vertices are not lost.  Each triangle is handled by one
+ * warp over the pixels of its conservative screen box.
+ * tri_dev: n_tri x 9 floats (device); trim_dev: height x width x 2 floats
+ * (device, overwritten).  The camera's row range is ignored.
+ * ------------------------------------------------------------------------- */
+int lrvol_trim(const lrvol_camera *cam, const float *tri_dev, int64_t n_tri, float *trim_dev, void *stream);
 
 /* ---------------------------------------------------------------------------
  * Streamlines of a 3-vector volume (Sec. 5): dx/dt = f(x) from each seed by

@@ -357,6 +357,7 @@ int prepare_render(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *tf
   prm->tf_scale = (float)(255.0 / (tf->vmax - tf->vmin));
   prm->tf_bias = (float)(-tf->vmin * 255.0 / (tf->vmax - tf->vmin));
   for (int q = 0; q < 256; ++q) prm->tf[q] = make_float4(tf->rgba[q][0], tf->rgba[q][1], tf->rgba[q][2], tf->rgba[q][3]);
+  prm->trim = reinterpret_cast<const float2 *>(step->trim);
   if (step->shading == LRVOL_SHADE_GRADIENT) {
     field = kFieldShaded;
     prm->light_set = ll > 0.0;
@@ -701,6 +702,17 @@ int lrvol_eval_grad(lrvol_t v, const float *pts, int64_t n, float *out, void *st
   if (v->nc != 1) return fail(LRVOL_ERR_UNSUPPORTED, "eval_grad needs a scalar volume");
   if (n == 0) return LRVOL_OK;
   CU(launch_eval_grad(v, pts, n, out, (cudaStream_t)stream), "eval_grad kernel");
+  return LRVOL_OK;
+}
+
+int lrvol_trim(const lrvol_camera *cam, const float *tri, int64_t n_tri, float *out, void *stream) {
+  if (!cam || !out || n_tri < 0 || (n_tri > 0 && !tri)) return fail(LRVOL_ERR_ARG, "bad arguments");
+  if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+    return fail(LRVOL_ERR_ARG, "bad image size");
+  if (cam->projection != LRVOL_ORTHO && cam->projection != LRVOL_PERSP) return fail(LRVOL_ERR_ARG, "bad projection");
+  RayConsts K;
+  camera_consts(cam, &K);
+  CU(launch_trim(K, cam->width, cam->height, tri, n_tri, out, (cudaStream_t)stream), "trim kernels");
   return LRVOL_OK;
 }
 

@@ -603,6 +603,17 @@ __device__ __forceinline__ f2 word_to_f2(unsigned w) {
   }
 }
 
+// A pixel's ray interval cut by its trimming interval (Sec. 4.1): no hit
+// hides the pixel; only back faces (the eye inside the mesh) keep
+// [t_in, t_back]; only front faces keep [t_front, t_out].
+__device__ __forceinline__ bool trim_cut(float2 tr, float &tin, float &tout) {
+  const float inf = __int_as_float(0x7f800000);
+  if (tr.x == inf && tr.y == 0.f) return false;
+  if (tr.x != inf && tr.x > tin) tin = tr.x;
+  if (tr.y != 0.f && tr.y < tout) tout = tr.y;
+  return tin < tout;
+}
+
 // One element's block in registers and its evaluation at monomials bx, by, bz.
 //   FIELD 0: scalar volume; 1: |v| of a 3-vector; 2: one component of a
 //   3-vector, read from the plain per-component copy.
@@ -929,7 +940,8 @@ __global__ void __launch_bounds__(128, (FIELD == 3 && P == 3) ? 3 : 4) k_render(
   Ray ray;
   if (i < prm.width && j < prm.row_end) {
     float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.f;
-    if (make_ray(prm.ray, i, j, ray)) {
+    if (make_ray(prm.ray, i, j, ray) &&
+        (prm.trim == nullptr || trim_cut(__ldg(prm.trim + (int64_t)j * prm.width + i), ray.tin, ray.tout))) {
       ++nhit;
       const float tr_stop = 1.f - prm.alpha_stop;
       float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
@@ -1568,6 +1580,146 @@ cudaError_t launch_labels(const RenderParams &prm, int degree, float h_fine, flo
     case 3: k_labels<3><<<grid, 128, 0, s>>>(prm, h_fine, tau, cand, n_cand, label); break;
     default: return cudaErrorInvalidValue;
   }
+  return cudaGetLastError();
+}
+
+// ----------------------------------------------------------------------------
+// Trimming (Sec. 4.1).  The paper's z-prepass rasterises the boundary mesh's
+// front and back faces into two depth buffers; here each triangle is one
+// warp that tests the rays of the pixels in its conservative screen box
+// (watertight test, FP32, in the oracle's order of operations) and keeps
+// the nearest front-face and farthest back-face distances with atomics on
+// the float bits (t > 0, so bit order is value order).
+// ----------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ float pick3(int k, float x, float y, float z) { return k == 0 ? x : (k == 1 ? y : z); }
+
+// Watertight ray/triangle test (Woop, Benthin and Wald, JCGT 2013), FP32,
+// with the oracle's order of operations; component selection by value so
+// that nothing goes to local memory.
+__device__ __forceinline__ bool tri_hit(const Ray &ray, const float *__restrict__ v, float &t, bool &front) {
+  const float d0 = ray.d[0], d1 = ray.d[1], d2 = ray.d[2];
+  int kz = 0;
+  if (fabsf(d1) > fabsf(pick3(kz, d0, d1, d2))) kz = 1;
+  if (fabsf(d2) > fabsf(pick3(kz, d0, d1, d2))) kz = 2;
+  int kx = kz == 2 ? 0 : kz + 1, ky = kx == 2 ? 0 : kx + 1;
+  const float dz = pick3(kz, d0, d1, d2);
+  if (dz < 0.f) {
+    const int w = kx;
+    kx = ky;
+    ky = w;
+  }
+  const float Sx = __fdiv_rn(pick3(kx, d0, d1, d2), dz), Sy = __fdiv_rn(pick3(ky, d0, d1, d2), dz);
+  const float Sz = __fdiv_rn(1.f, dz);
+  const float a0 = __fsub_rn(__ldg(v + 0), ray.o[0]), a1 = __fsub_rn(__ldg(v + 1), ray.o[1]);
+  const float a2 = __fsub_rn(__ldg(v + 2), ray.o[2]);
+  const float b0 = __fsub_rn(__ldg(v + 3), ray.o[0]), b1 = __fsub_rn(__ldg(v + 4), ray.o[1]);
+  const float b2 = __fsub_rn(__ldg(v + 5), ray.o[2]);
+  const float c0 = __fsub_rn(__ldg(v + 6), ray.o[0]), c1 = __fsub_rn(__ldg(v + 7), ray.o[1]);
+  const float c2 = __fsub_rn(__ldg(v + 8), ray.o[2]);
+  const float Akz = pick3(kz, a0, a1, a2), Bkz = pick3(kz, b0, b1, b2), Ckz = pick3(kz, c0, c1, c2);
+  const float Ax = __fsub_rn(pick3(kx, a0, a1, a2), __fmul_rn(Sx, Akz));
+  const float Ay = __fsub_rn(pick3(ky, a0, a1, a2), __fmul_rn(Sy, Akz));
+  const float Bx = __fsub_rn(pick3(kx, b0, b1, b2), __fmul_rn(Sx, Bkz));
+  const float By = __fsub_rn(pick3(ky, b0, b1, b2), __fmul_rn(Sy, Bkz));
+  const float Cx = __fsub_rn(pick3(kx, c0, c1, c2), __fmul_rn(Sx, Ckz));
+  const float Cy = __fsub_rn(pick3(ky, c0, c1, c2), __fmul_rn(Sy, Ckz));
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float V = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.f || V == 0.f || W == 0.f) {
+    U = __double2float_rn(__dsub_rn(__dmul_rn((double)Cx, (double)By), __dmul_rn((double)Cy, (double)Bx)));
+    V = __double2float_rn(__dsub_rn(__dmul_rn((double)Ax, (double)Cy), __dmul_rn((double)Ay, (double)Cx)));
+    W = __double2float_rn(__dsub_rn(__dmul_rn((double)Bx, (double)Ay), __dmul_rn((double)By, (double)Ax)));
+  }
+  if ((U < 0.f || V < 0.f || W < 0.f) && (U > 0.f || V > 0.f || W > 0.f)) return false;
+  const float det = __fadd_rn(__fadd_rn(U, V), W);
+  if (det == 0.f) return false;
+  const float Az = __fmul_rn(Sz, Akz), Bz = __fmul_rn(Sz, Bkz), Cz = __fmul_rn(Sz, Ckz);
+  const float T = __fadd_rn(__fadd_rn(__fmul_rn(U, Az), __fmul_rn(V, Bz)), __fmul_rn(W, Cz));
+  if (det > 0.f ? !(T > 0.f) : !(T < 0.f)) return false;
+  t = __fdiv_rn(T, det);
+  front = det > 0.f;
+  return true;
+}
+
+__global__ void k_trim_init(float2 *__restrict__ out, int64_t n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) out[q] = make_float2(__int_as_float(0x7f800000), 0.f);
+}
+
+__global__ void __launch_bounds__(128) k_trim_raster(const RayConsts K, int width, int height,
+                                                     const float *__restrict__ tri, int64_t n_tri,
+                                                     float2 *__restrict__ out) {
+  const int64_t tr = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (tr >= n_tri) return;
+  const float *v = tri + 9 * tr;
+  // conservative pixel box of the projected triangle (whole image when a
+  // vertex is at or behind the eye plane; nothing when all three are)
+  float amin = __int_as_float(0x7f800000), amax = -amin, bmin = amin, bmax = -amin;
+  bool full = false;
+  int behind = 0;
+#pragma unroll
+  for (int q = 0; q < 3; ++q) {
+    const float X = __ldg(v + 3 * q) - K.E[0], Y = __ldg(v + 3 * q + 1) - K.E[1], Z = __ldg(v + 3 * q + 2) - K.E[2];
+    const float r = X * K.R[0] + Y * K.R[1] + Z * K.R[2];
+    const float u = X * K.U[0] + Y * K.U[1] + Z * K.U[2];
+    float a = r, b = u;
+    if (K.persp) {
+      const float z = X * K.F[0] + Y * K.F[1] + Z * K.F[2];
+      if (!(z > 1e-6f)) {
+        full = true;
+        ++behind;
+        continue;
+      }
+      a = r / z;
+      b = u / z;
+    }
+    amin = fminf(amin, a);
+    amax = fmaxf(amax, a);
+    bmin = fminf(bmin, b);
+    bmax = fmaxf(bmax, b);
+  }
+  if (behind == 3) return;
+  int i0 = 0, i1 = width - 1, j0 = 0, j1 = height - 1;
+  if (!full) {
+    const float ia = (amin - K.sxo) / K.sxs - 0.5f, ib = (amax - K.sxo) / K.sxs - 0.5f;
+    const float ja = (bmin - K.syo) / K.sys - 0.5f, jb = (bmax - K.syo) / K.sys - 0.5f;
+    const float lo_i = fminf(ia, ib), hi_i = fmaxf(ia, ib), lo_j = fminf(ja, jb), hi_j = fmaxf(ja, jb);
+    if (!(hi_i >= -2.f && lo_i <= (float)width + 1.f && hi_j >= -2.f && lo_j <= (float)height + 1.f)) return;
+    i0 = max(0, (int)floorf(lo_i) - 2);
+    i1 = min(width - 1, (int)ceilf(hi_i) + 2);
+    j0 = max(0, (int)floorf(lo_j) - 2);
+    j1 = min(height - 1, (int)ceilf(hi_j) + 2);
+    if (i0 > i1 || j0 > j1) return;
+  }
+  const int bw = i1 - i0 + 1;
+  const int64_t cnt = (int64_t)bw * (j1 - j0 + 1);
+  for (int64_t p = lane; p < cnt; p += 32) {
+    const int i = i0 + (int)(p % bw), j = j0 + (int)(p / bw);
+    Ray ray;
+    make_ray(K, i, j, ray);   // origin and direction; the unit-cube interval is not needed here
+    float t;
+    bool front;
+    if (!tri_hit(ray, v, t, front)) continue;
+    unsigned *slot = reinterpret_cast<unsigned *>(out + (int64_t)j * width + i);
+    if (front)
+      atomicMin(slot, __float_as_uint(t));
+    else
+      atomicMax(slot + 1, __float_as_uint(t));
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_trim(const RayConsts &ray, int width, int height, const float *tri, int64_t n_tri, float *out,
+                        cudaStream_t s) {
+  const int64_t npix = (int64_t)width * height;
+  float2 *o = reinterpret_cast<float2 *>(out);
+  k_trim_init<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(o, npix);
+  if (n_tri > 0) k_trim_raster<<<(unsigned)((n_tri + 3) / 4), 128, 0, s>>>(ray, width, height, tri, n_tri, o);
   return cudaGetLastError();
 }
 

@@ -116,6 +116,7 @@ struct RenderParams {
   const float *mult;      // LEARNED: per-element step multipliers
   float h, inv_xi, alpha_stop;
   float tf_scale, tf_bias; // x = v * tf_scale + tf_bias, clamped to [0, 255]
+  const float2 *trim;     // NULL or per pixel (t_front, t_back), row major over the full image
   int light_set;          // shading: 1 = light[] (unit), 0 = towards the eye along the ray
   float light[3];
   float grad_eps;         // shading: gradients below this count as none (1e-3 (vmax - vmin))
@@ -208,6 +209,10 @@ struct FeatureParams {
 };
 
 cudaError_t launch_features(const FeatureParams &fp, float *out, cudaStream_t s);
+
+// Trimming (Sec. 4.1)
+cudaError_t launch_trim(const RayConsts &ray, int width, int height, const float *tri, int64_t n_tri, float *out,
+                        cudaStream_t s);
 
 // Streamlines (Sec. 5)
 struct SLParams {

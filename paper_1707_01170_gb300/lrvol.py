@@ -31,7 +31,7 @@ EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_rende
             "lrvol_server_set_priority_pixels", "lrvol_server_set_large_cap",
             "lrvol_server_submit", "lrvol_server_progress", "lrvol_server_drain", "lrvol_server_poll", "lrvol_server_info",
             "lrvol_server_release", "lrvol_server_get_stats", "lrvol_server_clock", "lrvol_server_destroy",
-            "lrvol_streamlines", "lrvol_streamline_error"]
+            "lrvol_streamlines", "lrvol_streamline_error", "lrvol_trim"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 SL_METHODS = ["RK1", "RK2", "RK3", "RK4", "RK38", "RKF5", "HE", "BS", "RKF45"]
 SL_RULES = ["fixed", "heuristic", "adaptive"]
@@ -58,7 +58,8 @@ class TF(ctypes.Structure):
 class Step(ctypes.Structure):
     _fields_ = [("mode", ctypes.c_int32), ("field", ctypes.c_int32), ("component", ctypes.c_int32),
                 ("h", ctypes.c_double), ("xi", ctypes.c_double), ("alpha_stop", ctypes.c_double),
-                ("mult", ctypes.c_void_p), ("shading", ctypes.c_int32), ("light", ctypes.c_double * 3)]
+                ("mult", ctypes.c_void_p), ("shading", ctypes.c_int32), ("light", ctypes.c_double * 3),
+                ("trim", ctypes.c_void_p)]
 
 
 class Stats(ctypes.Structure):
@@ -153,6 +154,8 @@ def load(path: str = LIB_PATH):
         L.lrvol_labels.restype = ctypes.c_int
         L.lrvol_labels.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
                                    ctypes.c_double, ctypes.c_double, vp, i32, vp, vp]
+        L.lrvol_trim.restype = ctypes.c_int
+        L.lrvol_trim.argtypes = [ctypes.POINTER(Camera), vp, i64, vp, vp]
         L.lrvol_streamlines.restype = ctypes.c_int
         L.lrvol_streamlines.argtypes = [vp, ctypes.POINTER(SLParams), vp, i64, vp, vp, vp, vp]
         L.lrvol_streamline_error.restype = ctypes.c_int
@@ -267,6 +270,11 @@ def make_step(step, allow_auto: bool = False) -> Step:
     s.shading = {"none": SHADE_NONE, "gradient": SHADE_GRADIENT}[getattr(step, "shading", "none")]
     for a, x in enumerate(getattr(step, "light", (0.0, 0.0, 0.0))):
         s.light[a] = float(x)
+    trim = getattr(step, "trim", None)
+    if trim is not None:
+        if not getattr(trim, "is_cuda", False) or not trim.is_contiguous():
+            raise ValueError("trim must be a contiguous CUDA tensor (height x width x 2 float32)")
+        s.trim = trim.data_ptr()
     return s
 
 
@@ -605,3 +613,19 @@ def streamline_error(ref, ref_count, app, app_count, stream=None):
                                          _dev(app, torch.float64), _dev(app_count), app.shape[1], n, _dev(sums),
                                          _stream_ptr(stream)), "lrvol_streamline_error")
     return sums
+
+
+# ---- trimming (Sec. 4.1) -----------------------------------------------------
+
+def trim(cam, tris, out=None, stream=None):
+    """Per-pixel (t_front, t_back) of a closed mesh (tris: CUDA float32 tensor
+    of n x 3 x 3 or n x 9 vertices, counter-clockwise seen from outside):
+    (H, W, 2) float32 CUDA tensor for lrvol_step.trim."""
+    import torch
+    c = cam if isinstance(cam, Camera) else make_camera(cam)
+    t = tris.reshape(-1, 9)
+    if out is None:
+        out = torch.empty((c.height, c.width, 2), dtype=torch.float32, device="cuda")
+    _check(load().lrvol_trim(ctypes.byref(c), _dev(t, torch.float32), t.shape[0], _dev(out, torch.float32),
+                             _stream_ptr(stream)), "lrvol_trim")
+    return out

@@ -441,6 +441,21 @@ def icosphere(centre=(0.5, 0.5, 0.5), radius: float = 0.3, subdiv: int = 3) -> n
     return V_[np.asarray(f)]
 
 
+def uv_sphere(centre=(0.5, 0.5, 0.5), radius: float = 0.3, n_lat: int = 64, n_lon: int = 128) -> np.ndarray:
+    """A latitude-longitude sphere, 2 * n_lat * n_lon triangles (those at the
+    poles degenerate), counter-clockwise seen from outside, (n, 3, 3)."""
+    th = np.linspace(0.0, np.pi, n_lat + 1)
+    ph = np.linspace(0.0, 2 * np.pi, n_lon + 1)
+    T, Ph = np.meshgrid(th, ph, indexing="ij")
+    P_ = np.stack([np.sin(T) * np.cos(Ph), np.sin(T) * np.sin(Ph), np.cos(T)], axis=-1) * radius
+    P_ = P_ + np.asarray(centre, dtype=np.float64)
+    a, b = P_[:-1, :-1], P_[1:, :-1]           # (lat k, lon l), (lat k+1, lon l)
+    c, d = P_[1:, 1:], P_[:-1, 1:]             # (lat k+1, lon l+1), (lat k, lon l+1)
+    t1 = np.stack([a, b, c], axis=2).reshape(-1, 3, 3)
+    t2 = np.stack([a, c, d], axis=2).reshape(-1, 3, 3)
+    return np.concatenate([t1, t2])
+
+
 # ----------------------------------------------------------------------------
 
 _BUILDERS = {1: config1, 2: config2, 3: config3}
