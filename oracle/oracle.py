@@ -122,6 +122,7 @@ def _load():
                                  ctypes.c_double, ctypes.c_double, vp, i32, vp, i32]
         L.orc_streamlines.argtypes = [vp, ctypes.POINTER(_SLParams), vp, i64, vp, vp, vp, i32]
         L.orc_trim.argtypes = [ctypes.POINTER(_Cam), vp, i64, vp, i32]
+        L.orc_tubes.argtypes = [vp, ctypes.POINTER(_Cam), vp, i64, ctypes.c_float, ctypes.POINTER(_TF), vp, i32]
         L.orc_ray.restype = i32
         L.orc_ray.argtypes = [ctypes.POINTER(_Cam), i32, i32, vp, vp, vp, vp]
         _lib = L
@@ -265,6 +266,21 @@ class Oracle:
                                 status.ctypes.data, _threads(threads or self.threads))
         return out, count, status
 
+    def tubes(self, cam, samples, count, radius: float, cmap, threads: int | None = None):
+        """Streamline tubes (Sec. 5.3): RGBA (H, W, 4) FP64 of the capsules of
+        radius r around every segment of the polylines (samples (n, max, 4),
+        count (n,)), coloured by the colour map at the field's speed on the
+        segment axis and shaded by max(0.4, |n . d|)."""
+        seg = tube_segments(samples, count)
+        table = np.ascontiguousarray(cmap.table, dtype=np.float64).reshape(256, 4)
+        t = _TF()
+        t.table = table.ctypes.data
+        t.vmin, t.vmax = float(cmap.vmin), float(cmap.vmax)
+        out = np.zeros((cam.height, cam.width, 4), dtype=np.float64)
+        _load().orc_tubes(self._h, ctypes.byref(_cam(cam)), seg.ctypes.data, len(seg), float(radius), ctypes.byref(t),
+                          out.ctypes.data, _threads(threads or self.threads))
+        return out
+
     def heuristic_step(self, e: int) -> float:
         return float(_load().orc_heuristic_step(self._h, int(e)))
 
@@ -387,3 +403,15 @@ def trim(cam, tris, threads: int | None = None):
     _load().orc_trim(ctypes.byref(_cam(cam)), tri.ctypes.data, len(tri), out.ctypes.data,
                      _threads(threads or 0))
     return out
+
+
+def tube_segments(samples, count):
+    """FP32 segments (n_seg x 6: a, b) of polylines, line by line in order."""
+    samples = np.asarray(samples)
+    segs = []
+    for j in range(len(samples)):
+        c = int(count[j])
+        if c >= 2:
+            pts = samples[j, :c, :3].astype(np.float32)
+            segs.append(np.concatenate([pts[:-1], pts[1:]], axis=1))
+    return np.ascontiguousarray(np.concatenate(segs) if segs else np.zeros((0, 6), np.float32), dtype=np.float32)

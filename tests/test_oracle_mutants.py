@@ -18,6 +18,7 @@ import test_oracle_learned as L
 import test_oracle_shading as S
 import test_oracle_streamlines as SL
 import test_oracle_trim as T
+import test_oracle_tubes as TU
 import test_oracle_pins as P
 
 SRC = os.path.join(os.path.dirname(orc.__file__), "oracle.c")
@@ -87,6 +88,9 @@ MUTANTS = [
     ("stages evaluated at x_n", "y[a] = x[a] + hs * acc;", "y[a] = x[a];"),
     ("trimming takes back faces for front faces", "*front = det > 0.0f;", "*front = det < 0.0f;"),
     ("trimming ignores the back faces", "if (tb != 0.0f && tb < *tout) *tout = tb;", ""),
+    ("tubes keep the farthest hit", "if (t < tbest) { /* strictly smaller", "if (tbest == INFINITY || t > tbest) { /* strictly smaller"),
+    ("tubes without caps", "const float h = bb * bb - cc;", "const float h = -1.0f;"),
+    ("tube shading without the 0.4 floor", "if (I < 0.4) I = 0.4;", ""),
     ("streamline Eq. 4 step without the element", "if (P->step_rule == 1) h = P->h * (double)orc_heuristic_step(v, e);",
      "if (P->step_rule == 1) h = P->h;"),
 ]
@@ -127,6 +131,8 @@ def _pins(cfg1):
     yield lambda: T.test_sphere_is_watertight()
     yield lambda: T.test_trimmed_constant_field_closed_form(cfg1, "outside")
     yield lambda: T.test_trimmed_constant_field_closed_form(cfg1, "inside")
+    yield lambda: TU.test_straight_segment_closed_form()
+    yield lambda: TU.test_caps_and_occlusion()
     H = orc.Oracle(SL.helix_volume())
     for m in sorted(SL.ORDERS):
         yield lambda m=m: SL.test_fixed_step_order(H, m)
