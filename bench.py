@@ -395,6 +395,27 @@ def streamline_leg(stream, n_seeds: int = 65536, n_err: int = 4096, t_end: float
                             "steps_per_s": steps / (ms / 1e3), "evals_per_s_accepted": evals / (ms / 1e3),
                             "eq7_max": float(sums.max()), "eq7_mean": float(sums.mean()),
                             "status_counts": {"t_end": st[0], "left": st[1], "cap": st[2], "control": st[3]}})
+    # tubes (Sec. 5.3) of the first 4,096 lines of the last run, 1920x1080
+    n_t, radius = 4096, 0.002
+    tf3, cam3 = V.config3_render(WIDTH, HEIGHT)
+    tf3.vmin, tf3.vmax = 0.0, 1.5
+    ccam, ctf = lv.make_camera(cam3), lv.make_tf(tf3)
+    vis = torch.empty((HEIGHT, WIDTH), dtype=torch.int64, device="cuda")
+    img = torch.empty((HEIGHT, WIDTH, 4), dtype=torch.float32, device="cuda")
+    samples, count, _ = buf
+    tub = lambda: lv.tubes(g, ccam, samples[:n_t], count[:n_t], radius, ctf, vis=vis, out=img, stream=stream)
+    tub()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        tub()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    segs = int((count[:n_t].to(torch.int64) - 1).clamp(min=0).sum())
+    out["tubes"] = {"lines": n_t, "segments": segs, "radius": radius, "image": f"{WIDTH}x{HEIGHT}",
+                    "ms": e0.elapsed_time(e1) / reps, "covered_pixels": int((img[..., 3] > 0).sum()),
+                    "from": "the last run's first lines"}
     g.close()
     return out
 

@@ -358,6 +358,24 @@ typedef struct {
 int lrvol_streamlines(lrvol_t vol, const lrvol_streamline_params *params, const double *seeds_dev, int64_t n,
                       double *samples_dev, int32_t *count_dev, int32_t *status_dev, void *stream);
 
+/* Streamline tubes (Sec. 5.3): every segment of the polylines that
+ * lrvol_streamlines wrote (samples_dev, count_dev; max_samples per line) is
+ * drawn as a capsule of the given radius around the segment (endpoints
+ * rounded to FP32).  Visibility is decided in FP32: per pixel the hit with
+ * the smallest t wins, ties going to the earlier segment (line by line, in
+ * order).  The pixel then takes the colour map's RGB at the speed |f| of the
+ * volume at the closest point on the winning segment's axis, times
+ * I = max(0.4, |n . d|), n the capsule normal at the hit; alpha 1; pixels
+ * without a hit are (0, 0, 0, 0).  Each segment is one warp over the pixels
+ * of its conservative screen box; hits merge by a 64-bit atomic minimum of
+ * (t bits, segment index) in vis_dev (height x width uint64 scratch,
+ * caller-owned), then one thread per pixel shades the winner into rgba_dev
+ * (height x width x 4 floats).  Needs a 3-vector volume (build_accel,
+ * to_bezier); n_lines * (max_samples - 1) < 2^32. */
+int lrvol_tubes(lrvol_t vol, const lrvol_camera *cam, const double *samples_dev, const int32_t *count_dev,
+                int64_t n_lines, int32_t max_samples, float radius, const lrvol_tf *cmap, uint64_t *vis_dev,
+                float *rgba_dev, void *stream);
+
 /* Eq. 7 per streamline (device): sums_dev[j] = sum over the approximation's
  * samples i >= 1 of (t_i - t_{i-1}) |x_j(t_i) - y_j(t_i)|_2, the reference
  * x_j linear between its samples; samples past the reference's last time

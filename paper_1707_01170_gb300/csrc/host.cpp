@@ -751,6 +751,46 @@ int lrvol_streamlines(lrvol_t v, const lrvol_streamline_params *P, const double 
   return LRVOL_OK;
 }
 
+int lrvol_tubes(lrvol_t v, const lrvol_camera *cam, const double *samples, const int32_t *count, int64_t n_lines,
+                int32_t max_samples, float radius, const lrvol_tf *cmap, uint64_t *vis, float *rgba, void *stream) {
+  if (!v || !cam || !cmap || !vis || !rgba || n_lines < 0 || (n_lines > 0 && (!samples || !count)))
+    return fail(LRVOL_ERR_ARG, "bad arguments");
+  if (!v->have_bezier || !v->have_accel) return fail(LRVOL_ERR_STATE, "tubes need to_bezier and build_accel");
+  if (v->nc != 3) return fail(LRVOL_ERR_UNSUPPORTED, "tubes need a 3-vector volume (speed colouring)");
+  if (v->p[0] != v->p[1] || v->p[0] != v->p[2] || v->p[0] > 3)
+    return fail(LRVOL_ERR_UNSUPPORTED, "tubes need equal degrees 1..3");
+  if (max_samples < 2 || !(radius > 0.f && radius < INFINITY)) return fail(LRVOL_ERR_ARG, "bad max_samples or radius");
+  if (n_lines * (int64_t)(max_samples - 1) >= ((int64_t)1 << 32)) return fail(LRVOL_ERR_ARG, "too many segments");
+  if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
+    return fail(LRVOL_ERR_ARG, "bad image size");
+  if (cam->projection != LRVOL_ORTHO && cam->projection != LRVOL_PERSP) return fail(LRVOL_ERR_ARG, "bad projection");
+  if (!(cmap->vmax > cmap->vmin)) return fail(LRVOL_ERR_ARG, "colour map needs vmax > vmin");
+  TubeParams tp;
+  std::memset(&tp, 0, sizeof(tp));
+  tp.field.elem = v->d_elem;
+  tp.field.n_elem = v->n_elem;
+  tp.field.bez = v->d_bez;
+  tp.field.elem_bytes = v->elem_bytes;
+  tp.field.forest = forest_view(v);
+  tp.field.status = v->d_status;
+  camera_consts(cam, &tp.ray);
+  tp.width = cam->width;
+  tp.height = cam->height;
+  tp.radius = radius;
+  tp.samples = samples;
+  tp.count = count;
+  tp.n_lines = n_lines;
+  tp.max_samples = max_samples;
+  tp.vis = reinterpret_cast<unsigned long long *>(vis);
+  tp.out = rgba;
+  tp.tf_scale = (float)(255.0 / (cmap->vmax - cmap->vmin));
+  tp.tf_bias = (float)(-cmap->vmin * 255.0 / (cmap->vmax - cmap->vmin));
+  for (int q = 0; q < 256; ++q)
+    tp.cmap[q] = make_float4(cmap->rgba[q][0], cmap->rgba[q][1], cmap->rgba[q][2], cmap->rgba[q][3]);
+  CU(launch_tubes(tp, v->p[0], v->storage, (cudaStream_t)stream), "tube kernels");
+  return LRVOL_OK;
+}
+
 int lrvol_streamline_error(const double *ref, const int32_t *rc, int32_t rmax, const double *app, const int32_t *ac,
                            int32_t amax, int64_t n, double *sums, void *stream) {
   if (n < 0 || rmax < 1 || amax < 1 || (n > 0 && (!ref || !rc || !app || !ac || !sums)))

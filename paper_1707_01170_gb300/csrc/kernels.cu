@@ -2007,6 +2007,210 @@ cudaError_t launch_streamlines(const SLParams &sp, int degree, int storage, cons
   return cudaGetLastError();
 }
 
+// ----------------------------------------------------------------------------
+// Streamline tubes (Sec. 5.3): capsules around the polyline segments,
+// visibility by a 64-bit atomic minimum of (t bits, segment index) per pixel,
+// then one thread per pixel shades the winner.
+// ----------------------------------------------------------------------------
+namespace {
+
+__device__ __forceinline__ float dot3r(float x0, float x1, float x2, float y0, float y1, float y2) {
+  return __fadd_rn(__fadd_rn(__fmul_rn(x0, y0), __fmul_rn(x1, y1)), __fmul_rn(x2, y2));
+}
+
+// Ray/capsule hit in FP32 with the oracle's order of operations; t > 0 only.
+__device__ __forceinline__ bool capsule_hit(const Ray &ray, const float *a, const float *b, float r, float &t) {
+  const float ba0 = __fsub_rn(b[0], a[0]), ba1 = __fsub_rn(b[1], a[1]), ba2 = __fsub_rn(b[2], a[2]);
+  const float oa0 = __fsub_rn(ray.o[0], a[0]), oa1 = __fsub_rn(ray.o[1], a[1]), oa2 = __fsub_rn(ray.o[2], a[2]);
+  const float ob0 = __fsub_rn(ray.o[0], b[0]), ob1 = __fsub_rn(ray.o[1], b[1]), ob2 = __fsub_rn(ray.o[2], b[2]);
+  const float d0 = ray.d[0], d1 = ray.d[1], d2 = ray.d[2];
+  const float baba = dot3r(ba0, ba1, ba2, ba0, ba1, ba2), bard = dot3r(ba0, ba1, ba2, d0, d1, d2);
+  const float baoa = dot3r(ba0, ba1, ba2, oa0, oa1, oa2), rdoa = dot3r(d0, d1, d2, oa0, oa1, oa2);
+  const float oaoa = dot3r(oa0, oa1, oa2, oa0, oa1, oa2), rr = __fmul_rn(r, r);
+  const float A = __fsub_rn(baba, __fmul_rn(bard, bard));
+  if (A > 0.f) {
+    const float B = __fsub_rn(__fmul_rn(baba, rdoa), __fmul_rn(baoa, bard));
+    const float C = __fsub_rn(__fsub_rn(__fmul_rn(baba, oaoa), __fmul_rn(baoa, baoa)), __fmul_rn(rr, baba));
+    const float H = __fsub_rn(__fmul_rn(B, B), __fmul_rn(A, C));
+    if (H >= 0.f) {
+      const float tb = __fdiv_rn(__fsub_rn(-B, __fsqrt_rn(H)), A);
+      const float y = __fadd_rn(baoa, __fmul_rn(tb, bard));
+      if (y > 0.f && y < baba) {
+        if (tb > 0.f) {
+          t = tb;
+          return true;
+        }
+        return false;
+      }
+    }
+  }
+  float best = __int_as_float(0x7f800000);
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const float c0 = k == 0 ? oa0 : ob0, c1 = k == 0 ? oa1 : ob1, c2 = k == 0 ? oa2 : ob2;
+    const float bb = dot3r(d0, d1, d2, c0, c1, c2), cc = __fsub_rn(dot3r(c0, c1, c2, c0, c1, c2), rr);
+    const float h = __fsub_rn(__fmul_rn(bb, bb), cc);
+    if (h > 0.f) {
+      const float tc = __fsub_rn(-bb, __fsqrt_rn(h));
+      if (tc > 0.f && tc < best) best = tc;
+    }
+  }
+  if (best < __int_as_float(0x7f800000)) {
+    t = best;
+    return true;
+  }
+  return false;
+}
+
+__device__ __forceinline__ bool tube_segment(const TubeParams &tp, int64_t s, float *a, float *b) {
+  const int per = tp.max_samples - 1;
+  const int64_t j = s / per;
+  const int k = (int)(s % per);
+  if (k >= tp.count[j] - 1) return false;
+  const double *p = tp.samples + (j * tp.max_samples + k) * 4;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    a[c] = __double2float_rn(p[c]);
+    b[c] = __double2float_rn(p[4 + c]);
+  }
+  return true;
+}
+
+__global__ void k_vis_init(unsigned long long *__restrict__ vis, int64_t n) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q < n) vis[q] = ~0ull;
+}
+
+__global__ void __launch_bounds__(128) k_tube_raster(const __grid_constant__ TubeParams tp) {
+  const int64_t s = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  if (s >= tp.n_lines * (int64_t)(tp.max_samples - 1)) return;
+  float a[3], b[3];
+  if (!tube_segment(tp, s, a, b)) return;
+  const RayConsts &K = tp.ray;
+  // conservative pixel box of the capsule's bounding box
+  float amin = __int_as_float(0x7f800000), amax = -amin, bmin = amin, bmax = -amin;
+  bool full = false;
+  int behind = 0;
+#pragma unroll
+  for (int q = 0; q < 8; ++q) {
+    const float cx = ((q & 1) ? fmaxf(a[0], b[0]) + tp.radius : fminf(a[0], b[0]) - tp.radius) - K.E[0];
+    const float cy = ((q & 2) ? fmaxf(a[1], b[1]) + tp.radius : fminf(a[1], b[1]) - tp.radius) - K.E[1];
+    const float cz = ((q & 4) ? fmaxf(a[2], b[2]) + tp.radius : fminf(a[2], b[2]) - tp.radius) - K.E[2];
+    const float r = cx * K.R[0] + cy * K.R[1] + cz * K.R[2];
+    const float u = cx * K.U[0] + cy * K.U[1] + cz * K.U[2];
+    float x = r, y = u;
+    if (K.persp) {
+      const float z = cx * K.F[0] + cy * K.F[1] + cz * K.F[2];
+      if (!(z > 1e-6f)) {
+        full = true;
+        ++behind;
+        continue;
+      }
+      x = r / z;
+      y = u / z;
+    }
+    amin = fminf(amin, x);
+    amax = fmaxf(amax, x);
+    bmin = fminf(bmin, y);
+    bmax = fmaxf(bmax, y);
+  }
+  if (behind == 8) return;
+  int i0 = 0, i1 = tp.width - 1, j0 = 0, j1 = tp.height - 1;
+  if (!full) {
+    const float ia = (amin - K.sxo) / K.sxs - 0.5f, ib = (amax - K.sxo) / K.sxs - 0.5f;
+    const float ja = (bmin - K.syo) / K.sys - 0.5f, jb = (bmax - K.syo) / K.sys - 0.5f;
+    const float lo_i = fminf(ia, ib), hi_i = fmaxf(ia, ib), lo_j = fminf(ja, jb), hi_j = fmaxf(ja, jb);
+    if (!(hi_i >= -2.f && lo_i <= (float)tp.width + 1.f && hi_j >= -2.f && lo_j <= (float)tp.height + 1.f)) return;
+    i0 = max(0, (int)floorf(lo_i) - 2);
+    i1 = min(tp.width - 1, (int)ceilf(hi_i) + 2);
+    j0 = max(0, (int)floorf(lo_j) - 2);
+    j1 = min(tp.height - 1, (int)ceilf(hi_j) + 2);
+    if (i0 > i1 || j0 > j1) return;
+  }
+  const int bw = i1 - i0 + 1;
+  const int64_t cnt = (int64_t)bw * (j1 - j0 + 1);
+  for (int64_t p = lane; p < cnt; p += 32) {
+    const int i = i0 + (int)(p % bw), j = j0 + (int)(p / bw);
+    Ray ray;
+    make_ray(K, i, j, ray);
+    float t;
+    if (!capsule_hit(ray, a, b, tp.radius, t)) continue;
+    const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)(uint32_t)s;
+    atomicMin(tp.vis + (int64_t)j * tp.width + i, key);
+  }
+}
+
+template <int P, int STORE>
+__global__ void __launch_bounds__(128) k_tube_resolve(const __grid_constant__ TubeParams tp) {
+  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= (int64_t)tp.width * tp.height) return;
+  float4 *o = reinterpret_cast<float4 *>(tp.out) + q;
+  const unsigned long long key = tp.vis[q];
+  if (key == ~0ull) {
+    *o = make_float4(0.f, 0.f, 0.f, 0.f);
+    return;
+  }
+  const int64_t s = (int64_t)(key & 0xffffffffull);
+  const float t = __uint_as_float((unsigned)(key >> 32));
+  float a[3], b[3];
+  tube_segment(tp, s, a, b);
+  Ray ray;
+  make_ray(tp.ray, (int)(q % tp.width), (int)(q / tp.width), ray);
+  float p[3], ba[3], pa[3], qa[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    p[c] = __fadd_rn(ray.o[c], __fmul_rn(t, ray.d[c]));
+    ba[c] = __fsub_rn(b[c], a[c]);
+    pa[c] = __fsub_rn(p[c], a[c]);
+  }
+  const float baba = dot3r(ba[0], ba[1], ba[2], ba[0], ba[1], ba[2]);
+  float hcl = baba > 0.f ? __fdiv_rn(dot3r(pa[0], pa[1], pa[2], ba[0], ba[1], ba[2]), baba) : 0.f;
+  hcl = fminf(fmaxf(hcl, 0.f), 1.f);
+#pragma unroll
+  for (int c = 0; c < 3; ++c) qa[c] = __fadd_rn(a[c], __fmul_rn(hcl, ba[c]));
+  SLField<P, STORE> F;
+  F.cur = kNone;
+  float v0 = 0.f, v1 = 0.f, v2 = 0.f;
+  F.eval(tp.field, qa[0], qa[1], qa[2], v0, v1, v2);
+  const float speed = sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
+  const float x = fminf(fmaxf(fmaf(speed, tp.tf_scale, tp.tf_bias), 0.f), 255.f);
+  const int k = min((int)x, 254);
+  const float fr = x - (float)k;
+  const float4 e0 = tp.cmap[k], e1 = tp.cmap[k + 1];
+  const float n0 = p[0] - qa[0], n1 = p[1] - qa[1], n2 = p[2] - qa[2];
+  const float nn = fmaf(n0, n0, fmaf(n1, n1, n2 * n2));
+  float I = nn > 0.f ? fabsf(fmaf(n0, ray.d[0], fmaf(n1, ray.d[1], n2 * ray.d[2]))) * rsqrtf(nn) : 1.f;
+  I = fmaxf(I, 0.4f);
+  *o = make_float4(I * fmaf(fr, e1.x - e0.x, e0.x), I * fmaf(fr, e1.y - e0.y, e0.y), I * fmaf(fr, e1.z - e0.z, e0.z),
+                   1.f);
+}
+
+}  // namespace
+
+cudaError_t launch_tubes(const TubeParams &tp, int degree, int storage, cudaStream_t s) {
+  const int64_t npix = (int64_t)tp.width * tp.height;
+  const int64_t nseg = tp.n_lines * (int64_t)(tp.max_samples - 1);
+  k_vis_init<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(tp.vis, npix);
+  if (nseg > 0) k_tube_raster<<<(unsigned)((nseg + 3) / 4), 128, 0, s>>>(tp);
+  const unsigned blocks = (unsigned)((npix + 127) / 128);
+#define LRVOL_TUBE_CASE(P_, S_) k_tube_resolve<P_, S_><<<blocks, 128, 0, s>>>(tp)
+  switch (degree * 3 + storage) {
+    case 3: LRVOL_TUBE_CASE(1, LRVOL_STORE_F32); break;
+    case 4: LRVOL_TUBE_CASE(1, LRVOL_STORE_F16); break;
+    case 5: LRVOL_TUBE_CASE(1, LRVOL_STORE_BF16); break;
+    case 6: LRVOL_TUBE_CASE(2, LRVOL_STORE_F32); break;
+    case 7: LRVOL_TUBE_CASE(2, LRVOL_STORE_F16); break;
+    case 8: LRVOL_TUBE_CASE(2, LRVOL_STORE_BF16); break;
+    case 9: LRVOL_TUBE_CASE(3, LRVOL_STORE_F32); break;
+    case 10: LRVOL_TUBE_CASE(3, LRVOL_STORE_F16); break;
+    case 11: LRVOL_TUBE_CASE(3, LRVOL_STORE_BF16); break;
+    default: return cudaErrorInvalidValue;
+  }
+#undef LRVOL_TUBE_CASE
+  return cudaGetLastError();
+}
+
 cudaError_t launch_streamline_error(const double *ref, const int32_t *rc, int rmax, const double *app,
                                     const int32_t *ac, int amax, int64_t n, double *sums, cudaStream_t s) {
   k_streamline_error<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(reinterpret_cast<const SLSample *>(ref), rc, rmax,

@@ -228,6 +228,21 @@ struct SLParams {
 };
 cudaError_t launch_streamlines(const SLParams &sp, int degree, int storage, const double *seeds, int64_t n,
                                double *out, int32_t *count, int32_t *status, cudaStream_t s);
+struct TubeParams {
+  SLParams field;          // volume access for the speed at the axis point
+  RayConsts ray;
+  int width, height;
+  float radius;
+  const double *samples;   // n_lines x max_samples x 4
+  const int32_t *count;
+  int64_t n_lines;
+  int max_samples;
+  unsigned long long *vis; // height x width
+  float *out;              // height x width x 4
+  float tf_scale, tf_bias;
+  float4 cmap[256];
+};
+cudaError_t launch_tubes(const TubeParams &tp, int degree, int storage, cudaStream_t s);
 cudaError_t launch_streamline_error(const double *ref, const int32_t *rc, int rmax, const double *app,
                                     const int32_t *ac, int amax, int64_t n, double *sums, cudaStream_t s);
 

@@ -31,7 +31,7 @@ EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_rende
             "lrvol_server_set_priority_pixels", "lrvol_server_set_large_cap",
             "lrvol_server_submit", "lrvol_server_progress", "lrvol_server_drain", "lrvol_server_poll", "lrvol_server_info",
             "lrvol_server_release", "lrvol_server_get_stats", "lrvol_server_clock", "lrvol_server_destroy",
-            "lrvol_streamlines", "lrvol_streamline_error", "lrvol_trim"]
+            "lrvol_streamlines", "lrvol_streamline_error", "lrvol_trim", "lrvol_tubes"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 SL_METHODS = ["RK1", "RK2", "RK3", "RK4", "RK38", "RKF5", "HE", "BS", "RKF45"]
 SL_RULES = ["fixed", "heuristic", "adaptive"]
@@ -154,6 +154,9 @@ def load(path: str = LIB_PATH):
         L.lrvol_labels.restype = ctypes.c_int
         L.lrvol_labels.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
                                    ctypes.c_double, ctypes.c_double, vp, i32, vp, vp]
+        L.lrvol_tubes.restype = ctypes.c_int
+        L.lrvol_tubes.argtypes = [vp, ctypes.POINTER(Camera), vp, vp, i64, i32, ctypes.c_float, ctypes.POINTER(TF),
+                                  vp, vp, vp]
         L.lrvol_trim.restype = ctypes.c_int
         L.lrvol_trim.argtypes = [ctypes.POINTER(Camera), vp, i64, vp, vp]
         L.lrvol_streamlines.restype = ctypes.c_int
@@ -628,4 +631,21 @@ def trim(cam, tris, out=None, stream=None):
         out = torch.empty((c.height, c.width, 2), dtype=torch.float32, device="cuda")
     _check(load().lrvol_trim(ctypes.byref(c), _dev(t, torch.float32), t.shape[0], _dev(out, torch.float32),
                              _stream_ptr(stream)), "lrvol_trim")
+    return out
+
+
+def tubes(vol: "Volume", cam, samples, count, radius: float, cmap, vis=None, out=None, stream=None):
+    """Streamline tubes (Sec. 5.3): (H, W, 4) float32 CUDA tensor of the
+    capsules around the polylines (samples n x max x 4 float64, count n int32,
+    CUDA tensors), coloured by cmap at the field's speed."""
+    import torch
+    c = cam if isinstance(cam, Camera) else make_camera(cam)
+    t = cmap if isinstance(cmap, TF) else make_tf(cmap)
+    if vis is None:
+        vis = torch.empty((c.height, c.width), dtype=torch.int64, device="cuda")
+    if out is None:
+        out = torch.empty((c.height, c.width, 4), dtype=torch.float32, device="cuda")
+    _check(load().lrvol_tubes(vol.handle, ctypes.byref(c), _dev(samples, torch.float64), _dev(count), samples.shape[0],
+                              samples.shape[1], float(radius), ctypes.byref(t), _dev(vis), _dev(out, torch.float32),
+                              _stream_ptr(stream)), "lrvol_tubes")
     return out
