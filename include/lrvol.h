@@ -327,6 +327,9 @@ int lrvol_trim(const lrvol_camera *cam, const float *tri_dev, int64_t n_tri, flo
  * A streamline stops at t_end (status 0), when a stage point or the next
  * point leaves [0,1]^3 (status 1; the point before is the last sample),
  * after max_samples samples (2), or when the step control gives up (3).
+ * One thread traces one line at a time; a grid that fits on the GPU at once
+ * takes the seeds from a counter in the handle, so concurrent streamline
+ * calls on one handle are not allowed (as for every call on a handle).
  * ------------------------------------------------------------------------- */
 enum {
   LRVOL_RK1 = 0,   /* explicit Euler */

@@ -740,6 +740,7 @@ int lrvol_streamlines(lrvol_t v, const lrvol_streamline_params *P, const double 
   sp.elem_bytes = v->elem_bytes;
   sp.forest = forest_view(v);
   sp.status = v->d_status;
+  sp.queue = v->d_counters + kCntQueue;
   sp.method = P->method;
   sp.rule = P->step_rule;
   sp.max_samples = P->max_samples;

@@ -1820,13 +1820,11 @@ struct SLField {
   }
 };
 
+// One streamline, seed q.
 template <int P, int STORE>
-__global__ void __launch_bounds__(128) k_streamlines(const __grid_constant__ SLParams sp,
-                                                     const double *__restrict__ seeds, int64_t n,
-                                                     SLSample *__restrict__ out, int32_t *__restrict__ count,
-                                                     int32_t *__restrict__ status) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n) return;
+__device__ __forceinline__ void trace_line(const SLParams &sp, const double *__restrict__ seeds, int64_t q,
+                                           SLSample *__restrict__ out, int32_t *__restrict__ count,
+                                           int32_t *__restrict__ status) {
   const SLTab &T = c_sl_tab[sp.method];
   SLField<P, STORE> F;
   F.cur = kNone;
@@ -1955,6 +1953,21 @@ __global__ void __launch_bounds__(128) k_streamlines(const __grid_constant__ SLP
   status[q] = st;
 }
 
+// Persistent threads: a grid that fits on the GPU at once takes lines from
+// a counter until none is left, so lines of very different lengths do not
+// leave a partial last wave idle behind the longest one.
+template <int P, int STORE>
+__global__ void __launch_bounds__(128) k_streamlines(const __grid_constant__ SLParams sp,
+                                                     const double *__restrict__ seeds, int64_t n,
+                                                     SLSample *__restrict__ out, int32_t *__restrict__ count,
+                                                     int32_t *__restrict__ status) {
+  for (;;) {
+    const int64_t q = (int64_t)atomicAdd(sp.queue, 1ull);
+    if (q >= n) return;
+    trace_line<P, STORE>(sp, seeds, q, out, count, status);
+  }
+}
+
 // Eq. 7 per streamline: sum over the approximation's samples i >= 1 of
 // (t_i - t_{i-1}) * |x_ref(t_i) - y_i|, x_ref linear between its samples.
 __global__ void k_streamline_error(const SLSample *__restrict__ ref, const int32_t *__restrict__ rc, int rmax,
@@ -1986,11 +1999,25 @@ __global__ void k_streamline_error(const SLSample *__restrict__ ref, const int32
 
 }  // namespace
 
+template <int P, int STORE>
+cudaError_t launch_sl(const SLParams &sp, const double *seeds, int64_t n, SLSample *o, int32_t *count,
+                      int32_t *status, cudaStream_t s) {
+  int dev = 0, sms = 0, per_sm = 0;
+  cudaError_t e;
+  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_streamlines<P, STORE>, 128, 0)) != cudaSuccess)
+    return e;
+  const int64_t need = (n + 127) / 128, fit = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  if ((e = cudaMemsetAsync(sp.queue, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
+  k_streamlines<P, STORE><<<(unsigned)(need < fit ? need : fit), 128, 0, s>>>(sp, seeds, n, o, count, status);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_streamlines(const SLParams &sp, int degree, int storage, const double *seeds, int64_t n,
                                double *out, int32_t *count, int32_t *status, cudaStream_t s) {
-  const unsigned blocks = (unsigned)((n + 127) / 128);
   SLSample *o = reinterpret_cast<SLSample *>(out);
-#define LRVOL_SL_CASE(P_, S_) k_streamlines<P_, S_><<<blocks, 128, 0, s>>>(sp, seeds, n, o, count, status)
+#define LRVOL_SL_CASE(P_, S_) return launch_sl<P_, S_>(sp, seeds, n, o, count, status, s)
   switch (degree * 3 + storage) {
     case 3: LRVOL_SL_CASE(1, LRVOL_STORE_F32); break;
     case 4: LRVOL_SL_CASE(1, LRVOL_STORE_F16); break;

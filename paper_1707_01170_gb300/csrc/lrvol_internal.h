@@ -21,7 +21,7 @@ constexpr int kMaxSamplesPerRay = 1 << 24;  // a longer ray stops with LRVOL_ERR
 enum : uint32_t { kStatusOk = 0, kStatusBounds = 1, kStatusTimeout = 2 };
 
 // Counters written by render (one slot each).
-enum { kCntSamples = 0, kCntLookups = 1, kCntRays = 2, kCntTiles = 3, kNumCounters = 8 };
+enum { kCntSamples = 0, kCntLookups = 1, kCntRays = 2, kCntQueue = 3, kNumCounters = 8 };
 
 // Static scratch of lrvol_render_noalloc: kNumCounters counters, then the
 // status word (in a 64-bit slot); 32 words = 256 bytes per device.  One call
@@ -222,6 +222,7 @@ struct SLParams {
   int elem_bytes;
   ForestView forest;
   uint32_t *status;   // device status word (bounds)
+  unsigned long long *queue;  // streamlines: next seed to trace (zeroed per call)
   int method, rule, max_samples;
   double h, t_end;
   float tol_f;
