@@ -159,3 +159,30 @@ def test_size_tiers_let_small_frames_overtake(resident):
     for t in large + small:
         srv.release(t)
     srv.close()
+
+
+@pytest.mark.slow
+def test_full_size_mix_identical_to_alone():
+    """The benchmark's serving mix at full size (configs 1-3 resident; 256x256,
+    1920x1080 and 3840x2160 frames, size tiers on): every frame equals the same
+    request rendered alone, bit for bit."""
+    vols = [V.load_config(1), V.load_config(2), V.load_config(3)]
+    gvs = [lv.Volume(v).build_accel((64, 64, 64)).to_bezier() for v in vols]
+    tf3 = V.config3_render()[0]
+    tf3.vmin, tf3.vmax = 0.0, 1.5
+    tfs = [V.config1_render()[0], V.config2_render(vol=vols[1])[0], tf3]
+    steps = [V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)] * 2 + \
+            [V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, field="magnitude")]
+    reqs = serve.request_stream(77, 12, 1000.0, 3)
+    srv = lv.Server(slots=8, arena_bytes=2 << 30)
+    srv.set_priority_pixels(1 << 20)
+    tickets = [srv.submit(gvs[r.volume], r.camera, tfs[r.volume], steps[r.volume]) for r in reqs]
+    srv.drain()
+    assert srv.stats()["max_running"] >= 2
+    for r, t in zip(reqs, tickets):
+        alone = gvs[r.volume].render(r.camera, tfs[r.volume], steps[r.volume])
+        assert torch.equal(srv.image(t), alone)
+        srv.release(t)
+    srv.close()
+    for g in gvs:
+        g.close()
