@@ -186,3 +186,27 @@ def test_full_size_mix_identical_to_alone():
     srv.close()
     for g in gvs:
         g.close()
+
+
+def test_drain_reports_memory_held_by_unreleased_frames(resident):
+    """Frames kept in the arena (no host copy, not released) can block the
+    queue; drain then returns an error instead of waiting forever, and
+    releasing them lets the rest through."""
+    gvs, tfs, steps = resident
+    img = 512 * 512 * 16
+    srv = lv.Server(slots=4, arena_bytes=2 * img + (1 << 20))
+    cams = [serve.orbit_view(0, k, 1, 512, 512) for k in range(4)]
+    tickets = [srv.submit(gvs[0], c, tfs[0], steps[0]) for c in cams]
+    with pytest.raises(lv.LrvolError) as e:
+        srv.drain()
+    assert e.value.status == lv.ERR_OOM
+    st = srv.stats()
+    assert st["done"] == 2 and st["queued"] == 2
+    for t in tickets[:2]:
+        srv.release(t)
+    srv.drain()
+    assert srv.stats()["done"] == 4
+    for c, t in zip(cams[2:], tickets[2:]):
+        assert torch.equal(srv.image(t), gvs[0].render(c, tfs[0], steps[0]))
+        srv.release(t)
+    srv.close()
