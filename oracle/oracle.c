@@ -20,7 +20,17 @@
  *   orc_render       per pixel: ray setup, sampling at a fixed step, at the
  *                    adaptive distance of Eq. 4, or at Eq. 4 scaled by a given
  *                    per-element multiplier (the learned step), transfer
- *                    function, and front-to-back compositing (Alg. 2)
+ *                    function, optional gradient shading (Sec. 4.1) and
+ *                    trimming interval, and front-to-back compositing (Alg. 2)
+ *   orc_bspline_d1, orc_eval_grad
+ *                    derivative of each Eq. 1 factor, gradient of Eq. 2
+ *   orc_labels       training labels of the learned step (Eq. 4 visits judged
+ *                    against fine-step Alg. 2 composites)
+ *   orc_trim         per-pixel first front / last back face of a closed mesh
+ *                    (the z-prepass of Sec. 4.1), watertight FP32 hits
+ *   orc_streamlines  streamlines by explicit Runge-Kutta methods (Sec. 5,
+ *                    Eq. 5), FP64 outer loop, fixed / Eq. 4 / adaptive steps
+ *   orc_tubes        streamline tubes as capsules (Sec. 5.3)
  *
  * Readings of points the paper leaves open (each listed in the design notes):
  *   - intervals are half open, [lo, hi); the upper domain face x = 1 belongs
