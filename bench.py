@@ -618,7 +618,7 @@ def run_ours(args):
 
     sl = None
     if args.streamlines and ws == 1:
-        sl = streamline_leg(stream)
+        sl = streamline_leg(stream, n_seeds=args.sl_seeds)
 
     trimming = None
     if ws == 1 and args.workload == "cfg2":
@@ -724,6 +724,8 @@ def main():
                     help="also time the frame for 1^3 .. 256^3 trees (the paper's look-up comparison)")
     ap.add_argument("--no-streamlines", dest="streamlines", action="store_false",
                     help="skip the streamline runs on config 3")
+    ap.add_argument("--sl-seeds", type=int, default=65536,
+                    help="seeds of the streamline runs (a smaller rake makes a small profiling case)")
     args = ap.parse_args()
     args.warmup = max(3, args.warmup)   # at least 3 untimed warm-up frames
     if args.impl == "reference":

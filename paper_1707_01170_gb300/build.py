@@ -20,6 +20,7 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
          # with a fixed order of operations, shared by the ray definition)
          "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math"]
 SOURCES = ["kernels.cu", "host.cpp", "server.cpp"]
+HEADERS = ["lrvol_internal.h"]
 
 
 def nvcc() -> str:
@@ -37,8 +38,8 @@ def _stale(lib: str, deps) -> bool:
 
 
 def build(force: bool = False, verbose: bool = False, extra=()) -> str:
-    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, "lrvol_internal.h"),
-                                                        os.path.join(INCLUDE, "lrvol.h"), __file__]
+    deps = [os.path.join(CSRC, s) for s in SOURCES] + [os.path.join(CSRC, h) for h in HEADERS] + \
+        [os.path.join(INCLUDE, "lrvol.h"), __file__]
     if not force and not _stale(LIB, deps):
         return LIB
     os.makedirs(OBJDIR, exist_ok=True)

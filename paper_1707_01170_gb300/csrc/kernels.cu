@@ -1726,7 +1726,7 @@ cudaError_t launch_trim(const RayConsts &ray, int width, int height, const float
 // ----------------------------------------------------------------------------
 // Streamlines (Sec. 5): dx/dt = f(x) by explicit Runge-Kutta methods (Eq. 5),
 // one thread per seed.  The outer loop keeps x as an unevaluated float pair
-// (hi + lo, about 48 significant bits) and t in FP64: on this GPU FP64
+// (hi + lo, about 48 significant bits) and t in FP64: on GB300 FP64
 // arithmetic runs at a small fraction of the FP32 rate, and compensated
 // FP32 sums keep the accumulation exact enough that the steps are not lost
 // to rounding (the reason for the paper's double-precision outer loop,
@@ -1846,11 +1846,19 @@ __device__ __forceinline__ void trace_line(const SLParams &sp, const double *__r
   o[0] = SLSample{(double)xh[0] + (double)xl[0], (double)xh[1] + (double)xl[1], (double)xh[2] + (double)xl[2],
                   0.0};
   nout = 1;
+  // FP64 runs at a small fraction of the FP32 rate on GB300, so the time
+  // bookkeeping keeps to one FP64 add per step: h and fl32(h) change only
+  // with the element (Eq. 4 rule) or the controller (adaptive rule); the
+  // comparisons with t_end compare bit patterns (t, t_end >= 0 order like
+  // their bits); the loop ends on a flag set with the step that reaches t_end.
   double t = 0.0;
   float dsn = F.ra.w;  // Eq. 4 step of the element holding x_n
   double h = sp.rule == 0 ? sp.h : (sp.rule == 1 ? sp.h * (double)dsn : (sp.h > 0.0 ? sp.h : (double)dsn));
+  float hf_h = __double2float_rn(h), ds_h = dsn;   // fl32(h); the Eq. 4 step h was formed from
+  const long long t_end_bits = __double_as_longlong(sp.t_end);
+  bool done = false;   // t >= t_end (t_end > 0 is checked on the host)
   for (;;) {
-    if (!(t < sp.t_end)) {
+    if (done) {
       st = 0;
       break;
     }
@@ -1858,18 +1866,22 @@ __device__ __forceinline__ void trace_line(const SLParams &sp, const double *__r
       st = 2;
       break;
     }
-    if (sp.rule == 1) h = sp.h * (double)dsn;
-    if (sp.rule == 0) h = sp.h;
+    if (sp.rule == 1 && dsn != ds_h) {
+      h = sp.h * (double)dsn;
+      hf_h = __double2float_rn(h);
+      ds_h = dsn;
+    }
     bool taken = false, left = false;
     float nh[3], nl[3];
     for (int tries = 0; tries < 64 && !taken; ++tries) {
+      const double tn = t + h;
+      const bool last = __double_as_longlong(tn) > t_end_bits;
       double hs = h;
-      bool last = false;
-      if (t + hs > sp.t_end) {
+      float hf = hf_h;
+      if (last) {
         hs = sp.t_end - t;
-        last = true;
+        hf = __double2float_rn(hs);
       }
-      const float hf = __double2float_rn(hs);
       float k[6][3];
 #pragma unroll
       for (int i = 0; i < 6; ++i) {
@@ -1914,9 +1926,13 @@ __device__ __forceinline__ void trace_line(const SLParams &sp, const double *__r
         fac = fminf(fmaxf(fac, 0.2f), 5.f);
         if (err > sp.tol_f) {
           h = hs * (double)fac;
+          hf_h = __double2float_rn(h);
           continue;
         }
-        if (!last) h = hs * (double)fac;
+        if (!last) {
+          h = hs * (double)fac;
+          hf_h = __double2float_rn(h);
+        }
       }
       for (int a = 0; a < 3; ++a) {
         nh[a] = xh[a];
@@ -1931,7 +1947,8 @@ __device__ __forceinline__ void trace_line(const SLParams &sp, const double *__r
         break;
       }
       dsn = F.ra.w;
-      t = last ? sp.t_end : t + hs;
+      t = last ? sp.t_end : tn;
+      done = last || __double_as_longlong(tn) == t_end_bits;
       taken = true;
     }
     if (left) {
@@ -1955,12 +1972,17 @@ __device__ __forceinline__ void trace_line(const SLParams &sp, const double *__r
 
 // Persistent threads: a grid that fits on the GPU at once takes lines from
 // a counter until none is left, so lines of very different lengths do not
-// leave a partial last wave idle behind the longest one.
+// leave a partial last wave idle behind the longest one.  Only the first
+// `lanes` lanes of each warp trace lines: with fewer lines than the GPU has
+// warp slots, one line per warp keeps a line from waiting on its warp-mates'
+// element look-ups (a line's steps are a sequential chain, so its latency is
+// what a small rake of seeds waits for).
 template <int P, int STORE>
 __global__ void __launch_bounds__(128) k_streamlines(const __grid_constant__ SLParams sp,
-                                                     const double *__restrict__ seeds, int64_t n,
+                                                     const double *__restrict__ seeds, int64_t n, int lanes,
                                                      SLSample *__restrict__ out, int32_t *__restrict__ count,
                                                      int32_t *__restrict__ status) {
+  if ((int)(threadIdx.x & 31) >= lanes) return;
   for (;;) {
     const int64_t q = (int64_t)atomicAdd(sp.queue, 1ull);
     if (q >= n) return;
@@ -2008,9 +2030,13 @@ cudaError_t launch_sl(const SLParams &sp, const double *seeds, int64_t n, SLSamp
   if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
   if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_streamlines<P, STORE>, 128, 0)) != cudaSuccess)
     return e;
-  const int64_t need = (n + 127) / 128, fit = (int64_t)sms * (per_sm > 0 ? per_sm : 1);
+  const int64_t fit = (int64_t)sms * (per_sm > 0 ? per_sm : 1);   // resident CTAs of 4 warps
+  int64_t lanes = (n + 4 * fit - 1) / (4 * fit);                      // lines per warp, 1..32
+  lanes = lanes < 1 ? 1 : (lanes > 32 ? 32 : lanes);
+  const int64_t need = (n + 4 * lanes - 1) / (4 * lanes);
   if ((e = cudaMemsetAsync(sp.queue, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
-  k_streamlines<P, STORE><<<(unsigned)(need < fit ? need : fit), 128, 0, s>>>(sp, seeds, n, o, count, status);
+  k_streamlines<P, STORE><<<(unsigned)(need < fit ? need : fit), 128, 0, s>>>(sp, seeds, n, (int)lanes, o, count,
+                                                                             status);
   return cudaGetLastError();
 }
 
