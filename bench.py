@@ -416,6 +416,26 @@ def streamline_leg(stream, n_seeds: int = 65536, n_err: int = 4096, t_end: float
     out["tubes"] = {"lines": n_t, "segments": segs, "radius": radius, "image": f"{WIDTH}x{HEIGHT}",
                     "ms": e0.elapsed_time(e1) / reps, "covered_pixels": int((img[..., 3] > 0).sum()),
                     "from": "the last run's first lines"}
+    # small rakes (the paper traces 88 to 250 seeds): a rake's time is its
+    # slowest line's latency, so these runs show the per-line latency path
+    out["small_rakes"] = []
+    for n_small in (256, 4096):
+        sub = seeds[:n_small].contiguous()
+        for method, rule, h, tol in (("RK4", "heuristic", 1.0, 0.0), ("RKF45", "adaptive", 0.0, 1e-6)):
+            run = lambda: lv.streamlines(g, sub, method, rule, h, t_end, tol, max_samples,
+                                         out=(buf[0][:n_small], buf[1][:n_small], buf[2][:n_small]), stream=stream)
+            run()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(reps):
+                run()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            cnt = buf[1][:n_small].to(torch.int64)
+            out["small_rakes"].append({"seeds": n_small, "method": method, "rule": rule, "ms": e0.elapsed_time(e1) / reps,
+                                       "accepted_steps": int((cnt - 1).clamp(min=0).sum()),
+                                       "longest_line_steps": int(cnt.max()) - 1})
     g.close()
     return out
 

@@ -1741,6 +1741,22 @@ struct __align__(32) SLSample {
   double x, y, z, t;
 };
 
+// A sample x = (double)x_hi + (double)x_lo.  With fewer than 32 lines per
+// warp the tracing kernel stores the float pairs (x_hi, x_lo, y_hi, y_lo,
+// z_hi, z_lo) and t in the same 32 bytes instead, and a second pass widens
+// them in place with all 32 lanes of a warp on one line's samples: FP64
+// instructions cost the same per warp whatever the number of active lanes.
+// With full warps the extra pass over the samples costs more than it saves.
+__device__ __forceinline__ void store_sample(SLSample *o, const float *xh, const float *xl, double t, bool pairs) {
+  if (pairs) {
+    float4 *o4 = reinterpret_cast<float4 *>(o);
+    o4[0] = make_float4(xh[0], xl[0], xh[1], xl[1]);
+    o4[1] = make_float4(xh[2], xl[2], __int_as_float(__double2loint(t)), __int_as_float(__double2hiint(t)));
+  } else {
+    *o = SLSample{(double)xh[0] + (double)xl[0], (double)xh[1] + (double)xl[1], (double)xh[2] + (double)xl[2], t};
+  }
+}
+
 struct SLTab {
   int s, embedded, q_low;
   float a[6][6], b[6], bh[6];
@@ -1843,8 +1859,7 @@ __device__ __forceinline__ void trace_line(const SLParams &sp, const double *__r
     status[q] = 1;
     return;
   }
-  o[0] = SLSample{(double)xh[0] + (double)xl[0], (double)xh[1] + (double)xl[1], (double)xh[2] + (double)xl[2],
-                  0.0};
+  store_sample(o, xh, xl, 0.0, sp.pair_out);
   nout = 1;
   // FP64 runs at a small fraction of the FP32 rate on GB300, so the time
   // bookkeeping keeps to one FP64 add per step: h and fl32(h) change only
@@ -1963,8 +1978,7 @@ __device__ __forceinline__ void trace_line(const SLParams &sp, const double *__r
       xh[a] = nh[a];
       xl[a] = nl[a];
     }
-    o[nout++] = SLSample{(double)xh[0] + (double)xl[0], (double)xh[1] + (double)xl[1],
-                         (double)xh[2] + (double)xl[2], t};
+    store_sample(o + nout++, xh, xl, t, sp.pair_out);
   }
   count[q] = nout;
   status[q] = st;
@@ -1987,6 +2001,21 @@ __global__ void __launch_bounds__(128) k_streamlines(const __grid_constant__ SLP
     const int64_t q = (int64_t)atomicAdd(sp.queue, 1ull);
     if (q >= n) return;
     trace_line<P, STORE>(sp, seeds, q, out, count, status);
+  }
+}
+
+// The FP64 samples x = (double)x_hi + (double)x_lo, in place; one warp per line.
+__global__ void __launch_bounds__(128) k_sl_widen(SLSample *__restrict__ out, const int32_t *__restrict__ count,
+                                                  int64_t n, int max_samples) {
+  const int64_t q = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  if (q >= n) return;
+  SLSample *o = out + q * (int64_t)max_samples;
+  const int c = count[q];
+  for (int i = threadIdx.x & 31; i < c; i += 32) {
+    const float4 *p4 = reinterpret_cast<const float4 *>(o + i);
+    const float4 a = p4[0], b = p4[1];
+    o[i] = SLSample{(double)a.x + (double)a.y, (double)a.z + (double)a.w, (double)b.x + (double)b.y,
+                    __hiloint2double(__float_as_int(b.w), __float_as_int(b.z))};
   }
 }
 
@@ -2034,9 +2063,13 @@ cudaError_t launch_sl(const SLParams &sp, const double *seeds, int64_t n, SLSamp
   int64_t lanes = (n + 4 * fit - 1) / (4 * fit);                      // lines per warp, 1..32
   lanes = lanes < 1 ? 1 : (lanes > 32 ? 32 : lanes);
   const int64_t need = (n + 4 * lanes - 1) / (4 * lanes);
+  SLParams spl = sp;
+  spl.pair_out = lanes < 32;
   if ((e = cudaMemsetAsync(sp.queue, 0, sizeof(unsigned long long), s)) != cudaSuccess) return e;
-  k_streamlines<P, STORE><<<(unsigned)(need < fit ? need : fit), 128, 0, s>>>(sp, seeds, n, (int)lanes, o, count,
+  k_streamlines<P, STORE><<<(unsigned)(need < fit ? need : fit), 128, 0, s>>>(spl, seeds, n, (int)lanes, o, count,
                                                                              status);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (spl.pair_out) k_sl_widen<<<(unsigned)((n + 3) / 4), 128, 0, s>>>(o, count, n, sp.max_samples);
   return cudaGetLastError();
 }
 

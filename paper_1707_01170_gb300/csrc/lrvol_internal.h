@@ -226,6 +226,7 @@ struct SLParams {
   int method, rule, max_samples;
   double h, t_end;
   float tol_f;
+  bool pair_out;      // streamlines: store float pairs, widened to FP64 by a second pass
 };
 cudaError_t launch_streamlines(const SLParams &sp, int degree, int storage, const double *seeds, int64_t n,
                                double *out, int32_t *count, int32_t *status, cudaStream_t s);

@@ -147,6 +147,22 @@ def test_exit_cap_and_status_match_oracle():
     gv.close()
 
 
+@pytest.mark.parametrize("method,rule,h,tol", [("RK4", "heuristic", 1.0, 0.0), ("RKF45", "adaptive", 0.0, 1e-6)])
+def test_lines_do_not_depend_on_the_rake_size(swirl, method, rule, h, tol):
+    """The launch traces 1 to 32 lines per warp depending on the number of
+    seeds; every line must come out bit for bit the same either way."""
+    vol, orc, gv = swirl
+    seeds = np.random.default_rng(3).uniform(0.15, 0.85, (20000, 3))
+    big = _gpu_lines(gv, seeds, method, rule, h, 0.6, tol, max_samples=512)
+    for n in (1, 37, 700):
+        small = _gpu_lines(gv, seeds[:n], method, rule, h, 0.6, tol, max_samples=512)
+        np.testing.assert_array_equal(small[1], big[1][:n])
+        np.testing.assert_array_equal(small[2], big[2][:n])
+        for j in range(n):
+            assert np.array_equal(small[0][j, :small[1][j]], big[0][j, :big[1][j]])
+    assert (big[1] >= 2).mean() > 0.9
+
+
 def test_rejects_bad_arguments(helix):
     vol, orc, gv = helix
     seeds = torch.zeros((2, 3), dtype=torch.float64, device="cuda")
