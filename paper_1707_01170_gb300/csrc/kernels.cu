@@ -2021,22 +2021,34 @@ __global__ void __launch_bounds__(128) k_sl_widen(SLSample *__restrict__ out, co
 
 // Eq. 7 per streamline: sum over the approximation's samples i >= 1 of
 // (t_i - t_{i-1}) * |x_ref(t_i) - y_i|, x_ref linear between its samples.
-__global__ void k_streamline_error(const SLSample *__restrict__ ref, const int32_t *__restrict__ rc, int rmax,
-                                   const SLSample *__restrict__ app, const int32_t *__restrict__ ac, int amax,
-                                   int64_t n, double *__restrict__ sums) {
-  const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+__global__ void __launch_bounds__(128) k_streamline_error(const SLSample *__restrict__ ref,
+                                                          const int32_t *__restrict__ rc, int rmax,
+                                                          const SLSample *__restrict__ app,
+                                                          const int32_t *__restrict__ ac, int amax, int64_t n,
+                                                          double *__restrict__ sums) {
+  // one warp per line; lane l takes the approximation's samples l+1, l+33, ...
+  const int64_t q = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
   if (q >= n) return;
+  const int lane = threadIdx.x & 31;
   const SLSample *r = ref + q * (int64_t)rmax, *y = app + q * (int64_t)amax;
   const int nr = rc[q], na = ac[q];
   double acc = 0.0;
   if (nr >= 2 && na >= 2) {
-    int j = 0;
     const double tlast = r[nr - 1].t;
-    for (int i = 1; i < na; ++i) {
+    for (int i = 1 + lane; i < na; i += 32) {
       const SLSample p = y[i];
-      if (!(p.t <= tlast)) break;
-      while (j + 2 < nr && r[j + 1].t < p.t) ++j;
-      const SLSample r0 = r[j], r1 = r[j + 1];
+      if (!(p.t <= tlast)) break;   // the samples after it are later still
+      // reference segment [j, j+1]: j = #{m in [1, nr-2] : t_m < t_i}, the
+      // first segment that ends at or after t_i (reference times increase)
+      int lo = 1, hi = nr - 1;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (r[mid].t < p.t)
+          lo = mid + 1;
+        else
+          hi = mid;
+      }
+      const SLSample r0 = r[lo - 1], r1 = r[lo];
       const double dt = r1.t - r0.t;
       const double f = dt > 0.0 ? (p.t - r0.t) / dt : 0.0;
       const double ex = fma(f, r1.x - r0.x, r0.x) - p.x;
@@ -2045,7 +2057,9 @@ __global__ void k_streamline_error(const SLSample *__restrict__ ref, const int32
       acc = fma(p.t - y[i - 1].t, sqrt(fma(ex, ex, fma(ey, ey, ez * ez))), acc);
     }
   }
-  sums[q] = acc;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+  if (lane == 0) sums[q] = acc;
 }
 
 }  // namespace
@@ -2299,9 +2313,9 @@ cudaError_t launch_tubes(const TubeParams &tp, int degree, int storage, cudaStre
 
 cudaError_t launch_streamline_error(const double *ref, const int32_t *rc, int rmax, const double *app,
                                     const int32_t *ac, int amax, int64_t n, double *sums, cudaStream_t s) {
-  k_streamline_error<<<(unsigned)((n + 127) / 128), 128, 0, s>>>(reinterpret_cast<const SLSample *>(ref), rc, rmax,
-                                                                 reinterpret_cast<const SLSample *>(app), ac, amax, n,
-                                                                 sums);
+  k_streamline_error<<<(unsigned)((n + 3) / 4), 128, 0, s>>>(reinterpret_cast<const SLSample *>(ref), rc, rmax,
+                                                             reinterpret_cast<const SLSample *>(app), ac, amax, n,
+                                                             sums);
   return cudaGetLastError();
 }
 

@@ -132,6 +132,37 @@ def test_eq7_kernel_matches_oracle(helix):
     assert E > 0
 
 
+def test_eq7_kernel_edge_cases():
+    """Synthetic line sets: approximations running past the reference's last
+    time, lines with 0 or 1 samples on either side, two-sample references,
+    samples exactly at reference times, and lines longer than a warp's 32
+    lanes many times over."""
+    rng = np.random.default_rng(17)
+    n, rmax, amax = 64, 700, 300
+    ref = np.zeros((n, rmax, 4))
+    app = np.zeros((n, amax, 4))
+    rc = rng.integers(0, rmax + 1, n).astype(np.int32)
+    ac = rng.integers(0, amax + 1, n).astype(np.int32)
+    rc[:4] = (0, 1, 2, 2)
+    ac[4:8] = (0, 1, 2, amax)
+    for j in range(n):
+        tr = np.cumsum(rng.uniform(1e-3, 3e-3, rmax))
+        tr -= tr[0]
+        ref[j, :, 3] = tr
+        ref[j, :, :3] = rng.normal(size=(rmax, 3)).cumsum(axis=0) * 1e-2
+        ta = np.cumsum(rng.uniform(1e-3, 8e-3, amax))
+        ta -= ta[0]
+        if j % 3 == 0:                       # some samples exactly at reference times
+            k = np.concatenate([[0], np.sort(rng.choice(np.arange(1, rmax), amax - 1, replace=False))])
+            ta = tr[k]
+        app[j, :, 3] = ta
+        app[j, :, :3] = rng.normal(size=(amax, 3)).cumsum(axis=0) * 1e-2
+    want, E = streamline_error(ref, rc, app, ac)
+    got = lv.streamline_error(*(torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in (ref, rc, app, ac))).cpu().numpy()
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-18)
+    assert np.count_nonzero(want) > n // 2
+
+
 def test_exit_cap_and_status_match_oracle():
     vol = V.tensor_product((2, 2, 2), (2, 2, 2), ncomp=3, coef=np.tile([1.0, 0.0, 0.0], (4 ** 3, 1)))
     gv = lv.Volume(vol).build_accel((4, 4, 4)).to_bezier(lv.STORE_BF16)
