@@ -37,7 +37,7 @@ _LAYERS = [(_IN, _HID), (_HID, _HID), (_HID, _HID), (_HID, 1)]
 class TrainConfig:
     seed: int = 1707011790
     h_fine: float = 1.0 / 2048
-    tau: float = 3e-4
+    tau: float = 4e-4
     cand: tuple = CAND
     steps: int = 2000
     batch: int = 8192
