@@ -305,8 +305,9 @@ int lrvol_get_bezier(lrvol_t vol, double *host_out);
  * front-facing when the ray sees that winding.  Hits are decided by the
  * watertight ray/triangle test of Woop, Benthin and Wald (JCGT 2013) in FP32,
  * retrying an edge function that is exactly 0 in FP64, so rays through
- * shared edges and vertices are not lost.  Each triangle is handled by one
- * warp over the pixels of its conservative screen box.
+ * shared edges and vertices are not lost.  A warp sets up 32 triangles, one
+ * per lane, and tests the pixel rays of their conservative screen boxes
+ * (pixel centres within 1/4 pixel of the projected box) 32 at a time.
  * tri_dev: n_tri x 9 floats (device); trim_dev: height x width x 2 floats
  * (device, overwritten).  The camera's row range is ignored.
  * ------------------------------------------------------------------------- */
@@ -369,8 +370,9 @@ int lrvol_streamlines(lrvol_t vol, const lrvol_streamline_params *params, const 
  * order).  The pixel then takes the colour map's RGB at the speed |f| of the
  * volume at the closest point on the winning segment's axis, times
  * I = max(0.4, |n . d|), n the capsule normal at the hit; alpha 1; pixels
- * without a hit are (0, 0, 0, 0).  Each segment is one warp over the pixels
- * of its conservative screen box; hits merge by a 64-bit atomic minimum of
+ * without a hit are (0, 0, 0, 0).  A warp sets up 32 consecutive segments of
+ * a line, one per lane, and tests the pixel rays of their conservative
+ * screen boxes 32 at a time; hits merge by a 64-bit atomic minimum of
  * (t bits, segment index) in vis_dev (height x width uint64 scratch,
  * caller-owned), then one thread per pixel shades the winner into rgba_dev
  * (height x width x 4 floats).  Needs a 3-vector volume (build_accel,

@@ -1598,6 +1598,7 @@ __device__ __forceinline__ float pick3(int k, float x, float y, float z) { retur
 // Watertight ray/triangle test (Woop, Benthin and Wald, JCGT 2013), FP32,
 // with the oracle's order of operations; component selection by value so
 // that nothing goes to local memory.
+// v: the triangle's 9 coordinates, in global memory or in registers (plain loads).
 __device__ __forceinline__ bool tri_hit(const Ray &ray, const float *__restrict__ v, float &t, bool &front) {
   const float d0 = ray.d[0], d1 = ray.d[1], d2 = ray.d[2];
   int kz = 0;
@@ -1612,12 +1613,12 @@ __device__ __forceinline__ bool tri_hit(const Ray &ray, const float *__restrict_
   }
   const float Sx = __fdiv_rn(pick3(kx, d0, d1, d2), dz), Sy = __fdiv_rn(pick3(ky, d0, d1, d2), dz);
   const float Sz = __fdiv_rn(1.f, dz);
-  const float a0 = __fsub_rn(__ldg(v + 0), ray.o[0]), a1 = __fsub_rn(__ldg(v + 1), ray.o[1]);
-  const float a2 = __fsub_rn(__ldg(v + 2), ray.o[2]);
-  const float b0 = __fsub_rn(__ldg(v + 3), ray.o[0]), b1 = __fsub_rn(__ldg(v + 4), ray.o[1]);
-  const float b2 = __fsub_rn(__ldg(v + 5), ray.o[2]);
-  const float c0 = __fsub_rn(__ldg(v + 6), ray.o[0]), c1 = __fsub_rn(__ldg(v + 7), ray.o[1]);
-  const float c2 = __fsub_rn(__ldg(v + 8), ray.o[2]);
+  const float a0 = __fsub_rn(v[0], ray.o[0]), a1 = __fsub_rn(v[1], ray.o[1]);
+  const float a2 = __fsub_rn(v[2], ray.o[2]);
+  const float b0 = __fsub_rn(v[3], ray.o[0]), b1 = __fsub_rn(v[4], ray.o[1]);
+  const float b2 = __fsub_rn(v[5], ray.o[2]);
+  const float c0 = __fsub_rn(v[6], ray.o[0]), c1 = __fsub_rn(v[7], ray.o[1]);
+  const float c2 = __fsub_rn(v[8], ray.o[2]);
   const float Akz = pick3(kz, a0, a1, a2), Bkz = pick3(kz, b0, b1, b2), Ckz = pick3(kz, c0, c1, c2);
   const float Ax = __fsub_rn(pick3(kx, a0, a1, a2), __fmul_rn(Sx, Akz));
   const float Ay = __fsub_rn(pick3(ky, a0, a1, a2), __fmul_rn(Sy, Akz));
@@ -1644,66 +1645,129 @@ __device__ __forceinline__ bool tri_hit(const Ray &ray, const float *__restrict_
   return true;
 }
 
+// The pixels whose centres (i + 1/2, j + 1/2) project into the image-plane
+// box [amin, amax] x [bmin, bmax], widened by a margin: 1/4 pixel plus 1e-5
+// of the box's coordinates in pixels.  The FP32 projection of a primitive's
+// vertices and the FP32 pixel rays of make_ray are each within a few ulps of
+// exact, a few thousandths of a pixel even for narrow fields of view, so
+// every pixel whose ray can hit the primitive is in the box.  False if the
+// box holds no pixel centre.
+__device__ __forceinline__ bool pixel_box(const RayConsts &K, int width, int height, float amin, float amax,
+                                          float bmin, float bmax, int &i0, int &i1, int &j0, int &j1) {
+  const float ia = (amin - K.sxo) / K.sxs - 0.5f, ib = (amax - K.sxo) / K.sxs - 0.5f;
+  const float ja = (bmin - K.syo) / K.sys - 0.5f, jb = (bmax - K.syo) / K.sys - 0.5f;
+  const float mi = 0.25f + 1e-5f * (fabsf(amin) + fabsf(amax) + 1.f) / fabsf(K.sxs);
+  const float mj = 0.25f + 1e-5f * (fabsf(bmin) + fabsf(bmax) + 1.f) / fabsf(K.sys);
+  // clamp before converting (NaN widens to the whole image)
+  const float lo_i = fmaxf(fminf(ia, ib) - mi, -1.f), hi_i = fminf(fmaxf(ia, ib) + mi, (float)width);
+  const float lo_j = fmaxf(fminf(ja, jb) - mj, -1.f), hi_j = fminf(fmaxf(ja, jb) + mj, (float)height);
+  i0 = max(0, (int)ceilf(lo_i));
+  i1 = min(width - 1, (int)floorf(hi_i));
+  j0 = max(0, (int)ceilf(lo_j));
+  j1 = min(height - 1, (int)floorf(hi_j));
+  return i0 <= i1 && j0 <= j1;
+}
+
 __global__ void k_trim_init(float2 *__restrict__ out, int64_t n) {
   const int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (q < n) out[q] = make_float2(__int_as_float(0x7f800000), 0.f);
 }
 
+// One warp takes 32 consecutive triangles: lane l projects triangle l of the
+// group and finds its pixel box, then the warp walks the group's (triangle,
+// pixel) pairs 32 at a time, each lane finding its pair's triangle by a
+// search over the lanes' prefix sums and fetching that triangle by shuffles.
+// Small triangles (most of a fine mesh covers a pixel centre or none) then
+// cost one lane's set-up instead of a warp's.  `split` warps share a group,
+// each taking a contiguous part of its pairs, so a coarse mesh of large
+// triangles still spreads over the GPU.
 __global__ void __launch_bounds__(128) k_trim_raster(const RayConsts K, int width, int height,
-                                                     const float *__restrict__ tri, int64_t n_tri,
+                                                     const float *__restrict__ tri, int64_t n_tri, int split,
                                                      float2 *__restrict__ out) {
-  const int64_t tr = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const unsigned full_mask = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  if (tr >= n_tri) return;
-  const float *v = tri + 9 * tr;
-  // conservative pixel box of the projected triangle (whole image when a
-  // vertex is at or behind the eye plane; nothing when all three are)
-  float amin = __int_as_float(0x7f800000), amax = -amin, bmin = amin, bmax = -amin;
-  bool full = false;
-  int behind = 0;
+  const int64_t wid = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int64_t group = wid / split;
+  const int part = (int)(wid - group * split);
+  if (group * 32 >= n_tri) return;   // whole warp
+  const int64_t tr = group * 32 + lane;
+  float v[9];
 #pragma unroll
-  for (int q = 0; q < 3; ++q) {
-    const float X = __ldg(v + 3 * q) - K.E[0], Y = __ldg(v + 3 * q + 1) - K.E[1], Z = __ldg(v + 3 * q + 2) - K.E[2];
-    const float r = X * K.R[0] + Y * K.R[1] + Z * K.R[2];
-    const float u = X * K.U[0] + Y * K.U[1] + Z * K.U[2];
-    float a = r, b = u;
-    if (K.persp) {
-      const float z = X * K.F[0] + Y * K.F[1] + Z * K.F[2];
-      if (!(z > 1e-6f)) {
-        full = true;
-        ++behind;
-        continue;
+  for (int c = 0; c < 9; ++c) v[c] = 0.f;
+  int i0 = 0, j0 = 0, bw = 1, cnt = 0;
+  if (tr < n_tri) {
+#pragma unroll
+    for (int c = 0; c < 9; ++c) v[c] = __ldg(tri + 9 * tr + c);
+    // conservative pixel box of the projected triangle (whole image when a
+    // vertex is at or behind the eye plane; nothing when all three are)
+    float amin = __int_as_float(0x7f800000), amax = -amin, bmin = amin, bmax = -amin;
+    bool full = false;
+    int behind = 0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      const float X = v[3 * q] - K.E[0], Y = v[3 * q + 1] - K.E[1], Z = v[3 * q + 2] - K.E[2];
+      const float r = X * K.R[0] + Y * K.R[1] + Z * K.R[2];
+      const float u = X * K.U[0] + Y * K.U[1] + Z * K.U[2];
+      float a = r, b = u;
+      if (K.persp) {
+        const float z = X * K.F[0] + Y * K.F[1] + Z * K.F[2];
+        if (!(z > 1e-6f)) {
+          full = true;
+          ++behind;
+          continue;
+        }
+        a = r / z;
+        b = u / z;
       }
-      a = r / z;
-      b = u / z;
+      amin = fminf(amin, a);
+      amax = fmaxf(amax, a);
+      bmin = fminf(bmin, b);
+      bmax = fmaxf(bmax, b);
     }
-    amin = fminf(amin, a);
-    amax = fmaxf(amax, a);
-    bmin = fminf(bmin, b);
-    bmax = fmaxf(bmax, b);
+    int i1 = width - 1, j1 = height - 1;
+    if (behind < 3 && (full || pixel_box(K, width, height, amin, amax, bmin, bmax, i0, i1, j0, j1))) {
+      if (full) {
+        i0 = 0;
+        j0 = 0;
+        i1 = width - 1;
+        j1 = height - 1;
+      }
+      bw = i1 - i0 + 1;
+      cnt = bw * (j1 - j0 + 1);   // <= 32768^2 < 2^31
+    }
   }
-  if (behind == 3) return;
-  int i0 = 0, i1 = width - 1, j0 = 0, j1 = height - 1;
-  if (!full) {
-    const float ia = (amin - K.sxo) / K.sxs - 0.5f, ib = (amax - K.sxo) / K.sxs - 0.5f;
-    const float ja = (bmin - K.syo) / K.sys - 0.5f, jb = (bmax - K.syo) / K.sys - 0.5f;
-    const float lo_i = fminf(ia, ib), hi_i = fmaxf(ia, ib), lo_j = fminf(ja, jb), hi_j = fmaxf(ja, jb);
-    if (!(hi_i >= -2.f && lo_i <= (float)width + 1.f && hi_j >= -2.f && lo_j <= (float)height + 1.f)) return;
-    i0 = max(0, (int)floorf(lo_i) - 2);
-    i1 = min(width - 1, (int)ceilf(hi_i) + 2);
-    j0 = max(0, (int)floorf(lo_j) - 2);
-    j1 = min(height - 1, (int)ceilf(hi_j) + 2);
-    if (i0 > i1 || j0 > j1) return;
+  // prefix sums of the lanes' pair counts
+  long long inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(full_mask, inc, o);
+    if (lane >= o) inc += y;
   }
-  const int bw = i1 - i0 + 1;
-  const int64_t cnt = (int64_t)bw * (j1 - j0 + 1);
-  for (int64_t p = lane; p < cnt; p += 32) {
-    const int i = i0 + (int)(p % bw), j = j0 + (int)(p / bw);
+  const long long total = __shfl_sync(full_mask, inc, 31), exc = inc - cnt;
+  const long long chunk = (((total + split - 1) / split) + 31) & ~31ll;
+  const long long w0 = (long long)part * chunk, w1 = w0 + chunk < total ? w0 + chunk : total;
+  for (long long base = w0; base < w1; base += 32) {
+    const long long w = base + lane;
+    int q = 0;   // the last lane whose pairs start at or before w (its count is then > 0)
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const long long e = __shfl_sync(full_mask, exc, q + step);
+      if (e <= w) q += step;
+    }
+    const long long eq = __shfl_sync(full_mask, exc, q);
+    const int qi0 = __shfl_sync(full_mask, i0, q), qj0 = __shfl_sync(full_mask, j0, q);
+    const int qbw = __shfl_sync(full_mask, bw, q);
+    float tv[9];
+#pragma unroll
+    for (int c = 0; c < 9; ++c) tv[c] = __shfl_sync(full_mask, v[c], q);
+    if (w >= w1) continue;
+    const unsigned pix = (unsigned)(w - eq);
+    const int i = qi0 + (int)(pix % (unsigned)qbw), j = qj0 + (int)(pix / (unsigned)qbw);
     Ray ray;
     make_ray(K, i, j, ray);   // origin and direction; the unit-cube interval is not needed here
     float t;
     bool front;
-    if (!tri_hit(ray, v, t, front)) continue;
+    if (!tri_hit(ray, tv, t, front)) continue;
     unsigned *slot = reinterpret_cast<unsigned *>(out + (int64_t)j * width + i);
     if (front)
       atomicMin(slot, __float_as_uint(t));
@@ -1719,7 +1783,15 @@ cudaError_t launch_trim(const RayConsts &ray, int width, int height, const float
   const int64_t npix = (int64_t)width * height;
   float2 *o = reinterpret_cast<float2 *>(out);
   k_trim_init<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(o, npix);
-  if (n_tri > 0) k_trim_raster<<<(unsigned)((n_tri + 3) / 4), 128, 0, s>>>(ray, width, height, tri, n_tri, o);
+  if (n_tri > 0) {
+    // warps per group of 32 triangles: about 512 pairs per warp when the
+    // mesh covers the image twice, 1 for fine meshes, at most 256
+    const int64_t groups = (n_tri + 31) / 32;
+    int64_t split = (2 * npix + groups * 512 - 1) / (groups * 512);
+    split = split < 1 ? 1 : (split > 256 ? 256 : split);
+    const int64_t warps = groups * split;
+    k_trim_raster<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(ray, width, height, tri, n_tri, (int)split, o);
+  }
   return cudaGetLastError();
 }
 
@@ -2181,62 +2253,102 @@ __global__ void k_vis_init(unsigned long long *__restrict__ vis, int64_t n) {
   if (q < n) vis[q] = ~0ull;
 }
 
-__global__ void __launch_bounds__(128) k_tube_raster(const __grid_constant__ TubeParams tp) {
-  const int64_t s = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+// One warp takes 32 consecutive segment slots of one line (the whole warp
+// leaves at once when the line has no segment there): lane l bounds segment
+// l's capsule on the screen, then the warp walks the group's (segment, pixel)
+// pairs 32 at a time, as the trimming raster does.  `split` warps share a
+// group when few long segments could cover much of the image.
+__global__ void __launch_bounds__(128) k_tube_raster(const __grid_constant__ TubeParams tp, int split) {
+  const unsigned full_mask = 0xffffffffu;
   const int lane = threadIdx.x & 31;
-  if (s >= tp.n_lines * (int64_t)(tp.max_samples - 1)) return;
-  float a[3], b[3];
-  if (!tube_segment(tp, s, a, b)) return;
+  const int64_t wid = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int64_t group = wid / split;
+  const int part = (int)(wid - group * split);
+  const int per = tp.max_samples - 1;                  // segment slots per line
+  const int64_t gpl = (per + 31) / 32;                 // groups per line
+  const int64_t line = group / gpl;
+  if (line >= tp.n_lines) return;                      // whole warp
+  const int k0 = (int)(group - line * gpl) * 32;
+  const int nseg = tp.count[line] - 1;
+  if (k0 >= nseg) return;                              // whole warp
   const RayConsts &K = tp.ray;
-  // conservative pixel box of the capsule's bounding box
-  float amin = __int_as_float(0x7f800000), amax = -amin, bmin = amin, bmax = -amin;
-  bool full = false;
-  int behind = 0;
+  float a[3] = {0.f, 0.f, 0.f}, b[3] = {0.f, 0.f, 0.f};
+  int i0 = 0, j0 = 0, bw = 1, cnt = 0;
+  if (k0 + lane < nseg && tube_segment(tp, line * per + k0 + lane, a, b)) {
+    // conservative pixel box of the capsule's bounding box
+    float amin = __int_as_float(0x7f800000), amax = -amin, bmin = amin, bmax = -amin;
+    bool full = false;
+    int behind = 0;
 #pragma unroll
-  for (int q = 0; q < 8; ++q) {
-    const float cx = ((q & 1) ? fmaxf(a[0], b[0]) + tp.radius : fminf(a[0], b[0]) - tp.radius) - K.E[0];
-    const float cy = ((q & 2) ? fmaxf(a[1], b[1]) + tp.radius : fminf(a[1], b[1]) - tp.radius) - K.E[1];
-    const float cz = ((q & 4) ? fmaxf(a[2], b[2]) + tp.radius : fminf(a[2], b[2]) - tp.radius) - K.E[2];
-    const float r = cx * K.R[0] + cy * K.R[1] + cz * K.R[2];
-    const float u = cx * K.U[0] + cy * K.U[1] + cz * K.U[2];
-    float x = r, y = u;
-    if (K.persp) {
-      const float z = cx * K.F[0] + cy * K.F[1] + cz * K.F[2];
-      if (!(z > 1e-6f)) {
-        full = true;
-        ++behind;
-        continue;
+    for (int q = 0; q < 8; ++q) {
+      const float cx = ((q & 1) ? fmaxf(a[0], b[0]) + tp.radius : fminf(a[0], b[0]) - tp.radius) - K.E[0];
+      const float cy = ((q & 2) ? fmaxf(a[1], b[1]) + tp.radius : fminf(a[1], b[1]) - tp.radius) - K.E[1];
+      const float cz = ((q & 4) ? fmaxf(a[2], b[2]) + tp.radius : fminf(a[2], b[2]) - tp.radius) - K.E[2];
+      const float r = cx * K.R[0] + cy * K.R[1] + cz * K.R[2];
+      const float u = cx * K.U[0] + cy * K.U[1] + cz * K.U[2];
+      float x = r, y = u;
+      if (K.persp) {
+        const float z = cx * K.F[0] + cy * K.F[1] + cz * K.F[2];
+        if (!(z > 1e-6f)) {
+          full = true;
+          ++behind;
+          continue;
+        }
+        x = r / z;
+        y = u / z;
       }
-      x = r / z;
-      y = u / z;
+      amin = fminf(amin, x);
+      amax = fmaxf(amax, x);
+      bmin = fminf(bmin, y);
+      bmax = fmaxf(bmax, y);
     }
-    amin = fminf(amin, x);
-    amax = fmaxf(amax, x);
-    bmin = fminf(bmin, y);
-    bmax = fmaxf(bmax, y);
+    int i1 = tp.width - 1, j1 = tp.height - 1;
+    if (behind < 8 && (full || pixel_box(K, tp.width, tp.height, amin, amax, bmin, bmax, i0, i1, j0, j1))) {
+      if (full) {
+        i0 = 0;
+        j0 = 0;
+        i1 = tp.width - 1;
+        j1 = tp.height - 1;
+      }
+      bw = i1 - i0 + 1;
+      cnt = bw * (j1 - j0 + 1);   // <= 32768^2 < 2^31
+    }
   }
-  if (behind == 8) return;
-  int i0 = 0, i1 = tp.width - 1, j0 = 0, j1 = tp.height - 1;
-  if (!full) {
-    const float ia = (amin - K.sxo) / K.sxs - 0.5f, ib = (amax - K.sxo) / K.sxs - 0.5f;
-    const float ja = (bmin - K.syo) / K.sys - 0.5f, jb = (bmax - K.syo) / K.sys - 0.5f;
-    const float lo_i = fminf(ia, ib), hi_i = fmaxf(ia, ib), lo_j = fminf(ja, jb), hi_j = fmaxf(ja, jb);
-    if (!(hi_i >= -2.f && lo_i <= (float)tp.width + 1.f && hi_j >= -2.f && lo_j <= (float)tp.height + 1.f)) return;
-    i0 = max(0, (int)floorf(lo_i) - 2);
-    i1 = min(tp.width - 1, (int)ceilf(hi_i) + 2);
-    j0 = max(0, (int)floorf(lo_j) - 2);
-    j1 = min(tp.height - 1, (int)ceilf(hi_j) + 2);
-    if (i0 > i1 || j0 > j1) return;
+  long long inc = cnt;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const long long y = __shfl_up_sync(full_mask, inc, o);
+    if (lane >= o) inc += y;
   }
-  const int bw = i1 - i0 + 1;
-  const int64_t cnt = (int64_t)bw * (j1 - j0 + 1);
-  for (int64_t p = lane; p < cnt; p += 32) {
-    const int i = i0 + (int)(p % bw), j = j0 + (int)(p / bw);
+  const long long total = __shfl_sync(full_mask, inc, 31), exc = inc - cnt;
+  const long long chunk = (((total + split - 1) / split) + 31) & ~31ll;
+  const long long w0 = (long long)part * chunk, w1 = w0 + chunk < total ? w0 + chunk : total;
+  for (long long base = w0; base < w1; base += 32) {
+    const long long w = base + lane;
+    int q = 0;   // the last lane whose pairs start at or before w (its count is then > 0)
+#pragma unroll
+    for (int step = 16; step > 0; step >>= 1) {
+      const long long e = __shfl_sync(full_mask, exc, q + step);
+      if (e <= w) q += step;
+    }
+    const long long eq = __shfl_sync(full_mask, exc, q);
+    const int qi0 = __shfl_sync(full_mask, i0, q), qj0 = __shfl_sync(full_mask, j0, q);
+    const int qbw = __shfl_sync(full_mask, bw, q);
+    float qa[3], qb[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      qa[c] = __shfl_sync(full_mask, a[c], q);
+      qb[c] = __shfl_sync(full_mask, b[c], q);
+    }
+    if (w >= w1) continue;
+    const unsigned pix = (unsigned)(w - eq);
+    const int i = qi0 + (int)(pix % (unsigned)qbw), j = qj0 + (int)(pix / (unsigned)qbw);
     Ray ray;
     make_ray(K, i, j, ray);
     float t;
-    if (!capsule_hit(ray, a, b, tp.radius, t)) continue;
-    const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)(uint32_t)s;
+    if (!capsule_hit(ray, qa, qb, tp.radius, t)) continue;
+    const uint32_t sid = (uint32_t)(line * per + k0 + q);
+    const unsigned long long key = ((unsigned long long)__float_as_uint(t) << 32) | (unsigned long long)sid;
     atomicMin(tp.vis + (int64_t)j * tp.width + i, key);
   }
 }
@@ -2292,7 +2404,15 @@ cudaError_t launch_tubes(const TubeParams &tp, int degree, int storage, cudaStre
   const int64_t npix = (int64_t)tp.width * tp.height;
   const int64_t nseg = tp.n_lines * (int64_t)(tp.max_samples - 1);
   k_vis_init<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(tp.vis, npix);
-  if (nseg > 0) k_tube_raster<<<(unsigned)((nseg + 3) / 4), 128, 0, s>>>(tp);
+  if (nseg > 0) {
+    // warps per group of 32 segment slots: as for trimming, counted over the
+    // slots (most of them are empty when lines are short)
+    const int64_t groups = tp.n_lines * ((tp.max_samples - 1 + 31) / 32);
+    int64_t split = (2 * npix + groups * 512 - 1) / (groups * 512);
+    split = split < 1 ? 1 : (split > 256 ? 256 : split);
+    const int64_t warps = groups * split;
+    k_tube_raster<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(tp, (int)split);
+  }
   const unsigned blocks = (unsigned)((npix + 127) / 128);
 #define LRVOL_TUBE_CASE(P_, S_) k_tube_resolve<P_, S_><<<blocks, 128, 0, s>>>(tp)
   switch (degree * 3 + storage) {
