@@ -58,3 +58,23 @@ def test_tubes_occlusion_and_caps():
     gv.close()
     assert np.array_equal(img[..., 3], ref[..., 3].astype(np.float32))
     assert np.abs(img - ref).max() <= 1e-4
+
+
+def test_tubes_few_large_segments_split_over_warps():
+    """Three short lines of thick tubes filling much of a 256x192 view: the
+    raster gives each group of 32 segment slots many warps (the image is
+    large against the number of segments); visibility must still equal the
+    oracle's brute force pixel for pixel."""
+    vol = TU._field_z()
+    gv = lv.Volume(vol).build_accel((8, 8, 8)).to_bezier()
+    s, c = TU._lines([[0.2, 0.3, 0.3], [0.5, 0.35, 0.4], [0.8, 0.3, 0.35]],
+                     [[0.3, 0.8, 0.6], [0.45, 0.5, 0.5], [0.7, 0.45, 0.7]],
+                     [[0.5, 0.2, 0.8], [0.55, 0.6, 0.2]])
+    cam = V.orbit_camera(V.Stream(31), 256, 192)
+    img = lv.tubes(gv, cam, torch.from_numpy(s).cuda(), torch.from_numpy(c.astype(np.int32)).cuda(), 0.06,
+                   TU._cmap()).cpu().numpy()
+    ref = Oracle(vol).tubes(cam, s, c, 0.06, TU._cmap())
+    gv.close()
+    assert np.array_equal(img[..., 3] > 0, ref[..., 3] > 0)
+    assert (ref[..., 3] > 0).mean() > 0.05
+    assert np.abs(img - ref).max() <= 1e-4
