@@ -465,13 +465,17 @@ def trim_leg(gv, vol, tf, cam, step, flush, stream, reps: int = 10):
 
 
 FOREST_SWEEP = (1, 4, 16, 64, 256)
+OCTREE_SWEEP = (1, 4, 16)   # midpoint (octree-style) trees; at 64^3 cfg2 has no trees at all
 
 
 def forest_leg(stream, frames: int = 20):
     """The paper's look-up comparison (Sec. 4.3 tables) on the synthetic
-    volumes: for each forest resolution (trees per axis), the build time on
-    the host, the tree depth statistics and the 1080p frame time (cfg2
-    scalar and cfg3 |v|, Eq. 4 steps, L2 flushed between frames)."""
+    volumes: for each forest resolution (trees per axis) and split rule
+    (depth-balanced k-d trees; octree-style midpoint trees), the build time
+    on the host, the tree depth statistics and the 1080p frame time (cfg2
+    scalar and cfg3 |v|, Eq. 4 steps, L2 flushed between frames).  One
+    balanced tree is the single k-d tree, one midpoint tree the octree, and
+    the forest at the finest element size (no trees) the look-up texture."""
     import torch
     from paper_1707_01170_gb300 import lrvol as lv
     from paper_1707_01170_gb300.synth import volumes as V
@@ -481,10 +485,15 @@ def forest_leg(stream, frames: int = 20):
         vol, tf, cam, step = _workload(name)
         ccam, ctf, cstep = lv.make_camera(cam), lv.make_tf(tf), lv.make_step(step)
         img = torch.empty((HEIGHT, WIDTH, 4), dtype=torch.float32, device="cuda")
-        for b in FOREST_SWEEP:
+        for split, b in [(lv.SPLIT_BALANCED, b) for b in FOREST_SWEEP] + [(lv.SPLIT_MIDPOINT, b) for b in OCTREE_SWEEP]:
             gv = lv.Volume(vol)
             t0 = time.perf_counter()
-            gv.build_accel((b, b, b), stream=stream)
+            try:
+                gv.build_accel((b, b, b), stream=stream, split=split)
+            except lv.LrvolError as e:
+                out.append({"workload": name, "split": "midpoint", "trees_per_axis": b, "unsupported": str(e)})
+                gv.close()
+                continue
             torch.cuda.synchronize()
             build_s = time.perf_counter() - t0
             gv.to_bezier(stream=stream)
@@ -493,7 +502,8 @@ def forest_leg(stream, frames: int = 20):
             torch.cuda.synchronize()
             st = gv.stats()
             ms = _timed_frames([lambda: gv.render(ccam, ctf, cstep, out=img, stream=stream)], frames, flush, stream)[0]
-            out.append({"workload": name, "trees_per_axis": b, "build_s": build_s, "nodes": st["n_nodes"],
+            out.append({"workload": name, "split": "balanced" if split == lv.SPLIT_BALANCED else "midpoint",
+                        "trees_per_axis": b, "build_s": build_s, "nodes": st["n_nodes"],
                         "depth": {"min": st["depth_min"], "max": st["depth_max"], "mean": st["depth_mean"],
                                   "var": st["depth_var"]},
                         "ms_per_frame": ms, "lookups_per_frame": st["lookups"],

@@ -152,6 +152,21 @@ int lrvol_create(const int32_t deg[3], int32_t ncomp, int64_t n_elem, const doub
  * Errors: LRVOL_ERR_ARG (blocks not powers of two), LRVOL_ERR_OOM, LRVOL_ERR_CUDA. */
 int lrvol_build_accel(lrvol_t vol, const int32_t blocks[3], void *stream);
 
+/* The same forest with a choice of split rule inside each block:
+ *   LRVOL_SPLIT_BALANCED  the depth-balanced trees of lrvol_build_accel;
+ *   LRVOL_SPLIT_MIDPOINT  octree-style trees: each node splits its region at
+ *                         the midpoint, on x, y and z in turn (three binary
+ *                         levels are one octree level of the paper's octree
+ *                         look-up, Sec. 3.2); with blocks at the finest
+ *                         element size and no trees the forest is the
+ *                         paper's look-up texture.
+ * Element ids are the same whichever rule builds the forest.  Midpoint splits
+ * reach element faces only at dyadic coordinates: a mesh with other faces
+ * returns LRVOL_ERR_UNSUPPORTED.  Errors otherwise as lrvol_build_accel. */
+#define LRVOL_SPLIT_BALANCED 0
+#define LRVOL_SPLIT_MIDPOINT 1
+int lrvol_build_accel_split(lrvol_t vol, const int32_t blocks[3], int32_t split, void *stream);
+
 /* Change of basis to Bezier blocks (Sec. 3.2.3), FP64 on the GPU by blossoming
  * each incident B-spline's univariate factors over the element (exact up to
  * rounding); kept in FP64 for lrvol_get_bezier, and stored for rendering as

@@ -132,6 +132,8 @@ struct ForestBuilder {
   std::vector<uint32_t> head;
   std::vector<int32_t> depth;  // per block
   int B[3];
+  bool midpoint = false;       // octree-style splits (LRVOL_SPLIT_MIDPOINT)
+  bool unresolved = false;     // a midpoint tree reached kMaxDepth
 
   const double *box(int32_t e) const { return &v->box[6 * (size_t)e]; }
 
@@ -139,6 +141,7 @@ struct ForestBuilder {
   uint32_t build(std::vector<int32_t> &els, const double *rlo, const double *rhi, int d, int *maxd) {
     *maxd = std::max(*maxd, d);
     if (els.size() == 1) return kLeaf | (uint32_t)els[0];
+    if (midpoint) return build_mid(els, rlo, rhi, d, maxd);
     int best_axis = -1;
     double best_t = 0;
     size_t best_score = SIZE_MAX;
@@ -198,6 +201,49 @@ struct ForestBuilder {
     nd.child[0] = build(L, llo, lhi, d + 1, maxd);
     nd.child[1] = build(R, hlo, hhi, d + 1, maxd);
     if (nd.child[0] == kNone || nd.child[1] == kNone) return kNone;
+    nodes[me] = nd;
+    return me;
+  }
+
+  // Octree-style tree: the region's midpoint on axes x, y, z in turn (three
+  // binary levels make one octree level).  An element straddling the plane
+  // goes to both sides; a leaf is a region that one element covers.  Dyadic
+  // faces are reached exactly (midpoints of dyadic regions are dyadic, and
+  // exact in FP32 down to 2^-149); a face at a non-dyadic coordinate never
+  // is, and the tree is abandoned at kMaxDepth.
+  uint32_t build_mid(std::vector<int32_t> &els, const double *rlo, const double *rhi, int d, int *maxd) {
+    if (d >= kMaxDepth - 1) {
+      unresolved = true;
+      return kNone;
+    }
+    const int a = d % 3;
+    const double t = 0.5 * (rlo[a] + rhi[a]);
+    std::vector<int32_t> L, R;
+    for (int32_t e : els) {
+      const double *b = box(e);
+      if (b[a] < t) L.push_back(e);
+      if (b[3 + a] > t) R.push_back(e);
+    }
+    if (L.empty() || R.empty()) return kNone;   // not a box partition
+    uint32_t me = (uint32_t)nodes.size();
+    nodes.push_back(Node{0, 0, {0, 0}});
+    Node nd;
+    float s = round_up_f32(t);
+    std::memcpy(&nd.split_bits, &s, 4);
+    nd.axis = (uint32_t)a;
+    double llo[3], lhi[3], hlo[3], hhi[3];
+    for (int c = 0; c < 3; ++c) {
+      llo[c] = hlo[c] = rlo[c];
+      lhi[c] = hhi[c] = rhi[c];
+    }
+    lhi[a] = t;
+    hlo[a] = t;
+    els.clear();
+    els.shrink_to_fit();
+    nd.child[0] = build(L, llo, lhi, d + 1, maxd);
+    if (nd.child[0] == kNone) return kNone;
+    nd.child[1] = build(R, hlo, hhi, d + 1, maxd);
+    if (nd.child[1] == kNone) return kNone;
     nodes[me] = nd;
     return me;
   }
@@ -477,12 +523,18 @@ int lrvol_create(const int32_t deg[3], int32_t ncomp, int64_t n_elem, const doub
 }
 
 int lrvol_build_accel(lrvol_t v, const int32_t blocks[3], void *stream) {
+  return lrvol_build_accel_split(v, blocks, LRVOL_SPLIT_BALANCED, stream);
+}
+
+int lrvol_build_accel_split(lrvol_t v, const int32_t blocks[3], int32_t split, void *stream) {
   if (!v || !blocks) return fail(LRVOL_ERR_ARG, "null pointer");
+  if (split != LRVOL_SPLIT_BALANCED && split != LRVOL_SPLIT_MIDPOINT) return fail(LRVOL_ERR_ARG, "bad split rule");
   for (int a = 0; a < 3; ++a)
     if (!is_pow2(blocks[a]) || blocks[a] > 1024) return fail(LRVOL_ERR_ARG, "blocks must be powers of two <= 1024");
   if ((int64_t)blocks[0] * blocks[1] * blocks[2] > (int64_t)1 << 28) return fail(LRVOL_ERR_ARG, "too many blocks");
   ForestBuilder fb;
   fb.v = v;
+  fb.midpoint = split == LRVOL_SPLIT_MIDPOINT;
   for (int a = 0; a < 3; ++a) fb.B[a] = blocks[a];
   size_t nblk = (size_t)blocks[0] * blocks[1] * blocks[2];
   fb.head.assign(nblk, kNone);
@@ -490,7 +542,11 @@ int lrvol_build_accel(lrvol_t v, const int32_t blocks[3], void *stream) {
   std::vector<int32_t> all(v->n_elem);
   std::iota(all.begin(), all.end(), 0);
   int b0[3] = {0, 0, 0}, b1[3] = {blocks[0], blocks[1], blocks[2]};
-  if (!fb.region(all, b0, b1)) return fail(LRVOL_ERR_ARG, "elements do not form a box partition of [0,1]^3");
+  if (!fb.region(all, b0, b1)) {
+    if (fb.unresolved)
+      return fail(LRVOL_ERR_UNSUPPORTED, "midpoint splits do not resolve this mesh (faces at non-dyadic coordinates)");
+    return fail(LRVOL_ERR_ARG, "elements do not form a box partition of [0,1]^3");
+  }
   for (uint32_t h : fb.head)
     if (h == kNone) return fail(LRVOL_ERR_ARG, "a forest block holds no element");
   if (fb.nodes.size() >= kLeaf) return fail(LRVOL_ERR_ARG, "forest too large");

@@ -20,9 +20,10 @@ STEP_FIXED, STEP_HEURISTIC, STEP_LEARNED = 0, 1, 2
 FIELD_SCALAR, FIELD_MAGNITUDE, FIELD_COMPONENT = 0, 1, 2
 STORE_F32, STORE_F16, STORE_BF16 = 0, 1, 2
 SHADE_NONE, SHADE_GRADIENT = 0, 1
+SPLIT_BALANCED, SPLIT_MIDPOINT = 0, 1
 NONE = 0xFFFFFFFF
 
-EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
+EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_build_accel_split", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
             "lrvol_eval", "lrvol_eval_grad", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
             "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features", "lrvol_mlp_pack", "lrvol_mlp_infer",
             "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels",
@@ -116,6 +117,8 @@ def load(path: str = LIB_PATH):
         L.lrvol_create.argtypes = [vp, i32, i64, vp, i64, vp, vp, vp, ctypes.POINTER(vp)]
         L.lrvol_build_accel.restype = ctypes.c_int
         L.lrvol_build_accel.argtypes = [vp, vp, vp]
+        L.lrvol_build_accel_split.restype = ctypes.c_int
+        L.lrvol_build_accel_split.argtypes = [vp, vp, i32, vp]
         L.lrvol_to_bezier.restype = ctypes.c_int
         L.lrvol_to_bezier.argtypes = [vp, i32, vp]
         L.lrvol_render.restype = ctypes.c_int
@@ -311,9 +314,14 @@ class Volume:
     def handle(self):
         return self._h
 
-    def build_accel(self, blocks=(64, 64, 64), stream=None):
+    def build_accel(self, blocks=(64, 64, 64), stream=None, split: int = None):
+        """The k-d forest; split=SPLIT_MIDPOINT builds octree-style trees instead."""
         b = np.ascontiguousarray(blocks, dtype=np.int32)
-        _check(load().lrvol_build_accel(self._h, b.ctypes.data, _stream_ptr(stream)), "lrvol_build_accel")
+        if split is None:
+            _check(load().lrvol_build_accel(self._h, b.ctypes.data, _stream_ptr(stream)), "lrvol_build_accel")
+        else:
+            _check(load().lrvol_build_accel_split(self._h, b.ctypes.data, int(split), _stream_ptr(stream)),
+                   "lrvol_build_accel_split")
         return self
 
     def to_bezier(self, storage: int = STORE_F32, stream=None):

@@ -106,6 +106,50 @@ def test_lookup_bit_exact(vols, oracles, name, blocks):
     gv.close()
 
 
+@pytest.mark.parametrize("blocks", [(1, 1, 1), (4, 4, 4), (8, 4, 16)])
+def test_octree_lookup_bit_exact(vols, oracles, blocks):
+    """Midpoint (octree-style) trees over a dyadic mesh give the brute-force
+    element ids, faces included; one tree over the whole cube is the paper's
+    octree look-up."""
+    vol = vols["cfg1"]
+    gv = lv.Volume(vol).build_accel(blocks, split=lv.SPLIT_MIDPOINT)
+    X = _probe_points(vol, 100_000, seed=zlib.crc32(f"oct{blocks}".encode()) % 1000, blocks=blocks)
+    got = gv.lookup(torch.from_numpy(X).cuda()).cpu().numpy().view(np.uint32)
+    want = oracles["cfg1"].lookup(X)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, f"{bad.size} mismatches, e.g. {X[bad[:3]]} gpu {got[bad[:3]]} orc {want[bad[:3]]}"
+    st = gv.stats()
+    assert st["depth_max"] >= st["depth_min"] >= 0 and st["n_nodes"] > 0
+    gv.close()
+
+
+def test_octree_render_identical_to_balanced_forest(vols):
+    vol = vols["cfg1"]
+    tf, cams = V.config1_render()
+    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
+    a = lv.Volume(vol).build_accel((64, 64, 64)).to_bezier()
+    b = lv.Volume(vol).build_accel((1, 1, 1), split=lv.SPLIT_MIDPOINT).to_bezier()
+    for cam in cams:
+        ia, ib = a.render(cam, tf, step), b.render(cam, tf, step)
+        assert torch.equal(ia, ib)
+    assert a.stats()["samples"] == b.stats()["samples"] and a.stats()["lookups"] == b.stats()["lookups"]
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("name", ["tp_p1", "nondyadic_p2_vec"])
+def test_octree_rejects_nondyadic_faces(vols, name):
+    gv = lv.Volume(vols[name])
+    with pytest.raises(lv.LrvolError) as ei:
+        gv.build_accel((4, 4, 4), split=lv.SPLIT_MIDPOINT)
+    assert ei.value.status == lv.ERR_UNSUPPORTED
+    with pytest.raises(lv.LrvolError) as ei:
+        gv.build_accel((4, 4, 4), split=7)
+    assert ei.value.status == lv.ERR_ARG
+    gv.build_accel((4, 4, 4))                  # the balanced rule handles any box partition
+    gv.close()
+
+
 def test_lookup_million_points_cfg1(vols, oracles):
     vol = vols["cfg1"]
     gv = lv.Volume(vol).build_accel((64, 64, 64))
