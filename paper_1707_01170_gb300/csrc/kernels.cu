@@ -36,6 +36,15 @@ __device__ void bernstein_of_bspline(const double *xi, int p, double a, double b
   int m = 0;
   for (int q = 1; q <= p; ++q)
     if (xi[q] <= a) m = q;
+  // the triangle's denominators depend on (r, k) only: one FP64 division
+  // each (FP64 division is a long instruction sequence on GB300), reused for
+  // all p + 1 blossoms
+  double inv[kMaxDeg + 1][kMaxDeg + 1];
+  for (int r = 1; r <= p; ++r) {
+    const int khi = m < r ? m : r;
+    const int klo = (m - p + r) > 0 ? (m - p + r) : 0;
+    for (int k = khi; k >= klo; --k) inv[r][k] = 1.0 / (xi[k + p + 1 - r] - xi[k]);
+  }
   for (int j = 0; j <= p; ++j) {
     double D[kMaxDeg + 1];
     D[0] = 1.0;
@@ -45,7 +54,7 @@ __device__ void bernstein_of_bspline(const double *xi, int p, double a, double b
       const int khi = m < r ? m : r;
       const int klo = (m - p + r) > 0 ? (m - p + r) : 0;
       for (int k = khi; k >= klo; --k) {
-        const double alpha = (t - xi[k]) / (xi[k + p + 1 - r] - xi[k]);
+        const double alpha = (t - xi[k]) * inv[r][k];
         const double prev = k > 0 ? D[k - 1] : 0.0;
         D[k] = (1.0 - alpha) * prev + alpha * D[k];
       }
