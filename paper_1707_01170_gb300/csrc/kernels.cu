@@ -63,9 +63,11 @@ __device__ void bernstein_of_bspline(const double *xi, int p, double a, double b
   }
 }
 
-__device__ __forceinline__ double binomial(int n, int k) {
-  double b = 1.0;
-  for (int i = 1; i <= k; ++i) b = b * (double)(n - k + i) / (double)i;
+// C(n, k) in integer arithmetic (each partial product is itself a binomial,
+// so every division is exact)
+__device__ __forceinline__ int binomial(int n, int k) {
+  int b = 1;
+  for (int i = 1; i <= k; ++i) b = b * (n - k + i) / i;
   return b;
 }
 
@@ -175,9 +177,10 @@ __global__ void __launch_bounds__(32 * kBezWarps) k_pack(const double *__restric
   }
   for (int q = lane; q < nb; q += 32) {
     const int ix = q % n0, iy = (q / n0) % n1, iz = q / (n0 * n1);
-    const double binom = binomial(p0, ix) * binomial(p1, iy) * binomial(p2, iz);
+    const double binom = (double)(binomial(p0, ix) * binomial(p1, iy) * binomial(p2, iz));
     for (int c = 0; c < nc; ++c) {
-      const double x = binom * (be[c * nb + q] - o[c]) / sc[c];
+      const double d = be[c * nb + q] - o[c];   // o = 0 and s = 1 for FP32 storage
+      const double x = storage == LRVOL_STORE_F32 ? binom * d : binom * d / sc[c];
       store_slot(out + e * ebytes, storage, render_slot(nc, n0, nb, iz * n1 + iy, ix, c), x);
       if (outc) store_slot(outc + e * ecbytes, storage, c * roundup8(nb) + q, x);
     }

@@ -336,39 +336,39 @@ class Volume:
         s = step if isinstance(step, Step) else make_step(step)
         if out is None:
             out = torch.zeros((c.height, c.width, 4), dtype=torch.float32, device="cuda")
-        assert out.is_cuda and out.dtype == torch.float32 and out.is_contiguous()
-        assert out.numel() == c.height * c.width * 4
-        _check(load().lrvol_render(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), out.data_ptr(),
+        ptr = _dev(out, torch.float32, c.height * c.width * 4, "render out", exact=True)
+        _check(load().lrvol_render(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), ptr,
                                    _stream_ptr(stream)), "lrvol_render")
         return out
 
     def lookup(self, pts, out=None, stream=None):
         import torch
-        assert pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous() and pts.shape[-1] == 3
-        n = pts.numel() // 3
+        n = _points(pts)
         if out is None:
             out = torch.empty(n, dtype=torch.int32, device=pts.device)
-        _check(load().lrvol_lookup(self._h, pts.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)), "lrvol_lookup")
+        if out.element_size() != 4:
+            raise TypeError("lookup out: expected a 32-bit integer tensor")
+        _check(load().lrvol_lookup(self._h, pts.data_ptr(), n, _dev(out, None, n, "lookup out"), _stream_ptr(stream)),
+               "lrvol_lookup")
         return out
 
     def eval(self, pts, out=None, stream=None):
         import torch
-        assert pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous() and pts.shape[-1] == 3
-        n = pts.numel() // 3
+        n = _points(pts)
         if out is None:
             out = torch.empty((n, self.ncomp), dtype=torch.float32, device=pts.device)
-        _check(load().lrvol_eval(self._h, pts.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)), "lrvol_eval")
+        _check(load().lrvol_eval(self._h, pts.data_ptr(), n, _dev(out, torch.float32, n * self.ncomp, "eval out"),
+                                 _stream_ptr(stream)), "lrvol_eval")
         return out
 
     def eval_grad(self, pts, out=None, stream=None):
         """(n, 4) float32 CUDA tensor: value and gradient of a scalar volume."""
         import torch
-        assert pts.is_cuda and pts.dtype == torch.float32 and pts.is_contiguous() and pts.shape[-1] == 3
-        n = pts.numel() // 3
+        n = _points(pts)
         if out is None:
             out = torch.empty((n, 4), dtype=torch.float32, device=pts.device)
-        _check(load().lrvol_eval_grad(self._h, pts.data_ptr(), n, out.data_ptr(), _stream_ptr(stream)),
-               "lrvol_eval_grad")
+        _check(load().lrvol_eval_grad(self._h, pts.data_ptr(), n, _dev(out, torch.float32, 4 * n, "eval_grad out"),
+                                      _stream_ptr(stream)), "lrvol_eval_grad")
         return out
 
     def get_bezier(self) -> np.ndarray:
@@ -385,11 +385,25 @@ class Volume:
 
 # ---- learned step sizes ----------------------------------------------------
 
-def _dev(t, dtype=None):
-    assert t.is_cuda and t.is_contiguous(), "expected a contiguous CUDA tensor"
-    if dtype is not None:
-        assert t.dtype == dtype, f"expected {dtype}"
+def _dev(t, dtype=None, numel=None, what="tensor", exact=False):
+    """Device pointer of a contiguous CUDA tensor after checking it: a wrong
+    device, layout, dtype or size raises here, so no kernel is ever handed a
+    buffer smaller than what it reads or writes."""
+    if not getattr(t, "is_cuda", False) or not t.is_contiguous():
+        raise ValueError(f"{what}: expected a contiguous CUDA tensor")
+    if dtype is not None and t.dtype != dtype:
+        raise TypeError(f"{what}: expected {dtype}, got {t.dtype}")
+    if numel is not None and (t.numel() != numel if exact else t.numel() < numel):
+        raise ValueError(f"{what}: {t.numel()} elements, {'expected' if exact else 'need at least'} {int(numel)}")
     return t.data_ptr()
+
+
+def _points(pts):
+    import torch
+    _dev(pts, torch.float32, what="points")
+    if pts.numel() % 3 != 0 or (pts.dim() > 0 and pts.shape[-1] != 3):
+        raise ValueError("points: expected n x 3 float32")
+    return pts.numel() // 3
 
 
 def features(vol: "Volume", cam, tf, step, out=None, stream=None):
@@ -400,8 +414,9 @@ def features(vol: "Volume", cam, tf, step, out=None, stream=None):
     c = cam if isinstance(cam, Camera) else make_camera(cam)
     t = tf if isinstance(tf, TF) else make_tf(tf)
     s = step if isinstance(step, Step) else make_step(step)
-    _check(load().lrvol_features(vol.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), _dev(out),
-                                 _stream_ptr(stream)), "lrvol_features")
+    _check(load().lrvol_features(vol.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s),
+                                 _dev(out, torch.float32, vol.n_elem * MLP_IN, "features out"), _stream_ptr(stream)),
+           "lrvol_features")
     return out
 
 
@@ -410,7 +425,8 @@ def mlp_pack(params, out=None, stream=None):
     import torch
     if out is None:
         out = torch.empty(MLP_PACKED, dtype=torch.int16, device="cuda")
-    _check(load().lrvol_mlp_pack(_dev(params, torch.float32), _dev(out), _stream_ptr(stream)), "lrvol_mlp_pack")
+    _check(load().lrvol_mlp_pack(_dev(params, torch.float32, MLP_PARAMS, "params"),
+                                 _dev(out, torch.int16, MLP_PACKED, "packed out"), _stream_ptr(stream)), "lrvol_mlp_pack")
     return out
 
 
@@ -420,8 +436,9 @@ def mlp_infer(x, packed, ymax: float, out=None, stream=None):
     n = x.shape[0]
     if out is None:
         out = torch.empty(n, dtype=torch.float32, device="cuda")
-    _check(load().lrvol_mlp_infer(_dev(x, torch.float32), n, _dev(packed), float(ymax), _dev(out),
-                                  _stream_ptr(stream)), "lrvol_mlp_infer")
+    _check(load().lrvol_mlp_infer(_dev(x, torch.float32, n * MLP_IN, "features"), n,
+                                  _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymax),
+                                  _dev(out, torch.float32, n, "multipliers out"), _stream_ptr(stream)), "lrvol_mlp_infer")
     return out
 
 
@@ -437,8 +454,10 @@ def mlp_grad(x, target, params, scratch=None, stream=None):
     scratch = mlp_scratch(n) if scratch is None else scratch
     grad = torch.empty(MLP_PARAMS, dtype=torch.float32, device="cuda")
     loss = torch.empty(1, dtype=torch.float32, device="cuda")
-    _check(load().lrvol_mlp_grad(_dev(x, torch.float32), _dev(target, torch.float32), n, _dev(params, torch.float32),
-                                 _dev(grad), _dev(loss), _dev(scratch), _stream_ptr(stream)), "lrvol_mlp_grad")
+    _check(load().lrvol_mlp_grad(_dev(x, torch.float32, n * MLP_IN, "x"), _dev(target, torch.float32, n, "target"), n,
+                                 _dev(params, torch.float32, MLP_PARAMS, "params"), _dev(grad), _dev(loss),
+                                 _dev(scratch, torch.float32, load().lrvol_mlp_scratch_floats(n), "scratch"),
+                                 _stream_ptr(stream)), "lrvol_mlp_grad")
     return loss, grad
 
 
@@ -446,10 +465,12 @@ def mlp_train_step(x, target, params, m, v, t: int, lr: float, scratch, loss=Non
     """One Adam step of the FP32 network on a batch (all CUDA tensors, in place)."""
     import torch
     n = x.shape[0]
-    _check(load().lrvol_mlp_train_step(_dev(x, torch.float32), _dev(target, torch.float32), n,
-                                       _dev(params, torch.float32), _dev(m), _dev(v), int(t), float(lr),
-                                       None if loss is None else _dev(loss), _dev(scratch), _stream_ptr(stream)),
-           "lrvol_mlp_train_step")
+    _check(load().lrvol_mlp_train_step(_dev(x, torch.float32, n * MLP_IN, "x"), _dev(target, torch.float32, n, "target"),
+                                       n, _dev(params, torch.float32, MLP_PARAMS, "params"),
+                                       _dev(m, torch.float32, MLP_PARAMS, "m"), _dev(v, torch.float32, MLP_PARAMS, "v"),
+                                       int(t), float(lr), None if loss is None else _dev(loss, torch.float32, 1, "loss"),
+                                       _dev(scratch, torch.float32, load().lrvol_mlp_scratch_floats(n), "scratch"),
+                                       _stream_ptr(stream)), "lrvol_mlp_train_step")
 
 
 def labels(vol: "Volume", cam, tf, step, h_fine: float, tau: float, cand, label=None, stream=None):
@@ -462,7 +483,8 @@ def labels(vol: "Volume", cam, tf, step, h_fine: float, tau: float, cand, label=
     t = tf if isinstance(tf, TF) else make_tf(tf)
     s = step if isinstance(step, Step) else make_step(step)
     _check(load().lrvol_labels(vol.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), float(h_fine),
-                               float(tau), _dev(cand_t), len(cand_t), _dev(label), _stream_ptr(stream)),
+                               float(tau), _dev(cand_t), len(cand_t), _dev(label, torch.int32, vol.n_elem, "label"),
+                               _stream_ptr(stream)),
            "lrvol_labels")
     return label
 
@@ -519,7 +541,9 @@ class Server:
 
     def set_step_model(self, packed, ymax: float) -> None:
         self._model = packed
-        _check(load().lrvol_server_set_step_model(self._h, _dev(packed), float(ymax)), "lrvol_server_set_step_model")
+        import torch
+        _check(load().lrvol_server_set_step_model(self._h, _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymax)),
+               "lrvol_server_set_step_model")
 
     def set_priority_pixels(self, max_pixels: int) -> None:
         _check(load().lrvol_server_set_priority_pixels(self._h, int(max_pixels)), "lrvol_server_set_priority_pixels")
@@ -534,7 +558,10 @@ class Server:
         ticket = ctypes.c_int64()
         hp = None
         if host_out is not None:
-            assert (not host_out.is_cuda) and host_out.is_contiguous() and host_out.numel() == c.width * c.height * 4
+            import torch
+            if host_out.is_cuda or not host_out.is_contiguous() or host_out.dtype != torch.float32 or \
+                    host_out.numel() != c.width * c.height * 4:
+                raise ValueError("host_out: expected a contiguous float32 host tensor of height x width x 4")
             hp = host_out.data_ptr()
         _check(load().lrvol_server_submit(self._h, vol.handle, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), hp,
                                           ctypes.byref(ticket)), "lrvol_server_submit")
@@ -610,8 +637,12 @@ def streamlines(vol: "Volume", seeds, method: str, rule: str, h: float, t_end: f
         out = (torch.empty((n, max_samples, 4), dtype=torch.float64, device="cuda"),
                torch.empty(n, dtype=torch.int32, device="cuda"), torch.empty(n, dtype=torch.int32, device="cuda"))
     samples, count, status = out
-    _check(load().lrvol_streamlines(vol.handle, ctypes.byref(P), _dev(seeds, torch.float64), n, _dev(samples),
-                                    _dev(count), _dev(status), _stream_ptr(stream)), "lrvol_streamlines")
+    if samples.dim() == 3 and samples.shape[1] != max_samples:
+        raise ValueError(f"samples: {samples.shape[1]} samples per line, max_samples is {max_samples}")
+    _check(load().lrvol_streamlines(vol.handle, ctypes.byref(P), _dev(seeds, torch.float64, 3 * n, "seeds"), n,
+                                    _dev(samples, torch.float64, n * max_samples * 4, "samples"),
+                                    _dev(count, torch.int32, n, "count"), _dev(status, torch.int32, n, "status"),
+                                    _stream_ptr(stream)), "lrvol_streamlines")
     return samples, count, status
 
 
@@ -620,8 +651,12 @@ def streamline_error(ref, ref_count, app, app_count, stream=None):
     import torch
     n = ref.shape[0]
     sums = torch.empty(n, dtype=torch.float64, device="cuda")
-    _check(load().lrvol_streamline_error(_dev(ref, torch.float64), _dev(ref_count), ref.shape[1],
-                                         _dev(app, torch.float64), _dev(app_count), app.shape[1], n, _dev(sums),
+    if ref.dim() != 3 or app.dim() != 3 or app.shape[0] != n:
+        raise ValueError("ref and app: expected n x max x 4 float64 tensors with the same n")
+    _check(load().lrvol_streamline_error(_dev(ref, torch.float64, n * ref.shape[1] * 4, "ref"),
+                                         _dev(ref_count, torch.int32, n, "ref_count"), ref.shape[1],
+                                         _dev(app, torch.float64, n * app.shape[1] * 4, "app"),
+                                         _dev(app_count, torch.int32, n, "app_count"), app.shape[1], n, _dev(sums),
                                          _stream_ptr(stream)), "lrvol_streamline_error")
     return sums
 
@@ -637,8 +672,9 @@ def trim(cam, tris, out=None, stream=None):
     t = tris.reshape(-1, 9)
     if out is None:
         out = torch.empty((c.height, c.width, 2), dtype=torch.float32, device="cuda")
-    _check(load().lrvol_trim(ctypes.byref(c), _dev(t, torch.float32), t.shape[0], _dev(out, torch.float32),
-                             _stream_ptr(stream)), "lrvol_trim")
+    _check(load().lrvol_trim(ctypes.byref(c), _dev(t, torch.float32, what="triangles"), t.shape[0],
+                             _dev(out, torch.float32, c.height * c.width * 2, "trim out"), _stream_ptr(stream)),
+           "lrvol_trim")
     return out
 
 
@@ -653,7 +689,12 @@ def tubes(vol: "Volume", cam, samples, count, radius: float, cmap, vis=None, out
         vis = torch.empty((c.height, c.width), dtype=torch.int64, device="cuda")
     if out is None:
         out = torch.empty((c.height, c.width, 4), dtype=torch.float32, device="cuda")
-    _check(load().lrvol_tubes(vol.handle, ctypes.byref(c), _dev(samples, torch.float64), _dev(count), samples.shape[0],
-                              samples.shape[1], float(radius), ctypes.byref(t), _dev(vis), _dev(out, torch.float32),
-                              _stream_ptr(stream)), "lrvol_tubes")
+    if samples.dim() != 3:
+        raise ValueError("samples: expected n x max x 4 float64")
+    n, ms = samples.shape[0], samples.shape[1]
+    _check(load().lrvol_tubes(vol.handle, ctypes.byref(c), _dev(samples, torch.float64, n * ms * 4, "samples"),
+                              _dev(count, torch.int32, n, "count"), n, ms, float(radius), ctypes.byref(t),
+                              _dev(vis, torch.int64, c.height * c.width, "vis"),
+                              _dev(out, torch.float32, c.height * c.width * 4, "tubes out"), _stream_ptr(stream)),
+           "lrvol_tubes")
     return out
