@@ -346,6 +346,11 @@ int lrvol_trim(const lrvol_camera *cam, const float *tri_dev, int64_t n_tri, flo
  * One thread traces one line at a time; a grid that fits on the GPU at once
  * takes the seeds from a counter in the handle, so concurrent streamline
  * calls on one handle are not allowed (as for every call on a handle).
+ * With fewer seeds than the GPU holds warps, each warp traces fewer than 32
+ * lines (down to one), so a small rake is not slowed by warp-mates' element
+ * look-ups; the samples are the same whatever the number of seeds.  The
+ * call returns when its kernels are queued; samples, counts and statuses are
+ * valid once the stream reaches that point.
  * ------------------------------------------------------------------------- */
 enum {
   LRVOL_RK1 = 0,   /* explicit Euler */
