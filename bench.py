@@ -347,6 +347,7 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
 
 SL_RUNS = (("RK2", "heuristic", 1.0, 0.0), ("RK4", "heuristic", 1.0, 0.0), ("RKF5", "heuristic", 1.0, 0.0),
            ("RK4", "heuristic", 0.5, 0.0), ("RKF45", "adaptive", 0.0, 1e-6), ("BS", "adaptive", 0.0, 1e-6))
+SL_BLOCKS = (256, 256, 256)
 SL_STAGES = {"RK1": 1, "RK2": 2, "RK3": 3, "RK4": 4, "RK38": 4, "RKF5": 6, "HE": 2, "BS": 4, "RKF45": 6}
 
 
@@ -361,13 +362,17 @@ def streamline_leg(stream, n_seeds: int = 65536, n_err: int = 4096, t_end: float
     from paper_1707_01170_gb300 import lrvol as lv
     from paper_1707_01170_gb300.synth import volumes as V
     vol = V.load_config(3)
-    g = lv.Volume(vol).build_accel(BLOCKS, stream=stream).to_bezier(stream=stream)
+    # 256^3 blocks: the trees near the obstacle, where the lines take most of
+    # their steps, are at most 3 levels deep (6 at 64^3), and every element
+    # change on a line waits for its look-up
+    g = lv.Volume(vol).build_accel(SL_BLOCKS, stream=stream).to_bezier(stream=stream)
     seeds = torch.from_numpy(V.config3_seeds(n_seeds)).cuda()
     href = 2.0 ** -12
     nref = int(t_end / href) + 2
     ref = lv.streamlines(g, seeds[:n_err].contiguous(), "RKF5", "fixed", href, t_end, max_samples=nref, stream=stream)
     torch.cuda.synchronize()
     out = {"volume": "config 3 (388,016 elements, triquadratic 3-vector wind flow)", "seeds": n_seeds,
+           "forest": f"{SL_BLOCKS[0]}^3 blocks",
            "t_end": t_end, "reference": f"RKF5 fixed step 2^-12 on the first {n_err} seeds",
            "precision": "outer loop in float pairs (about 48 bits) and FP64 time, field evaluation in FP32",
            "runs": []}
