@@ -331,11 +331,12 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
             mult_fn()
             render_fn()
         torch.cuda.synchronize()
-        samples = gq.stats()["samples"]
+        lst = gq.stats()
+        samples, lookups = lst["samples"], lst["lookups"]
         ms_mult, ms_render = _timed_frames([mult_fn, render_fn], steps, flush, stream)
         res["by_resolution"][f"{w}x{h}"] = {
             "ms_per_frame": ms_mult + ms_render, "ms_multipliers": ms_mult, "ms_render": ms_render,
-            "samples_per_frame": samples, "rmse_vs_fine": rmse(out, fine),
+            "samples_per_frame": samples, "lookups_per_frame": lookups, "rmse_vs_fine": rmse(out, fine),
             "plain_f32_ms_per_frame": ms_plain, "plain_f32_samples_per_frame": samples_plain,
             "plain_f32_rmse_vs_fine": rmse(ref_img, fine), "speedup_vs_plain_f32": ms_plain / (ms_mult + ms_render)}
         del fine, out
