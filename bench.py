@@ -310,7 +310,7 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
            "model": {"train_s": train_s, "rows": rows, "loss": losses[-1][1], "tau": model.cfg.tau,
                      "margin": model.cfg.margin, "ymax": model.cfg.ymax, "steps": model.cfg.steps,
                      "recipe": ("loaded from " + model_path) if model_path else
-                     "16 seeded 320x180 cameras on each of configs 1 and 2"},
+                     "32 seeded 320x180 cameras on each of configs 1 and 2"},
            "by_resolution": {}}
     for (w, h) in ((WIDTH, HEIGHT), (3840, 2160)):
         ccam = lv.make_camera(V.config2_render(w, h, vol)[1])

@@ -163,7 +163,7 @@ def train(X, target, cfg: TrainConfig, log_every: int = 0):
     return StepModel(params.cpu().numpy(), cfg), losses
 
 
-def fit(volumes, step, cfg: TrainConfig | None = None, cams_per_volume: int = 16, width: int = 320,
+def fit(volumes, step, cfg: TrainConfig | None = None, cams_per_volume: int = 32, width: int = 320,
         height: int = 180, log_every: int = 500):
     """The training recipe: labels and features of `cams_per_volume` seeded
     cameras per (volume, transfer function) pair, then Adam.  Volumes must be
