@@ -390,9 +390,9 @@ int lrvol_streamlines(lrvol_t vol, const lrvol_streamline_params *params, const 
  * order).  The pixel then takes the colour map's RGB at the speed |f| of the
  * volume at the closest point on the winning segment's axis, times
  * I = max(0.4, |n . d|), n the capsule normal at the hit; alpha 1; pixels
- * without a hit are (0, 0, 0, 0).  A warp sets up 32 consecutive segments of
- * a line, one per lane, and tests the pixel rays of their conservative
- * screen boxes 32 at a time; hits merge by a 64-bit atomic minimum of
+ * without a hit are (0, 0, 0, 0).  A warp walks a line's segments 32 at a
+ * time, one per lane, and tests the pixel rays of their conservative screen
+ * boxes 32 at a time; hits merge by a 64-bit atomic minimum of
  * (t bits, segment index) in vis_dev (height x width uint64 scratch,
  * caller-owned), then one thread per pixel shades the winner into rgba_dev
  * (height x width x 4 floats).  Needs a 3-vector volume (build_accel,

@@ -2265,24 +2265,29 @@ __global__ void k_vis_init(unsigned long long *__restrict__ vis, int64_t n) {
   if (q < n) vis[q] = ~0ull;
 }
 
-// One warp takes 32 consecutive segment slots of one line (the whole warp
-// leaves at once when the line has no segment there): lane l bounds segment
-// l's capsule on the screen, then the warp walks the group's (segment, pixel)
-// pairs 32 at a time, as the trimming raster does.  `split` warps share a
-// group when few long segments could cover much of the image.
+__device__ __forceinline__ void tube_group(const TubeParams &tp, int64_t line, int k0, int nseg, int split, int part,
+                                           int lane);
+
+// One warp per line (times `split`) walks the line's segments in groups of
+// 32: lane l bounds segment l of the group on the screen, then the warp walks
+// the group's (segment, pixel) pairs 32 at a time, as the trimming raster
+// does.  `split` warps share a line, each taking a contiguous part of every
+// group's pairs, when few long segments could cover much of the image.
 __global__ void __launch_bounds__(128) k_tube_raster(const __grid_constant__ TubeParams tp, int split) {
-  const unsigned full_mask = 0xffffffffu;
   const int lane = threadIdx.x & 31;
   const int64_t wid = (int64_t)blockIdx.x * 4 + (threadIdx.x >> 5);
-  const int64_t group = wid / split;
-  const int part = (int)(wid - group * split);
-  const int per = tp.max_samples - 1;                  // segment slots per line
-  const int64_t gpl = (per + 31) / 32;                 // groups per line
-  const int64_t line = group / gpl;
+  const int64_t line = wid / split;
+  const int part = (int)(wid - line * split);
   if (line >= tp.n_lines) return;                      // whole warp
-  const int k0 = (int)(group - line * gpl) * 32;
   const int nseg = tp.count[line] - 1;
-  if (k0 >= nseg) return;                              // whole warp
+  for (int k0 = 0; k0 < nseg; k0 += 32) tube_group(tp, line, k0, nseg, split, part, lane);
+}
+
+// One group of 32 segment slots of a line (see k_tube_raster).
+__device__ __forceinline__ void tube_group(const TubeParams &tp, int64_t line, int k0, int nseg, int split, int part,
+                                           int lane) {
+  const unsigned full_mask = 0xffffffffu;
+  const int per = tp.max_samples - 1;                  // segment slots per line
   const RayConsts &K = tp.ray;
   float a[3] = {0.f, 0.f, 0.f}, b[3] = {0.f, 0.f, 0.f};
   int i0 = 0, j0 = 0, bw = 1, cnt = 0;
@@ -2417,12 +2422,12 @@ cudaError_t launch_tubes(const TubeParams &tp, int degree, int storage, cudaStre
   const int64_t nseg = tp.n_lines * (int64_t)(tp.max_samples - 1);
   k_vis_init<<<(unsigned)((npix + 255) / 256), 256, 0, s>>>(tp.vis, npix);
   if (nseg > 0) {
-    // warps per group of 32 segment slots: as for trimming, counted over the
-    // slots (most of them are empty when lines are short)
-    const int64_t groups = tp.n_lines * ((tp.max_samples - 1 + 31) / 32);
-    int64_t split = (2 * npix + groups * 512 - 1) / (groups * 512);
+    // warps per line: about 512 pairs per warp and group when the lines'
+    // first groups cover the image twice, 1 for many lines, at most 256
+    const int64_t lines = tp.n_lines;
+    int64_t split = (2 * npix + lines * 512 - 1) / (lines * 512);
     split = split < 1 ? 1 : (split > 256 ? 256 : split);
-    const int64_t warps = groups * split;
+    const int64_t warps = lines * split;
     k_tube_raster<<<(unsigned)((warps + 3) / 4), 128, 0, s>>>(tp, (int)split);
   }
   const unsigned blocks = (unsigned)((npix + 127) / 128);
