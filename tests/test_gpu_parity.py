@@ -137,6 +137,27 @@ def test_octree_render_identical_to_balanced_forest(vols):
     b.close()
 
 
+@pytest.mark.slow
+def test_octree_on_the_benchmark_volume():
+    """cfg2 (174,000 elements): octree-style trees in 4^3 blocks give the
+    brute-force element ids on sampled points (faces included), and a frame
+    identical to the balanced 64^3 forest's."""
+    vol = V.load_config(2)
+    gv = lv.Volume(vol).build_accel((4, 4, 4), split=lv.SPLIT_MIDPOINT)
+    X = _probe_points(vol, 6000, seed=77, blocks=(4, 4, 4))
+    got = gv.lookup(torch.from_numpy(X).cuda()).cpu().numpy().view(np.uint32)
+    want = Oracle(vol).lookup(X)
+    np.testing.assert_array_equal(got, want)
+    tf, _ = V.config2_render(vol=vol)
+    cam = V.orbit_camera(V.Stream(4243), 320, 180)
+    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
+    img = gv.to_bezier().render(cam, tf, step)
+    ref = lv.Volume(vol).build_accel((64, 64, 64)).to_bezier()
+    assert torch.equal(img, ref.render(cam, tf, step))
+    gv.close()
+    ref.close()
+
+
 @pytest.mark.parametrize("name", ["tp_p1", "nondyadic_p2_vec"])
 def test_octree_rejects_nondyadic_faces(vols, name):
     gv = lv.Volume(vols[name])
