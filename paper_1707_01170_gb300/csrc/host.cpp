@@ -34,14 +34,23 @@ namespace {
 
 template <class T>
 int dev_alloc(lrvol_s *v, T **p, size_t count, const char *what) {
-  if (*p) {
+  if (*p) {   // a rebuild replaces the buffer
+    auto it = v->alloc_bytes.find(*p);
+    if (it != v->alloc_bytes.end()) {
+      v->bytes_device -= it->second;
+      v->alloc_bytes.erase(it);
+    }
     cudaFree(*p);
     *p = nullptr;
   }
   if (count == 0) count = 1;
   cudaError_t e = cudaMalloc((void **)p, count * sizeof(T));
-  if (e != cudaSuccess) return cuda_fail(e, what);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    return cuda_fail(e, what);
+  }
   v->bytes_device += (int64_t)(count * sizeof(T));
+  v->alloc_bytes[*p] = (int64_t)(count * sizeof(T));
   return LRVOL_OK;
 }
 
@@ -561,6 +570,9 @@ int lrvol_build_accel_split(lrvol_t v, const int32_t blocks[3], int32_t split, v
   }
   cudaStream_t st = (cudaStream_t)stream;
   int rc;
+  // from here the previous forest is replaced: until the new one is complete
+  // the handle has none (a failed host build above left the previous one)
+  v->have_accel = false;
   if ((rc = dev_alloc(v, &v->d_head, nblk, "alloc forest head")) ||
       (rc = dev_alloc(v, &v->d_nodes, fb.nodes.size(), "alloc forest nodes")))
     return rc;
@@ -589,6 +601,7 @@ int lrvol_to_bezier(lrvol_t v, int32_t storage, void *stream) {
   if (rc) return rc;
   cudaStream_t st = (cudaStream_t)stream;
   const int n0 = v->p[0] + 1, n1 = v->p[1] + 1, n2 = v->p[2] + 1, nb = n0 * n1 * n2;
+  v->have_bezier = false;   // the blocks are replaced: none until the new ones are complete
   v->storage = storage;
   v->elem_bytes = elem_bytes(storage, render_slots(v->nc, n0, n1, n2));
   v->elemc_bytes = v->nc == 3 ? elem_bytes(storage, 3 * roundup8(nb)) : 0;

@@ -5,6 +5,7 @@
 
 #include <cstdint>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "lrvol.h"
@@ -162,7 +163,8 @@ struct lrvol_s {
   // scratch
   unsigned long long *d_counters = nullptr;
   uint32_t *d_status = nullptr;
-  int64_t bytes_device = 0;
+  int64_t bytes_device = 0;                                 // sum of the live allocations below
+  std::unordered_map<const void *, int64_t> alloc_bytes;    // size of each live device allocation
 };
 
 namespace lrvol {

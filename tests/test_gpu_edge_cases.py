@@ -101,3 +101,19 @@ def test_binding_refuses_short_output_buffers(vec):
         lv.streamlines(vec, seeds, "RK4", "heuristic", 1.0, 1.0, max_samples=8, out=short)
     with pytest.raises(TypeError):
         lv.trim(cam, torch.zeros((1, 9), dtype=torch.float64, device="cuda"))
+
+
+def test_rebuilds_keep_the_device_accounting_and_a_failed_rebuild_keeps_the_forest():
+    vol = V.tensor_product((1, 1, 1), (5, 3, 4), seed=2)          # faces at thirds and fifths: not dyadic
+    gv = lv.Volume(vol).build_accel((4, 4, 4)).to_bezier()
+    bytes0 = gv.stats()["bytes_device"]
+    gv.build_accel((4, 4, 4)).to_bezier()
+    gv.build_accel((4, 4, 4)).to_bezier(lv.STORE_F32)
+    assert gv.stats()["bytes_device"] == bytes0
+    pts = torch.rand((2000, 3), generator=torch.Generator().manual_seed(5)).float().cuda()
+    before = gv.lookup(pts).clone()
+    with pytest.raises(lv.LrvolError) as ei:                       # the host build fails before any buffer is touched
+        gv.build_accel((4, 4, 4), split=lv.SPLIT_MIDPOINT)
+    assert ei.value.status == lv.ERR_UNSUPPORTED
+    assert torch.equal(gv.lookup(pts), before)
+    gv.close()
