@@ -191,20 +191,21 @@ __global__ void k_elem_records(const double *__restrict__ box, int64_t n_elem, i
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= n_elem) return;
   const double *b = box + 6 * e;
-  float lo[3], hi[3], dlo[3], iw[3];
+  float lo[3], hi[3], off[3], iw[3];
   double m = b[3] - b[0];
   if (b[4] - b[1] < m) m = b[4] - b[1];
   if (b[5] - b[2] < m) m = b[5] - b[2];
   for (int a = 0; a < 3; ++a) {
     lo[a] = __double2float_ru(b[a]);
     hi[a] = b[3 + a] == 1.0 ? __int_as_float(0x7f800000) : __double2float_ru(b[3 + a]);
-    dlo[a] = (float)((double)lo[a] - b[a]);
-    iw[a] = (float)(1.0 / (b[3 + a] - b[a]));
+    const double inv = 1.0 / (b[3 + a] - b[a]);
+    off[a] = (float)(((double)lo[a] - b[a]) * inv);   // (lo_RU - lo) / (hi - lo), in FP64
+    iw[a] = (float)inv;
   }
   ElemRec r;
   r.a = make_float4(lo[0], lo[1], lo[2], __double2float_rn(ldexp(m, -d)));
   r.b = make_float4(hi[0], hi[1], hi[2], 0.f);
-  r.c = make_float4(dlo[0], dlo[1], dlo[2], 0.f);
+  r.c = make_float4(off[0], off[1], off[2], 0.f);
   r.d = make_float4(iw[0], iw[1], iw[2], 0.f);
   out[e] = r;
 }
@@ -311,7 +312,11 @@ __device__ __forceinline__ float contract(const float *c, const float *bx, const
   return f;
 }
 
-__device__ __forceinline__ float local_u(float p, float lo, float dlo, float iw) { return ((p - lo) + dlo) * iw; }
+// u = (p - lo) / (hi - lo) as (p - lo_RU) * iw + (lo_RU - lo) * iw: one fused rounding after
+// the subtraction, which is exact when p is near lo_RU (the offset term is tiny).
+__device__ __forceinline__ float local_u(float p, float lo_ru, float off, float iw) {
+  return __fmaf_rn(__fsub_rn(p, lo_ru), iw, off);
+}
 
 // Generic-degree evaluation for the point kernel (any p0,p1,p2 <= 4).
 __device__ float eval_generic(const float *c, const int *deg, float ux, float uy, float uz) {

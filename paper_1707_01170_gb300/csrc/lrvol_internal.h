@@ -34,9 +34,9 @@ constexpr int kMaxImageSide = 32768;  // largest width or height a render accept
 // Element record, 4 x float4 = 64 bytes:
 //   a = {lo_ru.x, lo_ru.y, lo_ru.z, ds}   lower corner rounded up to FP32 (membership), Eq. 4 step
 //   b = {hi_ru.x, hi_ru.y, hi_ru.z, 0}    upper corner rounded up (+inf where hi = 1)
-//   c = {dlo.x, dlo.y, dlo.z, 0}          (float)(lo_ru - lo) >= 0, for accurate local coordinates
+//   c = {off.x, off.y, off.z, 0}          (float)((lo_ru - lo) / (hi - lo)) >= 0, from FP64
 //   d = {iw.x, iw.y, iw.z, 0}             (float)(1 / (hi - lo))
-// Local coordinate u = ((p - lo_ru) + dlo) * iw.
+// Local coordinate u = fma(p - lo_ru, iw, off).
 struct ElemRec {
   float4 a, b, c, d;
 };
