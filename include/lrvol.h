@@ -225,7 +225,7 @@ int lrvol_render_noalloc(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *t
 #define LRVOL_MLP_IN 16
 #define LRVOL_MLP_HIDDEN 64
 #define LRVOL_MLP_PARAMS 9473
-#define LRVOL_MLP_PACKED 10120 /* uint16 entries: BF16 weight fragments, then FP32 biases */
+#define LRVOL_MLP_PACKED 10120 /* uint16 entries: BF16 tensor-core operands, BF16 w4, FP32 biases */
 
 /* Features of every element for a camera and transfer function, n_elem x 16
  * floats into feat_dev (device).  With w the element's sides, [cmin, cmax] the
@@ -246,17 +246,30 @@ int lrvol_render_noalloc(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *t
 int lrvol_features(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
                    float *feat_dev, void *stream);
 
-/* Pack FP32 master parameters (device, LRVOL_MLP_PARAMS floats) into the BF16
- * tensor-core fragment order lrvol_mlp_infer reads (device, LRVOL_MLP_PACKED
- * uint16, caller-owned). */
+/* Pack FP32 master parameters (device, LRVOL_MLP_PARAMS floats) into the
+ * layout lrvol_mlp_infer reads (device, LRVOL_MLP_PACKED uint16,
+ * caller-owned): W1..W3 as BF16 tensor-core B operands in shared-memory
+ * order, w4 in BF16, the biases in FP32.  The layout is private to the
+ * library; treat the buffer as opaque. */
 int lrvol_mlp_pack(const float *params_dev, uint16_t *packed_dev, void *stream);
 
-/* Network forward on BF16 tensor cores (mma.sync m16n8k16, FP32 accumulate;
- * features and hidden activations rounded to BF16 as MMA operands) for n
- * feature rows (device, n x 16); writes out_dev[n] = 2^clamp(y, 0, ymax).
- * ymax in [0, 8]; packed_dev 16-byte aligned (it is read in 16-byte words). */
+/* Network forward for n feature rows (device, n x 16); writes out_dev[n] =
+ * 2^clamp(y, 0, ymax).  The three hidden layers run on the 5th-generation
+ * tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32 accumulators in
+ * tensor memory, 128 rows per tile); the features and hidden activations are
+ * rounded to BF16 as MMA operands, biases are added in FP32, and the 64 -> 1
+ * output layer is an FP32 dot product of the BF16 activations and BF16 w4.
+ * ymax in [0, 8]; packed_dev 16-byte aligned (it is read in 16-byte words).
+ * The kernel's waits for the tensor cores are bounded: if one runs out (not
+ * expected), the rows of the tiles it leaves get multiplier 1 (the Eq. 4
+ * step) and the library's network status records it for lrvol_mlp_check. */
 int lrvol_mlp_infer(const float *feat_dev, int64_t n, const uint16_t *packed_dev, float ymax, float *out_dev,
                     void *stream);
+
+/* Synchronises the device and reports the network status of every
+ * lrvol_mlp_infer since the last check: LRVOL_OK, or LRVOL_ERR_TIMEOUT if a
+ * tensor-core wait ran out (the status is then cleared). */
+int lrvol_mlp_check(void);
 
 /* FP32 training step of the network on a batch (device): loss = mean over
  * rows of (y - target)^2 / 2.  lrvol_mlp_grad writes the gradient

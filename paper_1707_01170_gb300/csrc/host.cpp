@@ -682,8 +682,21 @@ int lrvol_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float yma
   if (!(ymax >= 0.f && ymax <= 8.f)) return fail(LRVOL_ERR_ARG, "ymax must be in [0, 8]");
   if (n == 0) return LRVOL_OK;
   if (reinterpret_cast<uintptr_t>(packed) & 15) return fail(LRVOL_ERR_ARG, "packed weights must be 16-byte aligned");
-  CU(launch_mlp_infer(x, n, packed, ymax, out, (cudaStream_t)stream), "mlp infer kernel");
+  uint32_t *status = mlp_status_word();
+  if (!status) return fail(LRVOL_ERR_CUDA, "network status word unavailable");
+  CU(launch_mlp_infer(x, n, packed, ymax, out, status, (cudaStream_t)stream), "mlp infer kernel");
   return LRVOL_OK;
+}
+
+int lrvol_mlp_check(void) {
+  uint32_t *status = mlp_status_word();
+  if (!status) return fail(LRVOL_ERR_CUDA, "network status word unavailable");
+  uint32_t h = 0;
+  CU(cudaDeviceSynchronize(), "synchronise before the network status");
+  CU(cudaMemcpy(&h, status, sizeof h, cudaMemcpyDeviceToHost), "read the network status");
+  if (h == 0) return LRVOL_OK;
+  CU(cudaMemset(status, 0, sizeof h), "clear the network status");
+  return fail(LRVOL_ERR_TIMEOUT, "a tensor-core wait of lrvol_mlp_infer ran out; its rows got multiplier 1");
 }
 
 // activations and their gradients (n x (6*64 + 2)), then one gradient vector

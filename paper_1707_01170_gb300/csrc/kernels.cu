@@ -1239,39 +1239,33 @@ __global__ void k_features(const __grid_constant__ FeatureParams fp, float *__re
   o[15] = log2f(1.f + 255.f * (xhi - xlo));
 }
 
-// ---- BF16 weight fragments for mma.sync.m16n8k16 (B operand, "col") ----
-// Entry (ks, nt, lane, j): k = 16 ks + 2 t + (j & 1) + 8 (j >> 1), n = 8 nt + g,
-// with g = lane / 4, t = lane % 4.
+// ---- the step network on the 5th-generation tensor cores (tcgen05) ----
+// Pack: W1, W2, W3 into the canonical K-major layout of tc_off (B[n][k] =
+// W[k][n]), w4 as BF16, biases as FP32.
 __global__ void k_mlp_pack(const float *__restrict__ p, uint16_t *__restrict__ out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= kPacked) return;
-  float w = 0.f;
-  bool weight = false;
-  int N = 0, base = 0, woff = 0;
-  if (q < kPkL2) { N = kHid; base = kPkL1; woff = kOffW1; weight = true; }
-  else if (q < kPkL3) { N = kHid; base = kPkL2; woff = kOffW2; weight = true; }
-  else if (q < kPkL4) { N = kHid; base = kPkL3; woff = kOffW3; weight = true; }
-  else if (q < kPkBias) { N = 8; base = kPkL4; woff = kOffW4; weight = true; }
-  if (weight) {
-    const int r = q - base;
-    const int j = r & 3, lane = (r >> 2) & 31, tile = r >> 7;
-    const int ntn = N / 8, nt = tile % ntn, ks = tile / ntn;
-    const int g = lane >> 2, t = lane & 3;
-    const int k = 16 * ks + 2 * t + (j & 1) + 8 * (j >> 1), n = 8 * nt + g;
-    if (N == 8) w = n == 0 ? p[woff + k] : 0.f;
-    else w = p[woff + k * N + n];
-    out[q] = __bfloat16_as_ushort(__float2bfloat16_rn(w));
+  if (q < kTcW4) {
+    const int K = q < kTcW2 ? kIn : kHid;
+    const int base = q < kTcW2 ? kTcW1 : (q < kTcW3 ? kTcW2 : kTcW3);
+    const int woff = q < kTcW2 ? kOffW1 : (q < kTcW3 ? kOffW2 : kOffW3);
+    const int byte = 2 * (q - base), grp = byte / (K * 16), rem = byte % (K * 16);
+    const int n = grp * 8 + (rem % 128) / 16, k = (rem / 128) * 8 + (rem % 16) / 2;
+    out[q] = __bfloat16_as_ushort(__float2bfloat16_rn(p[woff + k * kHid + n]));
     return;
   }
-  // FP32 biases b1, b2, b3, b4 as pairs of uint16 (low half first)
-  const int r = q - kPkBias, f = r >> 1;
+  if (q < kTcBias) {
+    out[q] = __bfloat16_as_ushort(__float2bfloat16_rn(p[kOffW4 + (q - kTcW4)]));
+    return;
+  }
+  const int r = q - kTcBias, f = r >> 1;
   float bv = 0.f;
   if (f < kHid) bv = p[kOffB1 + f];
   else if (f < 2 * kHid) bv = p[kOffB2 + f - kHid];
   else if (f < 3 * kHid) bv = p[kOffB3 + f - 2 * kHid];
   else if (f == 3 * kHid) bv = p[kOffB4];
   const unsigned bits = __float_as_uint(bv);
-  out[q] = (r & 1) ? (uint16_t)(bits >> 16) : (uint16_t)(bits & 0xffffu);
+  out[q] = q >= kTcEnd ? (uint16_t)0 : ((r & 1) ? (uint16_t)(bits >> 16) : (uint16_t)(bits & 0xffffu));
 }
 
 __device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
@@ -1279,74 +1273,209 @@ __device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
          ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
 }
 
-__device__ __forceinline__ void mma_bf16(float *d, const unsigned *a, unsigned b0, unsigned b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+__device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor (tcgen05): start address, leading byte
+// offset (K-adjacent core matrices) and stride byte offset (8-row groups), all
+// in 16-byte units; descriptor version 1 at bit 46; no swizzling (bits 61-63 = 0).
+__device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr & 0x3FFFFu) >> 4) | ((uint64_t)(lbo >> 4) << 16) | ((uint64_t)(sbo >> 4) << 32) |
+         (1ull << 46);
 }
 
-// One warp evaluates 16 rows per tile; the C fragments of one layer are the A
-// fragments of the next (k-slice ks = n-tiles 2ks, 2ks+1), so activations stay
-// in registers.  Weights are staged in shared memory per CTA.
-__global__ void __launch_bounds__(128) k_mlp_infer(const float *__restrict__ x, int64_t n,
-                                                   const uint16_t *__restrict__ packed, float ymax,
-                                                   float *__restrict__ out) {
-  __shared__ __align__(16) uint16_t sw[kPacked];
-  for (int q = threadIdx.x; q < kPacked / 8; q += blockDim.x)
-    reinterpret_cast<uint4 *>(sw)[q] = reinterpret_cast<const uint4 *>(packed)[q];
+// Instruction descriptor of kind::f16: FP32 accumulator (bits 4-5 = 1), A and
+// B BF16 (bits 7-9 and 10-12 = 1), both K-major, N >> 3 at bits 17-22,
+// M >> 4 at bits 24-28.
+constexpr uint32_t kTcM = 128, kTcN = 64;
+constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((kTcN >> 3) << 17) | ((kTcM >> 4) << 24);
+constexpr int kTcSpin = 1 << 20;   // bound on mbarrier polls per wait
+
+__device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
+      :: "r"(tmem), "l"(a), "l"(b), "r"(kTcIdesc), "r"(acc) : "memory");
+}
+__device__ __forceinline__ void tc_commit(uint32_t mbar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" :: "r"(mbar) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
+
+// 16 consecutive FP32 columns of this thread's TMEM lane; the wait is in the
+// same statement, so the registers are complete when it returns.
+__device__ __forceinline__ void tc_ld16(uint32_t taddr, float *v) {
+  uint32_t r[16];
+  asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n\ttcgen05.wait::ld.sync.aligned;"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+               : "r"(taddr)
+               : "memory");
+#pragma unroll
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
+  return ok != 0;
+}
+
+// Synchronisation of the 128 threads of warpgroup g (named barrier 1 + g;
+// immediate ids, so only barriers 0-2 are reserved), and the AND of v over them.
+__device__ __forceinline__ void wg_sync(int g) {
+  if (g == 0) asm volatile("bar.sync 1, 128;" ::: "memory");
+  else asm volatile("bar.sync 2, 128;" ::: "memory");
+}
+__device__ __forceinline__ bool wg_sync_and(int g, bool v) {
+  uint32_t r;
+  if (g == 0)
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, 1, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)v) : "memory");
+  else
+    asm volatile("{\n\t.reg .pred p, q;\n\tsetp.ne.u32 q, %1, 0;\n\tbar.red.and.pred p, 2, 128, q;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+                 : "=r"(r) : "r"((uint32_t)v) : "memory");
+  return r != 0;
+}
+
+// Two BF16 values (round to nearest even) in one word, the first in the low half.
+__device__ __forceinline__ uint32_t bf16x2(float lo, float hi) {
+  const __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<const uint32_t *>(&v);
+}
+
+constexpr int kTcGroups = 2;                                   // warpgroups (row pipelines) per CTA
+constexpr int kTcSmemBytes = 2 * kTcW4 + kTcGroups * 2 * (int)kTcM * kHid;   // weights + operand tiles
+
+// A CTA holds the weights once in shared memory and runs two independent
+// pipelines, one per warpgroup, each taking tiles of 128 rows.  Per hidden
+// layer the warpgroup's first thread issues the MMAs (M = 128, N = 64, K = 16
+// per instruction) from the warpgroup's operand tile and the layer's weights
+// into its own 128 x 64 FP32 accumulator in tensor memory, and commits them
+// to the warpgroup's mbarrier; every warp then reads its 32 rows back
+// (tcgen05.ld), adds the bias, applies ReLU and writes the BF16 activations as
+// the next layer's operand tile.  The 64 -> 1 output layer runs on the CUDA
+// cores in FP32 on the BF16-rounded operands.  Waits are bounded: a tile
+// whose MMAs do not complete gets multiplier 1 (the Eq. 4 step) for its rows
+// and for every later tile of that pipeline, and the status word records
+// kStatusTimeout.
+__global__ void __launch_bounds__(128 * kTcGroups, 4) k_mlp_infer(const float *__restrict__ x, int64_t n,
+                                                               const uint16_t *__restrict__ packed, float ymax,
+                                                               float *__restrict__ out, uint32_t *__restrict__ status) {
+  extern __shared__ __align__(1024) unsigned char tc_smem[];
+  uint16_t *sw = reinterpret_cast<uint16_t *>(tc_smem);                         // W1, W2, W3 (18,432 B)
+  __shared__ float sb[3 * kHid + 1], sw4[kHid];
+  __shared__ __align__(8) unsigned long long mbar[kTcGroups];
+  __shared__ uint32_t tmem_slot;
+  const int tid = threadIdx.x, warp = tid >> 5, g = tid >> 7, gt = tid & 127;
+  for (int q = tid; q < kTcW4 / 8; q += blockDim.x)
+    reinterpret_cast<uint4 *>(sw)[q] = __ldg(reinterpret_cast<const uint4 *>(packed) + q);
+  for (int q = tid; q < kHid; q += blockDim.x) sw4[q] = __bfloat162float(__ushort_as_bfloat16(packed[kTcW4 + q]));
+  for (int q = tid; q < 3 * kHid + 1; q += blockDim.x)
+    sb[q] = __uint_as_float((unsigned)packed[kTcBias + 2 * q] | ((unsigned)packed[kTcBias + 2 * q + 1] << 16));
+  if (tid < kTcGroups) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" :: "r"(smem_u32(&mbar[tid])) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" :: "r"(smem_u32(&tmem_slot)),
+                 "r"(kTcN * kTcGroups) : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  tc_fence_before();
   __syncthreads();
-  const float *bias = reinterpret_cast<const float *>(sw + kPkBias);
-  const unsigned *wfrag = reinterpret_cast<const unsigned *>(sw);   // 2 registers per lane per fragment
-  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
-  const int64_t tiles = (n + 15) / 16;
-  const int64_t warp_id = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int64_t n_warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
-  for (int64_t tile = warp_id; tile < tiles; tile += n_warps) {
-    const int64_t r0 = tile * 16 + g, r1 = r0 + 8;
-    auto xin = [&](int64_t r, int c) { return r < n ? __ldg(x + r * kIn + c) : 0.f; };
-    unsigned A[4][4];
-    A[0][0] = pack_bf16x2(xin(r0, 2 * t), xin(r0, 2 * t + 1));
-    A[0][1] = pack_bf16x2(xin(r1, 2 * t), xin(r1, 2 * t + 1));
-    A[0][2] = pack_bf16x2(xin(r0, 2 * t + 8), xin(r0, 2 * t + 9));
-    A[0][3] = pack_bf16x2(xin(r1, 2 * t + 8), xin(r1, 2 * t + 9));
-    float C[8][4];
-    // three hidden layers
-    for (int layer = 0; layer < 3; ++layer) {
-      const int ksteps = layer == 0 ? 1 : 4;
-      const int pk = layer == 0 ? kPkL1 : (layer == 1 ? kPkL2 : kPkL3);
-      const float *bl = bias + layer * kHid;
+  tc_fence_after();
+  const uint32_t tmem = tmem_slot + kTcN * g;                               // this pipeline's accumulator
+  const uint32_t lane_addr = tmem + ((uint32_t)((warp & 3) * 32) << 16);    // this warp's 32 TMEM lanes
+  unsigned char *sa = tc_smem + 2 * kTcW4 + g * 2 * kTcM * kHid;            // this pipeline's operand tile
+  const uint32_t a_addr = smem_u32(sa), w_addr = smem_u32(sw), mb = smem_u32(&mbar[g]);
+  const bool vec = (reinterpret_cast<uintptr_t>(x) & 15) == 0;
+  uint32_t phase = 0;
+  bool ok = true;
+  const int64_t tiles = (n + kTcM - 1) / kTcM;
+  int64_t tile = (int64_t)blockIdx.x * kTcGroups + g;
+  for (; tile < tiles; tile += (int64_t)gridDim.x * kTcGroups) {
+    const int64_t row = tile * kTcM + gt;
+    {  // layer-1 operand: this thread's feature row in BF16 (K = 16)
+      float f[kIn];
+      if (row < n && vec) {
+        const float4 *xr = reinterpret_cast<const float4 *>(x + row * kIn);
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) {
-        const float b0 = bl[8 * nt + 2 * t], b1 = bl[8 * nt + 2 * t + 1];
-        C[nt][0] = b0; C[nt][1] = b1; C[nt][2] = b0; C[nt][3] = b1;
-      }
-      for (int ks = 0; ks < ksteps; ++ks)
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-          const unsigned *bf = wfrag + (pk >> 1) + ((ks * 8 + nt) * 32 + lane) * 2;
-          mma_bf16(C[nt], A[ks], bf[0], bf[1]);
+        for (int c = 0; c < kIn / 4; ++c) {
+          const float4 v = __ldg(xr + c);
+          f[4 * c] = v.x; f[4 * c + 1] = v.y; f[4 * c + 2] = v.z; f[4 * c + 3] = v.w;
         }
+      } else {
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        A[ks][0] = pack_bf16x2(fmaxf(C[2 * ks][0], 0.f), fmaxf(C[2 * ks][1], 0.f));
-        A[ks][1] = pack_bf16x2(fmaxf(C[2 * ks][2], 0.f), fmaxf(C[2 * ks][3], 0.f));
-        A[ks][2] = pack_bf16x2(fmaxf(C[2 * ks + 1][0], 0.f), fmaxf(C[2 * ks + 1][1], 0.f));
-        A[ks][3] = pack_bf16x2(fmaxf(C[2 * ks + 1][2], 0.f), fmaxf(C[2 * ks + 1][3], 0.f));
+        for (int c = 0; c < kIn; ++c) f[c] = row < n ? __ldg(x + row * kIn + c) : 0.f;
+      }
+      unsigned char *dst = sa + tc_off(gt, 0, kIn);
+      *reinterpret_cast<uint4 *>(dst) = make_uint4(bf16x2(f[0], f[1]), bf16x2(f[2], f[3]), bf16x2(f[4], f[5]), bf16x2(f[6], f[7]));
+      *reinterpret_cast<uint4 *>(dst + 128) =
+          make_uint4(bf16x2(f[8], f[9]), bf16x2(f[10], f[11]), bf16x2(f[12], f[13]), bf16x2(f[14], f[15]));
+    }
+    float y = sb[3 * kHid];
+    for (int layer = 0; layer < 3; ++layer) {
+      const int K = layer == 0 ? kIn : kHid;
+      fence_async_smem();   // the operand tile's generic-proxy stores, visible to the tensor core
+      tc_fence_before();
+      wg_sync(g);
+      if (gt == 0) {
+        tc_fence_after();
+        const uint32_t wl = w_addr + 2u * (layer == 0 ? kTcW1 : (layer == 1 ? kTcW2 : kTcW3));
+        for (int ks = 0; ks < K / 16; ++ks)
+          tc_mma(tmem, tc_desc(a_addr + 256u * ks, 128u, 16u * K), tc_desc(wl + 256u * ks, 128u, 16u * K), ks > 0);
+        tc_commit(mb);
+      }
+      bool done = false;
+      for (int it = 0; it < kTcSpin && !done; ++it) done = mbar_try_wait(mb, phase);
+      ok = wg_sync_and(g, done);
+      phase ^= 1u;
+      if (!ok) break;
+      tc_fence_after();
+      const float *bl = sb + layer * kHid;
+      unsigned char *dst = sa + tc_off(gt, 0, kHid);
+      float h[16];
+#pragma unroll
+      for (int c = 0; c < kHid / 8; ++c) {
+        if ((c & 1) == 0) tc_ld16(lane_addr + 8 * c, h);   // columns 8c .. 8c + 15
+        uint32_t w[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const int j = 8 * c + 2 * q, i = 8 * (c & 1) + 2 * q;
+          w[q] = bf16x2(fmaxf(h[i] + bl[j], 0.f), fmaxf(h[i + 1] + bl[j + 1], 0.f));
+        }
+        if (layer < 2) {
+          *reinterpret_cast<uint4 *>(dst + 128 * c) = make_uint4(w[0], w[1], w[2], w[3]);
+        } else {
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int j = 8 * c + 2 * q;
+            y = fmaf(__uint_as_float(w[q] << 16), sw4[j], y);
+            y = fmaf(__uint_as_float(w[q] & 0xffff0000u), sw4[j + 1], y);
+          }
+        }
       }
     }
-    // output layer (n padded to 8; column 0 is the output)
-    float D[4] = {t == 0 ? bias[3 * kHid] : 0.f, 0.f, t == 0 ? bias[3 * kHid] : 0.f, 0.f};
-#pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-      const unsigned *bf = wfrag + (kPkL4 >> 1) + (ks * 32 + lane) * 2;
-      mma_bf16(D, A[ks], bf[0], bf[1]);
-    }
-    if (t == 0) {
-      if (r0 < n) out[r0] = exp2f(fminf(fmaxf(D[0], 0.f), ymax));
-      if (r1 < n) out[r1] = exp2f(fminf(fmaxf(D[2], 0.f), ymax));
-    }
+    if (!ok) break;
+    if (row < n) out[row] = exp2f(fminf(fmaxf(y, 0.f), ymax));
+  }
+  if (!ok) {
+    if (gt == 0) set_status(status, kStatusTimeout);
+    for (; tile < tiles; tile += (int64_t)gridDim.x * kTcGroups)
+      if (tile * kTcM + gt < n) out[tile * kTcM + gt] = 1.f;
+    // one more bounded wait for the MMAs in flight before the accumulator is freed
+    bool done = false;
+    for (int it = 0; it < kTcSpin && !done; ++it) done = mbar_try_wait(mb, phase ^ 1u);
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) {
+    tc_fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(tmem_slot), "r"(kTcN * kTcGroups)
+                 : "memory");
   }
 }
 
@@ -1552,11 +1681,34 @@ cudaError_t launch_mlp_pack(const float *params, uint16_t *packed, cudaStream_t 
   return cudaGetLastError();
 }
 
+__device__ uint32_t g_mlp_status;
+
+uint32_t *mlp_status_word() {
+  void *p = nullptr;
+  return cudaGetSymbolAddress(&p, g_mlp_status) == cudaSuccess ? static_cast<uint32_t *>(p) : nullptr;
+}
+
 cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
-                             cudaStream_t s) {
-  const int64_t tiles = (n + 15) / 16;
-  const int64_t blocks = std::min<int64_t>((tiles + 3) / 4, 152 * 8);
-  k_mlp_infer<<<(unsigned)std::max<int64_t>(blocks, 1), 128, 0, s>>>(x, n, packed, ymax, out);
+                             uint32_t *status, cudaStream_t s) {
+  static int sms = 0;
+  if (sms == 0) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+  }
+  static bool smem_set = false;
+  if (!smem_set) {
+    const cudaError_t e = cudaFuncSetAttribute(k_mlp_infer, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcSmemBytes);
+    if (e != cudaSuccess) return e;
+    smem_set = true;
+  }
+  // Shared memory (about 52 KB per CTA) allows at most 4 CTAs per SM, so their
+  // tensor memory (128 columns each) never exceeds the SM's 512 columns.
+  const int64_t tiles = (n + kTcM - 1) / kTcM;
+  const int64_t blocks = std::min<int64_t>((tiles + kTcGroups - 1) / kTcGroups, 4 * (int64_t)sms);
+  k_mlp_infer<<<(unsigned)std::max<int64_t>(blocks, 1), 128 * kTcGroups, kTcSmemBytes, s>>>(x, n, packed, ymax, out,
+                                                                                           status);
   return cudaGetLastError();
 }
 

@@ -193,11 +193,24 @@ constexpr int kIn = 16, kHid = 64;
 constexpr int kOffW1 = 0, kOffB1 = kOffW1 + kIn * kHid, kOffW2 = kOffB1 + kHid, kOffB2 = kOffW2 + kHid * kHid,
               kOffW3 = kOffB2 + kHid, kOffB3 = kOffW3 + kHid * kHid, kOffW4 = kOffB3 + kHid, kOffB4 = kOffW4 + kHid,
               kParams = kOffB4 + 1;
-// packed BF16 fragments (uint16 offsets): [k-step][n-tile][lane][4]
-constexpr int kPkL1 = 0, kPkL2 = kPkL1 + 1 * 8 * 128, kPkL3 = kPkL2 + 4 * 8 * 128, kPkL4 = kPkL3 + 4 * 8 * 128,
-              kPkBias = kPkL4 + 4 * 1 * 128, kPacked = ((kPkBias + 2 * (3 * kHid + 1)) + 7) & ~7;
+// Packed weights (uint16 offsets).  W1, W2, W3 as BF16 tensor-core B operands
+// (N = 64 rows of K, K-major, in the canonical no-swizzle layout of 8-row x
+// 16-byte core matrices, see tc_off), then w4 as 64 BF16 values, then the FP32
+// biases b1, b2, b3, b4 as pairs of uint16 (low half first), zero padding to
+// the ABI size.
+constexpr int kTcW1 = 0, kTcW2 = kTcW1 + kHid * kIn, kTcW3 = kTcW2 + kHid * kHid, kTcW4 = kTcW3 + kHid * kHid,
+              kTcBias = kTcW4 + kHid, kTcEnd = kTcBias + 2 * (3 * kHid + 1), kPacked = 10120;
 static_assert(kParams == 9473, "parameter count");
-static_assert(kPacked == 10120, "packed size");
+static_assert(kTcEnd <= kPacked && (kTcBias * 2) % 4 == 0, "packed layout");
+
+// Byte offset of element (r, k) of a K-major BF16 operand with K columns in the
+// canonical no-swizzle layout: 8x8 core matrices (8 rows of 16 bytes, 128
+// contiguous bytes); core matrices adjacent in K are 128 B apart (the
+// descriptor's leading byte offset), 8-row groups K * 16 B apart (its stride
+// byte offset).
+__host__ __device__ constexpr int tc_off(int r, int k, int K) {
+  return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
+}
 
 struct FeatureParams {
   const double *box;
@@ -266,7 +279,11 @@ int prepare_features(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *
     if (_e != cudaSuccess) return ::lrvol::cuda_fail(_e, what); \
   } while (0)
 cudaError_t launch_mlp_pack(const float *params, uint16_t *packed, cudaStream_t s);
-cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out, cudaStream_t s);
+// status: device word that records LRVOL_ERR_TIMEOUT-class failures (kStatusTimeout) of the kernel's bounded waits
+cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
+                             uint32_t *status, cudaStream_t s);
+// the library's status word for lrvol_mlp_infer calls (device address)
+uint32_t *mlp_status_word();
 cudaError_t launch_mlp_grad(const float *x, const float *target, int64_t n, const float *params, float *grad,
                             float *loss, float *scratch, cudaStream_t s);
 cudaError_t launch_adam(float *params, const float *grad, float *m, float *v, int64_t t, float lr, cudaStream_t s);

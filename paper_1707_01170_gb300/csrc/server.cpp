@@ -182,7 +182,9 @@ int launch_request(lrvol_server_s *s, Request &r, int k) {
     int rc = prepare_features(r.vol, &r.cam, &r.tf, &step, &fp);
     if (rc) return rc;
     CU(launch_features(fp, feat, st), "server: features kernel");
-    CU(launch_mlp_infer(feat, r.vol->n_elem, s->packed, s->ymax, mult, st), "server: network kernel");
+    CU(launch_mlp_infer(feat, r.vol->n_elem, s->packed, s->ymax, mult, reinterpret_cast<uint32_t *>(sl.d_scratch + 64),
+                        st),
+       "server: network kernel");
     step.mult = mult;
   }
   RenderParams prm;

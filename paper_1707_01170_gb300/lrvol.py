@@ -25,7 +25,7 @@ NONE = 0xFFFFFFFF
 
 EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_build_accel_split", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
             "lrvol_eval", "lrvol_eval_grad", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
-            "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features", "lrvol_mlp_pack", "lrvol_mlp_infer",
+            "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features", "lrvol_mlp_pack", "lrvol_mlp_infer", "lrvol_mlp_check",
             "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels",
             "lrvol_arena_create", "lrvol_arena_alloc", "lrvol_arena_free", "lrvol_arena_used",
             "lrvol_arena_largest_free", "lrvol_arena_destroy", "lrvol_server_create", "lrvol_server_set_step_model",
@@ -148,6 +148,8 @@ def load(path: str = LIB_PATH):
         L.lrvol_mlp_pack.argtypes = [vp, vp, vp]
         L.lrvol_mlp_infer.restype = ctypes.c_int
         L.lrvol_mlp_infer.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
+        L.lrvol_mlp_check.restype = ctypes.c_int
+        L.lrvol_mlp_check.argtypes = []
         L.lrvol_mlp_scratch_floats.restype = i64
         L.lrvol_mlp_scratch_floats.argtypes = [i64]
         L.lrvol_mlp_grad.restype = ctypes.c_int
@@ -431,7 +433,7 @@ def mlp_pack(params, out=None, stream=None):
 
 
 def mlp_infer(x, packed, ymax: float, out=None, stream=None):
-    """Multipliers 2^clamp(y, 0, ymax) for feature rows x (n x 16) on BF16 tensor cores."""
+    """Multipliers 2^clamp(y, 0, ymax) for feature rows x (n x 16); hidden layers on the tcgen05 tensor cores."""
     import torch
     n = x.shape[0]
     if out is None:
@@ -440,6 +442,11 @@ def mlp_infer(x, packed, ymax: float, out=None, stream=None):
                                   _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymax),
                                   _dev(out, torch.float32, n, "multipliers out"), _stream_ptr(stream)), "lrvol_mlp_infer")
     return out
+
+
+def mlp_check() -> None:
+    """Synchronise and raise if a tensor-core wait of mlp_infer ran out since the last check."""
+    _check(load().lrvol_mlp_check(), "lrvol_mlp_check")
 
 
 def mlp_scratch(n: int):

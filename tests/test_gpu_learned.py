@@ -154,6 +154,7 @@ def test_mlp_infer_matches_bf16_forward(n):
     packed = lv.mlp_pack(torch.from_numpy(p.astype(np.float32)).cuda())
     got = lv.mlp_infer(torch.from_numpy(X).cuda(), packed, ymax).cpu().numpy().astype(np.float64)
     want = OL.multipliers(p, X.astype(np.float64), ymax, emulate_bf16=True)
+    lv.mlp_check()                                   # no tensor-core wait ran out
     d = np.abs(np.log2(got) - np.log2(want))
     assert d.max() <= 3e-2 and d.mean() <= 3e-3, (d.max(), d.mean())
     y = OL.forward(p, X.astype(np.float64), emulate_bf16=True)
