@@ -271,6 +271,13 @@ int lrvol_mlp_infer(const float *feat_dev, int64_t n, const uint16_t *packed_dev
  * tensor-core wait ran out (the status is then cleared). */
 int lrvol_mlp_check(void);
 
+/* Diagnostic of the timeout path: lrvol_mlp_infer with no MMAs issued, so
+ * every tile's bounded wait runs out (after at most 0.1 s per wait) and
+ * out_dev[0..n) becomes 1; lrvol_mlp_check then reports LRVOL_ERR_TIMEOUT.
+ * n in 1 .. 2^20. */
+int lrvol_mlp_infer_timeout_test(const float *feat_dev, int64_t n, const uint16_t *packed_dev, float ymax,
+                                 float *out_dev, void *stream);
+
 /* FP32 training step of the network on a batch (device): loss = mean over
  * rows of (y - target)^2 / 2.  lrvol_mlp_grad writes the gradient
  * (LRVOL_MLP_PARAMS floats) and the loss (1 float); lrvol_mlp_train_step then

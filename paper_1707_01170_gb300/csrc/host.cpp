@@ -688,6 +688,16 @@ int lrvol_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float yma
   return LRVOL_OK;
 }
 
+int lrvol_mlp_infer_timeout_test(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
+                                 void *stream) {
+  if (n < 1 || n > ((int64_t)1 << 20) || !x || !packed || !out) return fail(LRVOL_ERR_ARG, "bad arguments");
+  if (reinterpret_cast<uintptr_t>(packed) & 15) return fail(LRVOL_ERR_ARG, "packed weights must be 16-byte aligned");
+  uint32_t *status = mlp_status_word();
+  if (!status) return fail(LRVOL_ERR_CUDA, "network status word unavailable");
+  CU(launch_mlp_infer(x, n, packed, ymax, out, status, (cudaStream_t)stream, true), "mlp infer kernel (timeout test)");
+  return LRVOL_OK;
+}
+
 int lrvol_mlp_check(void) {
   uint32_t *status = mlp_status_word();
   if (!status) return fail(LRVOL_ERR_CUDA, "network status word unavailable");

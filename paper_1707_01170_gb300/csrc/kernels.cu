@@ -1288,7 +1288,8 @@ __device__ __forceinline__ uint64_t tc_desc(uint32_t saddr, uint32_t lbo, uint32
 // M >> 4 at bits 24-28.
 constexpr uint32_t kTcM = 128, kTcN = 64;
 constexpr uint32_t kTcIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((kTcN >> 3) << 17) | ((kTcM >> 4) << 24);
-constexpr int kTcSpin = 1 << 20;   // bound on mbarrier polls per wait
+constexpr int kTcSpin = 1 << 20;                 // bound on mbarrier polls per wait ...
+constexpr uint64_t kTcWaitNs = 100000000ull;     // ... and on its duration (100 ms)
 
 __device__ __forceinline__ void tc_mma(uint32_t tmem, uint64_t a, uint64_t b, uint32_t acc) {
   asm volatile(
@@ -1321,6 +1322,22 @@ __device__ __forceinline__ bool mbar_try_wait(uint32_t mbar, uint32_t parity) {
       "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok) : "r"(mbar), "r"(parity) : "memory");
   return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// Wait for the mbarrier phase with the given parity; false after kTcSpin polls
+// or kTcWaitNs nanoseconds, whichever comes first.
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t parity) {
+  if (mbar_try_wait(mbar, parity)) return true;
+  const uint64_t t0 = global_ns();
+  for (int it = 0; it < kTcSpin; ++it) {
+    if (mbar_try_wait(mbar, parity)) return true;
+    if (global_ns() - t0 > kTcWaitNs) return false;
+  }
+  return false;
 }
 
 // Synchronisation of the 128 threads of warpgroup g (named barrier 1 + g;
@@ -1360,10 +1377,12 @@ constexpr int kTcSmemBytes = 2 * kTcW4 + kTcGroups * 2 * (int)kTcM * kHid;   // 
 // cores in FP32 on the BF16-rounded operands.  Waits are bounded: a tile
 // whose MMAs do not complete gets multiplier 1 (the Eq. 4 step) for its rows
 // and for every later tile of that pipeline, and the status word records
-// kStatusTimeout.
+// kStatusTimeout.  no_mma (a diagnostic of that path) issues no MMAs and no
+// commits, so every pipeline's first wait runs out.
 __global__ void __launch_bounds__(128 * kTcGroups, 4) k_mlp_infer(const float *__restrict__ x, int64_t n,
                                                                const uint16_t *__restrict__ packed, float ymax,
-                                                               float *__restrict__ out, uint32_t *__restrict__ status) {
+                                                               float *__restrict__ out, uint32_t *__restrict__ status,
+                                                               bool no_mma) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
   uint16_t *sw = reinterpret_cast<uint16_t *>(tc_smem);                         // W1, W2, W3 (18,432 B)
   __shared__ float sb[3 * kHid + 1], sw4[kHid];
@@ -1422,16 +1441,14 @@ __global__ void __launch_bounds__(128 * kTcGroups, 4) k_mlp_infer(const float *_
       fence_async_smem();   // the operand tile's generic-proxy stores, visible to the tensor core
       tc_fence_before();
       wg_sync(g);
-      if (gt == 0) {
+      if (gt == 0 && !no_mma) {
         tc_fence_after();
         const uint32_t wl = w_addr + 2u * (layer == 0 ? kTcW1 : (layer == 1 ? kTcW2 : kTcW3));
         for (int ks = 0; ks < K / 16; ++ks)
           tc_mma(tmem, tc_desc(a_addr + 256u * ks, 128u, 16u * K), tc_desc(wl + 256u * ks, 128u, 16u * K), ks > 0);
         tc_commit(mb);
       }
-      bool done = false;
-      for (int it = 0; it < kTcSpin && !done; ++it) done = mbar_try_wait(mb, phase);
-      ok = wg_sync_and(g, done);
+      ok = wg_sync_and(g, mbar_wait_bounded(mb, phase));
       phase ^= 1u;
       if (!ok) break;
       tc_fence_after();
@@ -1467,8 +1484,7 @@ __global__ void __launch_bounds__(128 * kTcGroups, 4) k_mlp_infer(const float *_
     for (; tile < tiles; tile += (int64_t)gridDim.x * kTcGroups)
       if (tile * kTcM + gt < n) out[tile * kTcM + gt] = 1.f;
     // one more bounded wait for the MMAs in flight before the accumulator is freed
-    bool done = false;
-    for (int it = 0; it < kTcSpin && !done; ++it) done = mbar_try_wait(mb, phase ^ 1u);
+    if (!no_mma) mbar_wait_bounded(mb, phase ^ 1u);
   }
   tc_fence_before();
   __syncthreads();
@@ -1689,7 +1705,7 @@ uint32_t *mlp_status_word() {
 }
 
 cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
-                             uint32_t *status, cudaStream_t s) {
+                             uint32_t *status, cudaStream_t s, bool no_mma) {
   static int sms = 0;
   if (sms == 0) {
     int dev = 0;
@@ -1708,7 +1724,7 @@ cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, 
   const int64_t tiles = (n + kTcM - 1) / kTcM;
   const int64_t blocks = std::min<int64_t>((tiles + kTcGroups - 1) / kTcGroups, 4 * (int64_t)sms);
   k_mlp_infer<<<(unsigned)std::max<int64_t>(blocks, 1), 128 * kTcGroups, kTcSmemBytes, s>>>(x, n, packed, ymax, out,
-                                                                                           status);
+                                                                                           status, no_mma);
   return cudaGetLastError();
 }
 

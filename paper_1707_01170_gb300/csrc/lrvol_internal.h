@@ -280,8 +280,9 @@ int prepare_features(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *
   } while (0)
 cudaError_t launch_mlp_pack(const float *params, uint16_t *packed, cudaStream_t s);
 // status: device word that records LRVOL_ERR_TIMEOUT-class failures (kStatusTimeout) of the kernel's bounded waits
+// no_mma: diagnostic of the timeout path (no MMAs issued, every wait runs out)
 cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
-                             uint32_t *status, cudaStream_t s);
+                             uint32_t *status, cudaStream_t s, bool no_mma = false);
 // the library's status word for lrvol_mlp_infer calls (device address)
 uint32_t *mlp_status_word();
 cudaError_t launch_mlp_grad(const float *x, const float *target, int64_t n, const float *params, float *grad,

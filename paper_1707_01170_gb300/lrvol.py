@@ -25,7 +25,7 @@ NONE = 0xFFFFFFFF
 
 EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_build_accel_split", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
             "lrvol_eval", "lrvol_eval_grad", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
-            "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features", "lrvol_mlp_pack", "lrvol_mlp_infer", "lrvol_mlp_check",
+            "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features", "lrvol_mlp_pack", "lrvol_mlp_infer", "lrvol_mlp_check", "lrvol_mlp_infer_timeout_test",
             "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels",
             "lrvol_arena_create", "lrvol_arena_alloc", "lrvol_arena_free", "lrvol_arena_used",
             "lrvol_arena_largest_free", "lrvol_arena_destroy", "lrvol_server_create", "lrvol_server_set_step_model",
@@ -150,6 +150,8 @@ def load(path: str = LIB_PATH):
         L.lrvol_mlp_infer.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
         L.lrvol_mlp_check.restype = ctypes.c_int
         L.lrvol_mlp_check.argtypes = []
+        L.lrvol_mlp_infer_timeout_test.restype = ctypes.c_int
+        L.lrvol_mlp_infer_timeout_test.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
         L.lrvol_mlp_scratch_floats.restype = i64
         L.lrvol_mlp_scratch_floats.argtypes = [i64]
         L.lrvol_mlp_grad.restype = ctypes.c_int
@@ -441,6 +443,19 @@ def mlp_infer(x, packed, ymax: float, out=None, stream=None):
     _check(load().lrvol_mlp_infer(_dev(x, torch.float32, n * MLP_IN, "features"), n,
                                   _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymax),
                                   _dev(out, torch.float32, n, "multipliers out"), _stream_ptr(stream)), "lrvol_mlp_infer")
+    return out
+
+
+def mlp_infer_timeout_test(x, packed, ymax: float, out=None, stream=None):
+    """Diagnostic: the network kernel with no MMAs issued, so its bounded waits run out."""
+    import torch
+    n = x.shape[0]
+    if out is None:
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+    _check(load().lrvol_mlp_infer_timeout_test(_dev(x, torch.float32, n * MLP_IN, "features"), n,
+                                               _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymax),
+                                               _dev(out, torch.float32, n, "multipliers out"), _stream_ptr(stream)),
+           "lrvol_mlp_infer_timeout_test")
     return out
 
 

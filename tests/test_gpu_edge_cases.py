@@ -117,3 +117,31 @@ def test_rebuilds_keep_the_device_accounting_and_a_failed_rebuild_keeps_the_fore
     assert ei.value.status == lv.ERR_UNSUPPORTED
     assert torch.equal(gv.lookup(pts), before)
     gv.close()
+
+
+def test_mlp_wait_timeout_is_reported_and_the_context_recovers():
+    """The network kernel's tensor-core waits are bounded.  With no MMAs
+    issued (the diagnostic entry point) every wait runs out: the rows get
+    multiplier 1 (the Eq. 4 step), lrvol_mlp_check reports LRVOL_ERR_TIMEOUT
+    once, and the next real inference on the same context is correct."""
+    import time
+    gen = torch.Generator().manual_seed(5)
+    p = (0.25 * (2 * torch.rand(lv.MLP_PARAMS, generator=gen) - 1)).cuda()
+    packed = lv.mlp_pack(p)
+    X = (2 * torch.rand((1000, lv.MLP_IN), generator=gen) - 0.5).cuda()
+    want = lv.mlp_infer(X, packed, 3.0)
+    lv.mlp_check()
+    t0 = time.perf_counter()
+    out = lv.mlp_infer_timeout_test(X, packed, 3.0)
+    torch.cuda.synchronize()
+    elapsed = time.perf_counter() - t0
+    assert elapsed < 5.0
+    assert torch.all(out == 1.0)
+    with pytest.raises(lv.LrvolError) as e:
+        lv.mlp_check()
+    assert e.value.status == lv.ERR_TIMEOUT
+    lv.mlp_check()                                  # the report clears the status
+    again = lv.mlp_infer(X, packed, 3.0)
+    lv.mlp_check()
+    assert torch.equal(again, want)
+    assert not torch.all(want == 1.0)
