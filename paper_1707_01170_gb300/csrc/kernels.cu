@@ -7,7 +7,15 @@
 //   k_lookup       Alg. 1 element look-up through the k-d forest.
 //   k_eval         look-up + Bezier block evaluation at points.
 //   k_render       Sec. 4: per-pixel ray casting with element reuse, Eq. 4
-//                  steps, transfer function and Alg. 2 compositing.
+//                  steps, transfer function and Alg. 2 compositing (and
+//                  gradient shading, Sec. 4.1).
+//   k_features, k_mlp_infer, k_labels, k_dense_*, k_adam
+//                  learned step multipliers (not in the paper; Eq. 4 stays the
+//                  base): per-element features, the network on the tcgen05
+//                  tensor cores, training labels and FP32 training.
+//   k_streamlines, k_streamline_error, k_tube_*
+//                  Sec. 5 streamlines (Eq. 4 steps), the Eq. 7 error, tubes.
+//   k_trim_raster  Sec. 4.1 trimming: per-pixel interval of a boundary mesh.
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
@@ -1266,11 +1274,6 @@ __global__ void k_mlp_pack(const float *__restrict__ p, uint16_t *__restrict__ o
   else if (f == 3 * kHid) bv = p[kOffB4];
   const unsigned bits = __float_as_uint(bv);
   out[q] = q >= kTcEnd ? (uint16_t)0 : ((r & 1) ? (uint16_t)(bits >> 16) : (uint16_t)(bits & 0xffffu));
-}
-
-__device__ __forceinline__ unsigned pack_bf16x2(float lo, float hi) {
-  return (unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(lo)) |
-         ((unsigned)__bfloat16_as_ushort(__float2bfloat16_rn(hi)) << 16);
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) { return (uint32_t)__cvta_generic_to_shared(p); }

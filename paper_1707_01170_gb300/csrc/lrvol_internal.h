@@ -211,6 +211,9 @@ static_assert(kTcEnd <= kPacked && (kTcBias * 2) % 4 == 0, "packed layout");
 __host__ __device__ constexpr int tc_off(int r, int k, int K) {
   return (r >> 3) * (K * 16) + (k >> 3) * 128 + (r & 7) * 16 + (k & 7) * 2;
 }
+static_assert(tc_off(1, 0, 64) == 16 && tc_off(0, 1, 64) == 2 && tc_off(0, 8, 64) == 128 && tc_off(8, 0, 64) == 1024 &&
+                  tc_off(127, 63, 64) == 128 * 64 * 2 - 2 && tc_off(127, 15, 16) == 128 * 16 * 2 - 2,
+              "canonical operand layout");
 
 struct FeatureParams {
   const double *box;
