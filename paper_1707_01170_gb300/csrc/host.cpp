@@ -691,6 +691,7 @@ int lrvol_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float yma
 int lrvol_mlp_infer_timeout_test(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
                                  void *stream) {
   if (n < 1 || n > ((int64_t)1 << 20) || !x || !packed || !out) return fail(LRVOL_ERR_ARG, "bad arguments");
+  if (!(ymax >= 0.f && ymax <= 8.f)) return fail(LRVOL_ERR_ARG, "ymax must be in [0, 8]");
   if (reinterpret_cast<uintptr_t>(packed) & 15) return fail(LRVOL_ERR_ARG, "packed weights must be 16-byte aligned");
   uint32_t *status = mlp_status_word();
   if (!status) return fail(LRVOL_ERR_CUDA, "network status word unavailable");
