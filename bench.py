@@ -227,6 +227,18 @@ def measured_hbm_gbs():
         return None
 
 
+def measured_bf16_tflops():
+    """Burst dense BF16 rate (a kernel timed alone), else the stated fallback."""
+    try:
+        return float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]), "measured (burst)"
+    except (OSError, ValueError, KeyError):
+        return 1900.0, "fallback"
+
+
+# tensor-core work of the step network per feature row: the three hidden layers
+NET_TENSOR_FLOP_PER_ROW = 2 * (16 * 64 + 64 * 64 + 64 * 64)
+
+
 def run_reference(args):
     ws, rank, local = _dist()
     if rank != 0:
@@ -276,8 +288,8 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
     """Learned step sizes with reduced-precision blocks against the plain FP32
     Eq. 4 renderer on the same frames (1920x1080 and 3840x2160): both images
     against the fine-step (1/2048) reference, and the learned frame timed
-    whole (features, BF16 network, render), L2 flushed between frames like
-    the main loop."""
+    whole (features, BF16 tcgen05 network, render, each in its own event
+    pair), L2 flushed between frames like the main loop."""
     import torch
     from paper_1707_01170_gb300 import learned as LS
     from paper_1707_01170_gb300 import lrvol as lv
@@ -325,22 +337,38 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
             ms_plain = _timed_frames([lambda: gv32.render(ccam, ctf, pstep, out=ref_img, stream=stream)],
                                      steps, flush, stream)[0]
             samples_plain = gv32.stats()["samples"]
-        mult_fn = lambda: model.multipliers(gq, ccam, ctf, step, feat=feat, out=mult, stream=stream)
+        feat_fn = lambda: lv.features(gq, ccam, ctf, step, out=feat, stream=stream)
+        net_fn = lambda: lv.mlp_infer(feat, model.packed, model.cfg.ymax, out=mult, stream=stream)
         render_fn = lambda: gq.render(ccam, ctf, lstep, out=out, stream=stream)
         for _ in range(3):
-            mult_fn()
+            feat_fn()
+            net_fn()
             render_fn()
         torch.cuda.synchronize()
+        lv.mlp_check()
         lst = gq.stats()
         samples, lookups = lst["samples"], lst["lookups"]
-        ms_mult, ms_render = _timed_frames([mult_fn, render_fn], steps, flush, stream)
+        ms_feat, ms_net, ms_render = _timed_frames([feat_fn, net_fn, render_fn], steps, flush, stream)
+        ms_mult = ms_feat + ms_net
         res["by_resolution"][f"{w}x{h}"] = {
-            "ms_per_frame": ms_mult + ms_render, "ms_multipliers": ms_mult, "ms_render": ms_render,
+            "ms_per_frame": ms_mult + ms_render, "ms_multipliers": ms_mult, "ms_features": ms_feat,
+            "ms_network": ms_net, "ms_render": ms_render,
             "samples_per_frame": samples, "lookups_per_frame": lookups, "rmse_vs_fine": rmse(out, fine),
             "plain_f32_ms_per_frame": ms_plain, "plain_f32_samples_per_frame": samples_plain,
             "plain_f32_rmse_vs_fine": rmse(ref_img, fine), "speedup_vs_plain_f32": ms_plain / (ms_mult + ms_render)}
         del fine, out
     res.update(res["by_resolution"][f"{WIDTH}x{HEIGHT}"])
+    peak, peak_src = measured_bf16_tflops()
+    achieved = NET_TENSOR_FLOP_PER_ROW * vol.n_elem / (res["ms_network"] * 1e-3) / 1e12
+    res["network"] = {
+        "kernel": "k_mlp_infer: tcgen05.mma kind::f16 (BF16 operands, FP32 accumulators in tensor memory), "
+                  "M 128, N 64, K 16 per MMA; two 128-row pipelines per CTA",
+        "rows": vol.n_elem, "us_per_frame": res["ms_network"] * 1e3,
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "flop_per_row": NET_TENSOR_FLOP_PER_ROW,
+                     "peak_source": peak_src + " dense BF16",
+                     "note": "a small contraction (K <= 64, N = 64): latency of the three dependent layers per "
+                             "tile bounds it, not the tensor pipe"}}
     gq.close()
     res["_model"] = model
     return res
