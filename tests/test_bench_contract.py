@@ -24,3 +24,44 @@ def test_reference_arm_prints_one_json_line():
     assert d["impl"] == "reference" and d["steps"] == 1 and d["warmup"] == 3 and d["value"] > 0
     assert d["cpu_baseline"]["kind"] == "oracle" and d["e2e"]["h2d_bytes_per_step"] == 0
     assert "workload" in d["config"]
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(mod)
+    return mod
+
+
+def test_traffic_record_is_used_only_for_the_captured_source(tmp_path, monkeypatch):
+    """The roofline's ncu traffic comes from the committed k_render summary
+    only while kernels.cu still has the hash that summary records."""
+    import hashlib
+    b = _bench_module()
+    (tmp_path / "profiles").mkdir()
+    src = tmp_path / "paper_1707_01170_gb300" / "csrc"
+    src.mkdir(parents=True)
+    (src / "kernels.cu").write_bytes(b"// kernel source A\n")
+    sha = hashlib.sha256(b"// kernel source A\n").hexdigest()[:16]
+    (tmp_path / "profiles" / "k_render_cfg2_1080p.md").write_text(
+        "# summary\n\n    kernels_cu_sha256_16: %s\n    traffic_bytes_per_launch: 123\n    l2_bytes_per_launch: 456\n" % sha)
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    assert b.profiled_counters() == {"traffic": 123, "l2": 456}
+    (src / "kernels.cu").write_bytes(b"// kernel source B\n")
+    assert b.profiled_counters() is None
+
+
+def test_committed_traffic_record_parses():
+    rec = _bench_module().profiled_counters()
+    assert rec is None or (rec["traffic"] > 0 and rec["l2"] > rec["traffic"])
+
+
+def test_network_roofline_inputs(tmp_path, monkeypatch):
+    b = _bench_module()
+    assert b.NET_TENSOR_FLOP_PER_ROW == 2 * (16 * 64 + 64 * 64 * 2)     # the three hidden layers, FMA = 2
+    peak, src = b.measured_bf16_tflops()
+    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
+        assert src.startswith("measured") and peak == json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    monkeypatch.setattr(b, "ROOT", str(tmp_path))
+    assert b.measured_bf16_tflops() == (1900.0, "fallback")
