@@ -162,6 +162,25 @@ def test_mlp_infer_matches_bf16_forward(n):
     assert inside.mean() > 0.5                       # the comparison is not all clamps
 
 
+def test_mlp_infer_unaligned_features_match_aligned():
+    """Feature rows at an address that is not 16-byte aligned take the
+    kernel's scalar-load path; the multipliers are the same as from an
+    aligned copy of the same rows (ragged last tile included)."""
+    n = 1000
+    p = _net(11)
+    X = (2 * Stream(12, 16 * n + 8).take(16 * n).reshape(n, 16) - 0.5).astype(np.float32)
+    packed = lv.mlp_pack(torch.from_numpy(p.astype(np.float32)).cuda())
+    aligned = torch.from_numpy(X).cuda()
+    buf = torch.zeros(16 * n + 1, dtype=torch.float32, device="cuda")
+    buf[1:] = aligned.reshape(-1)
+    shifted = buf[1:].view(n, 16)
+    assert shifted.data_ptr() % 16 != 0
+    want = lv.mlp_infer(aligned, packed, 8.0)
+    got = lv.mlp_infer(shifted, packed, 8.0)
+    lv.mlp_check()
+    assert torch.equal(got, want)
+
+
 def _separated_case(n, seed0):
     """Parameters and inputs whose FP64 pre-activations stay 2e-5 from 0
     (about 10 times the typical FP32 error of a 64-term sum here)."""
