@@ -144,3 +144,76 @@ def test_labels_weigh_errors_by_front_transmittance():
     lab = orc.labels(cam, _slab_tf(), V.StepParams(mode="heuristic", xi=1 / 256), 1 / 2048, 1e-3, cand)
     assert lab[1] == len(cand) - 1
     assert lab[2] < len(cand) - 1          # the ramp in front is judged at full weight
+
+
+# ----------------------------------------------------------------------------
+# the network forward against a hand-built network
+# ----------------------------------------------------------------------------
+
+def _hand_network():
+    """Sparse weights whose forward is known in closed form (W[in][out]):
+    h1_0 = relu(2 x0), h1_1 = relu(x1 + 0.5), h1_2 = relu(-1) = 0;
+    h2_0 = relu(h1_0 + 3 h1_1 - 0.25) (the 3 sits at W2[1][0], so a
+    transposed W2 feeds h2_1 instead); h3_5 = relu(0.5 h2_0 + 0.125);
+    y = 4 h3_5 + 0.375.  Every weight and bias is exact in BF16."""
+    d = {name: np.zeros(shape) for name, shape in OL.SIZES}
+    d["W1"][0, 0], d["W1"][1, 1], d["b1"][1], d["b1"][2] = 2.0, 1.0, 0.5, -1.0
+    d["W2"][0, 0], d["W2"][1, 0], d["b2"][0] = 1.0, 3.0, -0.25
+    d["W3"][0, 5], d["b3"][5] = 0.5, 0.125
+    d["W4"][5], d["b4"][0] = 4.0, 0.375
+    return OL.pack(d)
+
+
+def _hand_y(x0, x1):
+    relu = lambda v: max(v, 0.0)
+    h10, h11 = relu(2 * x0), relu(x1 + 0.5)
+    h20 = relu(h10 + 3 * h11 - 0.25)
+    return 4 * relu(0.5 * h20 + 0.125) + 0.375
+
+
+# inputs exact in BF16 whose intermediates stay exact in BF16 too
+_HAND_X = [(0.5, 0.25), (-0.75, 1.5), (0.0, -0.5), (1.25, -2.0), (-1.0, -1.0), (0.125, 0.0)]
+
+
+def _hand_pin_holds(forward) -> bool:
+    p = _hand_network()
+    X = np.zeros((len(_HAND_X), OL.IN))
+    X[:, 0], X[:, 1] = [a for a, _ in _HAND_X], [b for _, b in _HAND_X]
+    X[:, 7] = 5.0                                   # an input no weight reads
+    want = np.array([_hand_y(a, b) for a, b in _HAND_X])
+    return bool(np.array_equal(forward(p, X), want) and np.array_equal(forward(p, X, emulate_bf16=True), want))
+
+
+def test_forward_matches_hand_built_network():
+    assert _hand_pin_holds(OL.forward)
+    assert len({_hand_y(a, b) for a, b in _HAND_X}) >= 4           # the cases are not all alike
+
+
+def test_multipliers_clamp_the_exponent():
+    p = OL.pack({name: np.zeros(shape) for name, shape in OL.SIZES})
+    X = np.zeros((1, OL.IN))
+    for b4, ymax, want in ((-1.5, 3.0, 1.0), (1.5, 3.0, 2 ** 1.5), (5.0, 3.0, 8.0), (0.0, 0.0, 1.0)):
+        p[-1] = b4
+        np.testing.assert_allclose(OL.multipliers(p, X, ymax), [want], rtol=1e-15)
+
+
+def test_hand_pin_catches_planted_forward_mistakes():
+    """Mistakes planted in copies of the forward (on the CPU) trip the pin."""
+    def make(mistake):
+        def fwd(p, X, emulate_bf16=False):
+            w = OL.unpack(p)
+            r = OL.bf16 if emulate_bf16 else (lambda a: np.asarray(a, dtype=np.float64))
+            h = r(X)
+            for k in (1, 2, 3):
+                W = r(w[f"W{k}"])
+                if mistake == "transposed W2" and k == 2:
+                    W = W.T
+                z = h @ W + (0.0 if mistake == "no bias" and k == 1 else w[f"b{k}"])
+                h = r(z if mistake == "no relu" and k == 1 else np.maximum(z, 0.0))
+            b4 = 0.0 if mistake == "no output bias" else w["b4"][0]
+            return h @ (r(w["W4"]) if mistake != "W4 shifted" else np.roll(r(w["W4"]), 1)) + b4
+        return fwd
+
+    assert _hand_pin_holds(make(None))                                  # the copy itself is right
+    for mistake in ("transposed W2", "no relu", "no bias", "no output bias", "W4 shifted"):
+        assert not _hand_pin_holds(make(mistake)), mistake
