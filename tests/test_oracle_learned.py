@@ -42,6 +42,20 @@ def test_adam_first_step_closed_form():
     np.testing.assert_allclose(v, 0.001 * g * g)
 
 
+def test_adam_constant_gradient_every_step_closed_form():
+    """With a constant gradient the bias-corrected moments are exactly g and
+    g^2 at every step t, so each update is lr * g / (|g| + eps): a wrong or
+    missing bias correction shows from t = 2 on."""
+    g = np.array([0.3, -4.0, 1e-3])
+    p, m, v = np.array([1.0, -2.0, 0.5]), np.zeros(3), np.zeros(3)
+    for t in range(1, 8):
+        p1, m, v = OL.adam(p, g, m, v, t, 0.01)
+        np.testing.assert_allclose(p1 - p, -0.01 * g / (np.abs(g) + 1e-8), rtol=1e-9)
+        np.testing.assert_allclose(m, (1 - 0.9 ** t) * g, rtol=1e-12)
+        np.testing.assert_allclose(v, (1 - 0.999 ** t) * g * g, rtol=1e-12)
+        p = p1
+
+
 def test_bf16_rounding_known_values():
     x = np.array([1.0, 1 + 2 ** -8, 1 + 3 * 2 ** -9, 1 + 2 ** -7, -2.5, 3.140625, 1 + 2 ** -8 + 2 ** -20])
     want = np.array([1.0, 1.0, 1 + 2 ** -7, 1 + 2 ** -7, -2.5, 3.140625, 1 + 2 ** -7])
