@@ -65,3 +65,22 @@ def test_network_roofline_inputs(tmp_path, monkeypatch):
         assert src.startswith("measured") and peak == json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     assert b.measured_bf16_tflops() == (1900.0, "fallback")
+
+
+@pytest.mark.slow
+def test_reference_arm_under_torchrun_prints_once_from_rank_0():
+    """Launched like the multi-GPU runs (torchrun, two ranks, 127.0.0.1),
+    rank 0 alone prints the one JSON line and every rank exits 0."""
+    import socket
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    r = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                        "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.join(ROOT, "bench.py"),
+                        "--impl", "reference", "--gpus", "2", "--steps", "1", "--warmup", "3"],
+                       capture_output=True, text=True, timeout=600, cwd=ROOT)
+    assert r.returncode == 0, r.stderr[-2000:]
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip().startswith("{")]
+    assert len(lines) == 1, r.stdout[-2000:]
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["n_gpus"] == 2 and d["value"] > 0
