@@ -23,14 +23,15 @@ SHADE_NONE, SHADE_GRADIENT = 0, 1
 SPLIT_BALANCED, SPLIT_MIDPOINT = 0, 1
 NONE = 0xFFFFFFFF
 
-EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_build_accel_split", "lrvol_to_bezier", "lrvol_render", "lrvol_lookup",
-            "lrvol_eval", "lrvol_eval_grad", "lrvol_get_bezier", "lrvol_stats", "lrvol_status_string", "lrvol_last_error",
-            "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features", "lrvol_mlp_pack", "lrvol_mlp_infer", "lrvol_mlp_check", "lrvol_mlp_infer_timeout_test",
+EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_build_accel_split", "lrvol_to_bezier", "lrvol_render",
+            "lrvol_lookup", "lrvol_eval", "lrvol_eval_grad", "lrvol_get_bezier", "lrvol_stats",
+            "lrvol_status_string", "lrvol_last_error", "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features",
+            "lrvol_mlp_pack", "lrvol_mlp_infer", "lrvol_mlp_check", "lrvol_mlp_infer_timeout_test",
             "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels",
             "lrvol_arena_create", "lrvol_arena_alloc", "lrvol_arena_free", "lrvol_arena_used",
             "lrvol_arena_largest_free", "lrvol_arena_destroy", "lrvol_server_create", "lrvol_server_set_step_model",
-            "lrvol_server_set_priority_pixels", "lrvol_server_set_large_cap",
-            "lrvol_server_submit", "lrvol_server_progress", "lrvol_server_drain", "lrvol_server_poll", "lrvol_server_info",
+            "lrvol_server_set_priority_pixels", "lrvol_server_set_large_cap", "lrvol_server_submit",
+            "lrvol_server_progress", "lrvol_server_drain", "lrvol_server_poll", "lrvol_server_info",
             "lrvol_server_release", "lrvol_server_get_stats", "lrvol_server_clock", "lrvol_server_destroy",
             "lrvol_streamlines", "lrvol_streamline_error", "lrvol_trim", "lrvol_tubes"]
 REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3

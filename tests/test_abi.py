@@ -102,3 +102,35 @@ def test_struct_layouts_match_header(tmp_path):
         assert int(got[cname]) == ctypes.sizeof(cls), cname
         for f, _ in cls._fields_:
             assert int(got[f"{cname}.{f}"]) == getattr(cls, f).offset, (cname, f)
+
+
+def test_binding_constants_match_header(tmp_path):
+    """Every enum value and size constant the binding mirrors equals what a C
+    compiler makes of include/lrvol.h."""
+    names = {"OK": "LRVOL_OK", "ERR_ARG": "LRVOL_ERR_ARG", "ERR_OOM": "LRVOL_ERR_OOM", "ERR_CUDA": "LRVOL_ERR_CUDA",
+             "ERR_STATE": "LRVOL_ERR_STATE", "ERR_BOUNDS": "LRVOL_ERR_BOUNDS", "ERR_TIMEOUT": "LRVOL_ERR_TIMEOUT",
+             "ERR_UNSUPPORTED": "LRVOL_ERR_UNSUPPORTED", "ORTHO": "LRVOL_ORTHO", "PERSP": "LRVOL_PERSP",
+             "MLP_IN": "LRVOL_MLP_IN", "MLP_HIDDEN": "LRVOL_MLP_HIDDEN", "MLP_PARAMS": "LRVOL_MLP_PARAMS",
+             "MLP_PACKED": "LRVOL_MLP_PACKED"}
+    for group in ("STEP_FIXED STEP_HEURISTIC STEP_LEARNED", "FIELD_SCALAR FIELD_MAGNITUDE FIELD_COMPONENT",
+                  "STORE_F32 STORE_F16 STORE_BF16", "SHADE_NONE SHADE_GRADIENT", "SPLIT_BALANCED SPLIT_MIDPOINT",
+                  "REQ_QUEUED REQ_RUNNING REQ_DONE REQ_FAILED"):
+        names.update({n: "LRVOL_" + n for n in group.split()})
+    methods = {m: "LRVOL_" + m for m in lv.SL_METHODS}
+    rules = {r: "LRVOL_SL_" + r.upper() for r in lv.SL_RULES}
+    lines = ['#include <stdio.h>', '#include "lrvol.h"', "int main(void) {"]
+    for py, c in {**names, **methods, **rules}.items():
+        lines.append(f'  printf("{py} %ld\\n", (long)({c}));')
+    lines.append("  return 0; }")
+    src = tmp_path / "consts.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "consts"
+    import subprocess
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)])
+    got = dict(line.split() for line in subprocess.check_output([str(exe)]).decode().splitlines())
+    for py in names:
+        assert int(got[py]) == getattr(lv, py), py
+    for i, m in enumerate(lv.SL_METHODS):
+        assert int(got[m]) == i, m                   # the binding passes the list index as the method
+    for i, r in enumerate(lv.SL_RULES):
+        assert int(got[r]) == i, r
