@@ -45,7 +45,8 @@ def test_traffic_record_is_used_only_for_the_captured_source(tmp_path, monkeypat
     (src / "kernels.cu").write_bytes(b"// kernel source A\n")
     sha = hashlib.sha256(b"// kernel source A\n").hexdigest()[:16]
     (tmp_path / "profiles" / "k_render_cfg2_1080p.md").write_text(
-        "# summary\n\n    kernels_cu_sha256_16: %s\n    traffic_bytes_per_launch: 123\n    l2_bytes_per_launch: 456\n" % sha)
+        "# summary\n\n    kernels_cu_sha256_16: %s\n" % sha
+        + "    traffic_bytes_per_launch: 123\n    l2_bytes_per_launch: 456\n")
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     assert b.profiled_counters() == {"traffic": 123, "l2": 456}
     (src / "kernels.cu").write_bytes(b"// kernel source B\n")
@@ -61,8 +62,9 @@ def test_network_roofline_inputs(tmp_path, monkeypatch):
     b = _bench_module()
     assert b.NET_TENSOR_FLOP_PER_ROW == 2 * (16 * 64 + 64 * 64 * 2)     # the three hidden layers, FMA = 2
     peak, src = b.measured_bf16_tflops()
-    if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")):
-        assert src.startswith("measured") and peak == json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"]
+    peaks = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(peaks):
+        assert src.startswith("measured") and peak == json.load(open(peaks))["bf16_tflops"]
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     assert b.measured_bf16_tflops() == (1900.0, "fallback")
 
