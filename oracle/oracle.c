@@ -580,6 +580,9 @@ typedef struct {
   double *rgba; /* npix x 4 */
   int tid, nth;
   orc_stats stats;
+  int32_t max_trace; /* records kept per pixel (trace only) */
+  double *trace;     /* NULL, or npix x max_trace x 4: t, element id, value, segment */
+  int32_t *count;    /* NULL, or npix: samples composited */
 } render_job;
 
 static void *render_worker(void *arg) {
@@ -662,6 +665,13 @@ static void *render_worker(void *arg) {
         s = val[J->st->component];
       else
         s = val[0];
+      if (J->trace && k < J->max_trace) {
+        double *rec = J->trace + 4 * ((int64_t)q * J->max_trace + k);
+        rec[0] = (double)t;
+        rec[1] = (double)cur;
+        rec[2] = s;
+        rec[3] = seg;
+      }
       double src[4];
       tf_lookup(J->tf, s, src);
       /* Alg. 2 */
@@ -678,20 +688,21 @@ static void *render_worker(void *arg) {
     out[1] = C[1];
     out[2] = C[2];
     out[3] = A;
+    if (J->count) J->count[q] = (int32_t)k;
   }
   free(inc);
   return NULL;
 }
 
-/* Render npix pixels (pix = NULL: the whole width x height image, row major). */
-void orc_render(const orc_vol *v, const orc_camera *cam, const orc_tf *tf, const orc_step *st,
-                const int32_t *pix, int64_t npix, double *rgba, int nth, orc_stats *stats) {
+static void render_common(const orc_vol *v, const orc_camera *cam, const orc_tf *tf, const orc_step *st,
+                          const int32_t *pix, int64_t npix, double *rgba, int nth, orc_stats *stats,
+                          int32_t max_trace, double *trace, int32_t *count) {
   if (nth < 1) nth = 1;
   if (!pix) npix = (int64_t)cam->width * cam->height;
   pthread_t *th = (pthread_t *)malloc(sizeof(pthread_t) * nth);
   render_job *jobs = (render_job *)calloc(nth, sizeof(render_job));
   for (int t = 0; t < nth; ++t) {
-    render_job J = {v, cam, tf, st, pix, npix, rgba, t, nth, {0, 0, 0}};
+    render_job J = {v, cam, tf, st, pix, npix, rgba, t, nth, {0, 0, 0}, max_trace, trace, count};
     jobs[t] = J;
     pthread_create(&th[t], NULL, render_worker, &jobs[t]);
   }
@@ -705,6 +716,22 @@ void orc_render(const orc_vol *v, const orc_camera *cam, const orc_tf *tf, const
   if (stats) *stats = s;
   free(th);
   free(jobs);
+}
+
+/* Render npix pixels (pix = NULL: the whole width x height image, row major). */
+void orc_render(const orc_vol *v, const orc_camera *cam, const orc_tf *tf, const orc_step *st,
+                const int32_t *pix, int64_t npix, double *rgba, int nth, orc_stats *stats) {
+  render_common(v, cam, tf, st, pix, npix, rgba, nth, stats, 0, NULL, NULL);
+}
+
+/* The same march, also keeping each pixel's samples in order: for sample k <
+   max_trace of pixel q, trace[q][k] = (t_k, element id, value before the
+   transfer function, segment min(t_{k+1}, t_out) - t_k), and count[q] = the
+   samples composited (Sec. 4, Alg. 1, Eq. 4, Alg. 2). */
+void orc_render_trace(const orc_vol *v, const orc_camera *cam, const orc_tf *tf, const orc_step *st,
+                      const int32_t *pix, int64_t npix, int32_t max_trace, double *trace, int32_t *count,
+                      double *rgba, int nth, orc_stats *stats) {
+  render_common(v, cam, tf, st, pix, npix, rgba, nth, stats, max_trace, trace, count);
 }
 
 /* The FP32 ray of one pixel (for tests of the ray setup). */

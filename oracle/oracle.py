@@ -118,6 +118,8 @@ def _load():
         L.orc_heuristic_step.argtypes = [vp, ctypes.c_uint32]
         L.orc_render.argtypes = [vp, ctypes.POINTER(_Cam), ctypes.POINTER(_TF), ctypes.POINTER(_Step),
                                  vp, i64, vp, i32, ctypes.POINTER(_Stats)]
+        L.orc_render_trace.argtypes = [vp, ctypes.POINTER(_Cam), ctypes.POINTER(_TF), ctypes.POINTER(_Step),
+                                       vp, i64, i32, vp, vp, vp, i32, ctypes.POINTER(_Stats)]
         L.orc_labels.argtypes = [vp, ctypes.POINTER(_Cam), ctypes.POINTER(_TF), ctypes.POINTER(_Step),
                                  ctypes.c_double, ctypes.c_double, vp, i32, vp, i32]
         L.orc_streamlines.argtypes = [vp, ctypes.POINTER(_SLParams), vp, i64, vp, vp, vp, i32]
@@ -317,6 +319,17 @@ class Oracle:
     def render(self, cam, tf, step, pixels=None, threads: int | None = None):
         """RGBA (premultiplied) per pixel: (H, W, 4), or (n, 4) for a pixel list
         of (i, j) pairs.  Returns (rgba, stats dict)."""
+        return self._render(cam, tf, step, pixels, threads, 0)
+
+    def render_trace(self, cam, tf, step, pixels, max_samples: int, threads: int | None = None):
+        """The march of each listed pixel, sample by sample: (trace (n, max, 4)
+        FP64 of (t_k, element id, value before the transfer function, segment
+        min(t_{k+1}, t_out) - t_k); count (n,) samples composited; rgba (n, 4);
+        stats dict).  t_k and the element ids are the FP32 decisions of R11 and
+        Alg. 1 (exact), the values FP64 Eq. 2."""
+        return self._render(cam, tf, step, pixels, threads, int(max_samples))
+
+    def _render(self, cam, tf, step, pixels, threads, max_trace):
         table = np.ascontiguousarray(tf.table, dtype=np.float64).reshape(256, 4)
         t = _TF()
         t.table = table.ctypes.data
@@ -342,6 +355,15 @@ class Oracle:
             s.light[a] = float(x)
         c = _cam(cam)
         st = _Stats()
+        if max_trace > 0:
+            pix = np.ascontiguousarray(pixels, dtype=np.int32).reshape(-1, 2)
+            out = np.zeros((len(pix), 4), dtype=np.float64)
+            trace = np.zeros((len(pix), max_trace, 4), dtype=np.float64)
+            count = np.zeros(len(pix), dtype=np.int32)
+            _load().orc_render_trace(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), pix.ctypes.data,
+                                     len(pix), max_trace, trace.ctypes.data, count.ctypes.data, out.ctypes.data,
+                                     _threads(threads or self.threads), ctypes.byref(st))
+            return trace, count, out, {"samples": st.samples, "lookups": st.lookups, "rays_hit": st.rays_hit}
         if pixels is None:
             n = cam.width * cam.height
             out = np.zeros((n, 4), dtype=np.float64)

@@ -5,7 +5,8 @@ a transposed axis, an off-by-one), builds the edited copy on the CPU into a
 temporary directory, points the oracle module at it, and runs the pins of
 test_oracle_pins, the label pins of test_oracle_learned and the gradient and
 shading pins of test_oracle_shading, the streamline pins of
-test_oracle_streamlines and the trimming pins of test_oracle_trim; at least
+test_oracle_streamlines, the trimming pins of test_oracle_trim and the
+per-sample trace pins of test_oracle_trace; at least
 one must fail.  The default build is restored
 afterwards.  No GPU is involved.
 """
@@ -20,6 +21,7 @@ import test_oracle_streamlines as SL
 import test_oracle_trim as T
 import test_oracle_tubes as TU
 import test_oracle_pins as P
+import test_oracle_trace as TR
 
 SRC = os.path.join(os.path.dirname(orc.__file__), "oracle.c")
 
@@ -93,6 +95,10 @@ MUTANTS = [
     ("tube shading without the 0.4 floor", "if (I < 0.4) I = 0.4;", ""),
     ("streamline Eq. 4 step without the element", "if (P->step_rule == 1) h = P->h * (double)orc_heuristic_step(v, e);",
      "if (P->step_rule == 1) h = P->h;"),
+    ("trace keeps the next sample's t", "rec[0] = (double)t;", "rec[0] = (double)tn;"),
+    ("trace keeps the unclipped segment", "rec[3] = seg;", "rec[3] = (double)tn - (double)t;"),
+    ("trace counts one sample too many", "if (J->count) J->count[q] = (int32_t)k;",
+     "if (J->count) J->count[q] = (int32_t)k + 1;"),
 ]
 
 
@@ -118,6 +124,8 @@ def _pins(cfg1):
     yield lambda: P.test_heuristic_step_counts_anisotropic()
     yield lambda: P.test_learned_step_counts()
     yield lambda: P.test_early_termination_and_miss(O)
+    yield lambda: TR.test_trace_cfg1_oblique(cfg1, O, "heuristic")
+    yield lambda: TR.test_trace_matches_render_and_counts(cfg1, O)
     yield lambda: L.test_labels_constant_field_accept_every_candidate(cfg1)
     yield lambda: L.test_labels_monotone_in_tau(cfg1, O)
     yield lambda: L.test_labels_count_what_the_last_step_skips()
