@@ -44,8 +44,30 @@ BLOCKS = (64, 64, 64)
 METRIC = "Gsamples/s (1080p frame, MR-like tricubic LR-spline, Eq. 4 steps)"
 L2_FLUSH_BYTES = 512 << 20
 
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
-FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12   # 80.5 TFLOP/s
+FP32_LANES = 128   # FP32 FMA lanes per SM (Blackwell)
+
+
+def fp32_peak(clocks: dict | None = None):
+    """FP32 FMA peak of the current device in TFLOP/s and how it was derived:
+    the SM count from the device properties x 128 lanes x 2 flop x the median
+    SM clock sampled during the timed region (else the GPU's maximum SM clock,
+    from the same sampling or the measured-peaks file).  No FP32 rate is
+    measured by a copy or a GEMM, so this is a derived denominator."""
+    import torch
+    sms = torch.cuda.get_device_properties(torch.cuda.current_device()).multi_processor_count
+    mhz, src = None, None
+    if clocks and clocks.get("sm_mhz"):
+        mhz, src = float(clocks["sm_mhz"]), "median SM clock sampled during the timed region"
+    elif clocks and clocks.get("sm_max_mhz"):
+        mhz, src = float(clocks["sm_max_mhz"]), "maximum SM clock reported by nvidia-smi"
+    else:
+        try:
+            mhz = float(json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["sm_max_mhz"])
+            src = "maximum SM clock in the measured-peaks file"
+        except (OSError, ValueError, KeyError):
+            mhz, src = 2070.0, "nominal maximum SM clock (no clock sampled)"
+    peak = sms * FP32_LANES * 2 * mhz * 1e6 / 1e12
+    return peak, f"derived: {sms} SMs (device property) x {FP32_LANES} FP32 lanes x 2 x {mhz:.0f} MHz ({src})"
 
 
 def _dist():
@@ -642,6 +664,7 @@ def run_ours(args):
             evs[k][1].record(stream)
         torch.cuda.synchronize()
         wall = time.perf_counter() - w0
+    clk_summary = clk.summary()
     if dist:
         dist.barrier()
     per = [a.elapsed_time(b) for a, b in evs]
@@ -677,7 +700,8 @@ def run_ours(args):
         shading = {"what": "gradient shading (Sec. 4.1), light at the eye, same frame and storage",
                    "ms_per_frame": ms_sh, "samples_per_frame": s_samples,
                    "gsamples_per_s": s_samples / (ms_sh / 1e3) / 1e9, "flop_per_sample": fps_sh,
-                   "achieved_tflops": ach, "frac_of_fp32_peak": ach / FP32_PEAK_TFLOPS, "frames_timed": n_sh,
+                   "achieved_tflops": ach, "frac_of_fp32_peak": ach / fp32_peak(clk_summary)[0],
+                   "frames_timed": n_sh,
                    "kernel": f"k_render<{int(vol.deg[0])},3,{args.storage}>"}
 
     sl = None
@@ -753,10 +777,11 @@ def run_ours(args):
     achieved = flop / (ms_per_step / 1e3) / 1e12
     prof = profiled_counters() if (args.workload == "cfg2" and args.storage == "f32") else None
     fcode = {"scalar": 0, "magnitude": 1, "component": 2}[step.field]
-    roof = {"bound": "alu", "achieved": achieved, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-            "frac": achieved / FP32_PEAK_TFLOPS, "traffic": prof["traffic"] if prof else None,
+    peak, peak_src = fp32_peak(clk_summary)
+    roof = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": prof["traffic"] if prof else None,
             "kernel": f"k_render<{int(vol.deg[0])},{fcode},{args.storage}>", "flop_per_sample": fps,
-            "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2070 MHz (no FP32 figure measured)"}
+            "peak_source": peak_src}
     hbm = measured_hbm_gbs()
     if prof:
         dram_gbs = prof["traffic"] / (ms_per_step / 1e3) / 1e9
@@ -773,7 +798,7 @@ def run_ours(args):
                        "samples_per_frame": samples_per_frame, "rays_hit": st["rays_hit"],
                        "lookups_per_frame": st["lookups"], "parallelism": f"replicas x{ws}"},
             "wall_s": wall, "gpu_launches": args.steps,
-            "roofline": roof, "e2e": e2e, "clocks": clk.summary(),
+            "roofline": roof, "e2e": e2e, "clocks": clk_summary,
             "setup": {"create_s": t1 - t0, "build_accel_s": t2 - t1, "to_bezier_s": t3 - t2,
                       "forest_depth": [st["depth_min"], st["depth_max"], st["depth_mean"], st["depth_var"]],
                       "n_nodes": st["n_nodes"], "incidence_entries": st["incidence_entries"]}}
