@@ -186,6 +186,39 @@ int lrvol_to_bezier(lrvol_t vol, int32_t storage, void *stream);
 int lrvol_render(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
                  float *rgba_dev, void *stream);
 
+/* Trace of the render kernel's own samples for a list of pixels: the parity
+ * hook that compares the march of lrvol_render, sample by sample, with an
+ * independent implementation of Sec. 4 (ray setup), Alg. 1 (element look-up),
+ * Sec. 3.2.3 (Bezier evaluation), Eq. 4 (step) and Alg. 2 (compositing).  It
+ * runs the same kernel template as lrvol_render, with a compile-time trace
+ * flag that is off in every lrvol_render launch; every per-ray decision and
+ * value is the same as in lrvol_render's image (one thread per listed pixel
+ * instead of per tile position; a ray's work does not depend on its
+ * neighbours).
+ *   pix_dev      n_pix x 2 int32 (i, j) pixel coordinates (device); the
+ *                camera's row range is ignored.  A pixel outside the image
+ *                gets count 0, RGBA 0 and sets the status word (LRVOL_ERR_BOUNDS
+ *                at the next lrvol_stats).
+ *   trace_dev    n_pix x max_samples x 4 floats (device): for composited
+ *                sample k < max_samples of pixel q, at [q][k]:
+ *                (t_k, element id as the bits of a uint32, the field value
+ *                before the transfer function -- scalar, |v| or the chosen
+ *                component --, segment length min(t_{k+1}, t_out) - t_k).
+ *                Entries past a pixel's count are unspecified (the sample
+ *                evaluated after the last composited one may be written).
+ *   count_dev    n_pix int32 (device): samples composited for the pixel (may
+ *                exceed max_samples; only the first max_samples are written).
+ *   rgba_dev     n_pix x 4 floats (device): the pixel's premultiplied RGBA,
+ *                equal to lrvol_render's for that pixel.
+ * lrvol_stats then reports this call's samples, look-ups and rays hit.
+ * Asynchronous on `stream`.  n_pix = 0 launches nothing.
+ * Errors: LRVOL_ERR_ARG (negative sizes, null pointers with n_pix > 0, bad
+ * camera/step as lrvol_render), LRVOL_ERR_STATE, LRVOL_ERR_UNSUPPORTED,
+ * LRVOL_ERR_CUDA. */
+int lrvol_render_trace(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                       const int32_t *pix_dev, int64_t n_pix, int32_t max_samples, float *trace_dev,
+                       int32_t *count_dev, float *rgba_dev, void *stream);
+
 /* lrvol_render for callers that may not allocate device memory.  Some
  * callers cannot call cudaMalloc: a host application that owns every byte of
  * device memory through its own pool and forbids libraries to allocate, or a
@@ -202,13 +235,17 @@ int lrvol_render(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const
  * optionally counters_dev (4 uint64 on the device, or NULL) receiving samples,
  * look-ups, rays hit and the device status word (0 ok, 1 bounds, 2 timeout).
  * The first call on each device looks up the array's device address with
- * that device current (make that first call before any stream capture).
- * Each call clears the counters on `stream` first; all calls share the one
+ * that device current (make that first call before any stream capture); the
+ * address is kept for the life of the process, so a caller that resets the
+ * device (cudaDeviceReset) must not call this function afterwards.
+ * Each call clears the scratch on `stream` first; all calls share the one
  * array and it keeps the last call's contents, so calls that overlap on the
- * GPU (other streams, other threads) race on it.
- * Sizes: one call needs 40 of the 256 bytes, whatever the image size; the
- * maximum image is 32768 x 32768 (as for lrvol_render), larger ones are
- * rejected with LRVOL_ERR_ARG.  Other errors: as lrvol_render. */
+ * GPU (other streams, other threads) race on it.  An empty row band
+ * (row_begin == row_end != 0) launches no kernel and reports zero counters.
+ * Sizes: one call uses 72 of the 256 bytes (8 counter slots and the status
+ * word), whatever the image size; the maximum image is 32768 x 32768 (as for
+ * lrvol_render), larger ones are rejected with LRVOL_ERR_ARG.  Other errors:
+ * as lrvol_render. */
 int lrvol_render_noalloc(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
                          float *rgba_dev, uint64_t *counters_dev, void *stream);
 

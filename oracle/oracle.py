@@ -216,6 +216,31 @@ class Oracle:
         n = _load().orc_incidence(self._h, int(e), out.ctypes.data)
         return out[:n].copy()
 
+    def coefficient_hull(self, elements, threads: int | None = None):
+        """Per element and component, (min, max) of the coefficients c_i of the
+        B-splines whose support contains the element.  The element's Bernstein
+        coefficients are convex combinations of these (gamma_i N_i sum to one
+        and each restricted N_i has non-negative Bernstein coefficients), so
+        the hull bounds the block's range without computing the block.
+        Returns (n, nc, 2)."""
+        from concurrent.futures import ThreadPoolExecutor
+        el = np.asarray(elements, dtype=np.int64).reshape(-1)
+        out = np.empty((len(el), self.nc, 2), dtype=np.float64)
+        L = _load()
+
+        def work(rows):
+            buf = np.empty(self.n_basis, dtype=np.int64)
+            for r in rows:
+                n = L.orc_incidence(self._h, int(el[r]), buf.ctypes.data)
+                c = self.coef[buf[:n]]
+                out[r, :, 0] = c.min(axis=0)
+                out[r, :, 1] = c.max(axis=0)
+
+        nth = max(1, min(_threads(threads or self.threads), len(el)))
+        with ThreadPoolExecutor(nth) as ex:
+            list(ex.map(work, [range(t, len(el), nth) for t in range(nth)]))
+        return out
+
     def lookup(self, pts_f32) -> np.ndarray:
         p = np.ascontiguousarray(pts_f32, dtype=np.float32).reshape(-1, 3)
         out = np.empty(len(p), dtype=np.uint32)

@@ -19,8 +19,8 @@ FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-I", INCLUDE, "-I", CSRC,
          # host code: no FMA contraction (the camera constants are FP64 algebra
          # with a fixed order of operations, shared by the ray definition)
          "-Xcompiler", "-fPIC,-ffp-contract=off,-fno-fast-math"]
-SOURCES = ["kernels.cu", "host.cpp", "server.cpp"]
-HEADERS = ["lrvol_internal.h"]
+SOURCES = ["kernels.cu", "render.cu", "host.cpp", "server.cpp"]
+HEADERS = ["lrvol_internal.h", "device_common.cuh"]
 
 
 def nvcc() -> str:

@@ -642,6 +642,35 @@ int lrvol_render(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   return LRVOL_OK;
 }
 
+// The render kernel's own samples for a list of pixels (parity diagnostic):
+// same checks and kernel template as lrvol_render, with the trace compiled in.
+int lrvol_render_trace(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step,
+                       const int32_t *pix_dev, int64_t n_pix, int32_t max_samples, float *trace_dev,
+                       int32_t *count_dev, float *rgba_dev, void *stream) {
+  if (n_pix < 0 || max_samples < 0) return fail(LRVOL_ERR_ARG, "n_pix and max_samples must be >= 0");
+  if (n_pix > ((int64_t)1 << 37)) return fail(LRVOL_ERR_ARG, "more than 2^37 pixels");
+  if (n_pix > 0 && (!pix_dev || !count_dev || !rgba_dev || (max_samples > 0 && !trace_dev)))
+    return fail(LRVOL_ERR_ARG, "null pointer");
+  RenderParams prm;
+  int field = 0;
+  float unused = 0.f;   // prepare_render wants an image pointer; the traced kernel writes none
+  int rc = prepare_render(v, cam, tf, step, &unused, &prm, &field);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  prm.counters = v->d_counters;
+  prm.status = v->d_status;
+  prm.out = nullptr;
+  prm.trace_pix = pix_dev;
+  prm.trace_n = n_pix;
+  prm.trace_max = max_samples;
+  prm.trace_rec = reinterpret_cast<float4 *>(trace_dev);
+  prm.trace_count = count_dev;
+  prm.trace_rgba = reinterpret_cast<float4 *>(rgba_dev);
+  CU(cudaMemsetAsync(v->d_counters, 0, sizeof(unsigned long long) * kNumCounters, st), "clear counters");
+  CU(launch_render_trace(prm, v->p[0], field, v->storage, st), "render trace kernel");
+  return LRVOL_OK;
+}
+
 // The allocation-free render: same checks and kernel as lrvol_render, but the
 // kernel's scratch (statistics counters, status word) is the library's
 // static device array instead of memory of the handle, and nothing is allocated.

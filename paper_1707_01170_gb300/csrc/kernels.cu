@@ -6,9 +6,8 @@
 //   k_elem_records element boxes -> FP32 records (rounded-up corners, Eq. 4 step).
 //   k_lookup       Alg. 1 element look-up through the k-d forest.
 //   k_eval         look-up + Bezier block evaluation at points.
-//   k_render       Sec. 4: per-pixel ray casting with element reuse, Eq. 4
-//                  steps, transfer function and Alg. 2 compositing (and
-//                  gradient shading, Sec. 4.1).
+//   (k_render, the per-pixel ray casting of Sec. 4, is in render.cu; the
+//   device helpers both files use are in device_common.cuh.)
 //   k_features, k_mlp_infer, k_labels, k_dense_*, k_adam
 //                  learned step multipliers (not in the paper; Eq. 4 stays the
 //                  base): per-element features, the network on the tcgen05
@@ -16,20 +15,12 @@
 //   k_streamlines, k_streamline_error, k_tube_*
 //                  Sec. 5 streamlines (Eq. 4 steps), the Eq. 7 error, tubes.
 //   k_trim_raster  Sec. 4.1 trimming: per-pixel interval of a boundary mesh.
-#include <cuda_bf16.h>
-#include <cuda_fp16.h>
-#include <cuda_runtime.h>
-
 #include <algorithm>
-#include <cstdint>
-#include <mutex>
 
-#include "lrvol_internal.h"
+#include "device_common.cuh"
 
 namespace lrvol {
 namespace {
-
-__device__ __forceinline__ void set_status(uint32_t *status, uint32_t code) { atomicCAS(status, 0u, code); }
 
 // ----------------------------------------------------------------------------
 // change of basis (FP64)
@@ -218,26 +209,6 @@ __global__ void k_elem_records(const double *__restrict__ box, int64_t n_elem, i
   out[e] = r;
 }
 
-// ----------------------------------------------------------------------------
-// look-up (Alg. 1)
-// ----------------------------------------------------------------------------
-
-__device__ __forceinline__ uint32_t forest_lookup(const ForestView &f, float x, float y, float z, uint32_t *status) {
-  const int bx = min((int)(x * f.fbx), f.bx - 1);
-  const int by = min((int)(y * f.fby), f.by - 1);
-  const int bz = min((int)(z * f.fbz), f.bz - 1);
-  uint32_t w = __ldg(f.head + ((int64_t)bz * f.by + by) * f.bx + bx);
-  for (int depth = 0; !(w & kLeaf); ++depth) {
-    if ((int64_t)w >= f.n_nodes || depth >= kMaxDepth) {
-      set_status(status, kStatusBounds);
-      return kNone;
-    }
-    const uint4 n = __ldg(f.nodes + w);
-    const float pa = n.y == 0 ? x : (n.y == 1 ? y : z);
-    w = pa < __uint_as_float(n.x) ? n.z : n.w;
-  }
-  return w & ~kLeaf;
-}
 
 __global__ void k_lookup(ForestView f, int64_t n_elem, const float *__restrict__ pts, int64_t n,
                          uint32_t *__restrict__ out, uint32_t *status) {
@@ -255,76 +226,6 @@ __global__ void k_lookup(ForestView f, int64_t n_elem, const float *__restrict__
   out[q] = e;
 }
 
-// ----------------------------------------------------------------------------
-// Bezier evaluation.  Render blocks hold binomially scaled coefficients, so a
-// block is evaluated as sum c'_ijk m_i(u) m_j(v) m_k(w) with monomials
-// m_i(u) = u^i (1-u)^(p-i).
-// ----------------------------------------------------------------------------
-
-template <int P>
-__device__ __forceinline__ void monomials(float u, float *m) {
-  const float v = 1.f - u;
-  if constexpr (P == 1) {
-    m[0] = v;
-    m[1] = u;
-  } else if constexpr (P == 2) {
-    m[0] = v * v;
-    m[1] = u * v;
-    m[2] = u * u;
-  } else {
-    const float u2 = u * u, v2 = v * v;
-    m[0] = v2 * v;
-    m[1] = u * v2;
-    m[2] = u2 * v;
-    m[3] = u2 * u;
-  }
-}
-
-// Derivatives d m_i / du = i u^(i-1) (1-u)^(p-i) - (p-i) u^i (1-u)^(p-i-1).
-template <int P>
-__device__ __forceinline__ void dmonomials(float u, float *d) {
-  const float v = 1.f - u;
-  if constexpr (P == 1) {
-    d[0] = -1.f;
-    d[1] = 1.f;
-  } else if constexpr (P == 2) {
-    d[0] = -2.f * v;
-    d[1] = v - u;
-    d[2] = 2.f * u;
-  } else {
-    const float uv = u * v;
-    d[0] = -3.f * (v * v);
-    d[1] = fmaf(-2.f, uv, v * v);
-    d[2] = fmaf(2.f, uv, -(u * u));
-    d[3] = 3.f * (u * u);
-  }
-}
-
-// sum_{k,j,i} c[k][j][i] bx[i] by[j] bz[k], x fastest
-template <int P>
-__device__ __forceinline__ float contract(const float *c, const float *bx, const float *by, const float *bz) {
-  constexpr int N = P + 1;
-  float f = 0.f;
-#pragma unroll
-  for (int k = 0; k < N; ++k) {
-    float t = 0.f;
-#pragma unroll
-    for (int j = 0; j < N; ++j) {
-      float s = 0.f;
-#pragma unroll
-      for (int i = 0; i < N; ++i) s = fmaf(c[(k * N + j) * N + i], bx[i], s);
-      t = fmaf(s, by[j], t);
-    }
-    f = fmaf(t, bz[k], f);
-  }
-  return f;
-}
-
-// u = (p - lo) / (hi - lo) as (p - lo_RU) * iw + (lo_RU - lo) * iw: one fused rounding after
-// the subtraction, which is exact when p is near lo_RU (the offset term is tiny).
-__device__ __forceinline__ float local_u(float p, float lo_ru, float off, float iw) {
-  return __fmaf_rn(__fsub_rn(p, lo_ru), iw, off);
-}
 
 // Generic-degree evaluation for the point kernel (any p0,p1,p2 <= 4).
 __device__ float eval_generic(const float *c, const int *deg, float ux, float uy, float uz) {
@@ -476,601 +377,6 @@ __global__ void k_eval_grad(ForestView f, const ElemRec *__restrict__ elem, int6
   *o = make_float4(v, sc * g[0] * r.d.x, sc * g[1] * r.d.y, sc * g[2] * r.d.z);
 }
 
-// ----------------------------------------------------------------------------
-// render (Sec. 4, Alg. 2, Eq. 4)
-// ----------------------------------------------------------------------------
-
-__device__ __forceinline__ float ex2_approx(float x) {
-  float y;
-  asm("ex2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-__device__ __forceinline__ float lg2_approx(float x) {
-  float y;
-  asm("lg2.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
-  return y;
-}
-
-struct Ray {
-  float o[3], d[3], tin, tout;
-};
-
-// FP32 ray of pixel (i, j) and its interval in the unit cube (order of
-// operations as stated in lrvol.h).  Returns false on a miss.
-__device__ __forceinline__ bool make_ray(const RayConsts &K, int i, int j, Ray &r) {
-  const float a = __fmaf_rn(__fadd_rn((float)i, 0.5f), K.sxs, K.sxo);
-  const float b = __fmaf_rn(__fadd_rn((float)j, 0.5f), K.sys, K.syo);
-  if (K.persp) {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      r.d[c] = __fmaf_rn(a, K.R[c], __fmaf_rn(b, K.U[c], K.F[c]));
-      r.o[c] = K.E[c];
-    }
-    const float n = __fsqrt_rn(__fmaf_rn(r.d[0], r.d[0], __fmaf_rn(r.d[1], r.d[1], __fmul_rn(r.d[2], r.d[2]))));
-#pragma unroll
-    for (int c = 0; c < 3; ++c) r.d[c] = __fdiv_rn(r.d[c], n);
-  } else {
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      r.o[c] = __fmaf_rn(a, K.R[c], __fmaf_rn(b, K.U[c], K.E[c]));
-      r.d[c] = K.F[c];
-    }
-  }
-  float tin = 0.f, tout = __int_as_float(0x7f800000);
-  bool hit = true;
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    if (r.d[c] == 0.f) {
-      if (r.o[c] < 0.f || r.o[c] > 1.f) hit = false;
-    } else {
-      const float inv = __fdiv_rn(1.f, r.d[c]);
-      const float ta = __fmul_rn(__fsub_rn(0.f, r.o[c]), inv);
-      const float tb = __fmul_rn(__fsub_rn(1.f, r.o[c]), inv);
-      tin = fmaxf(tin, fminf(ta, tb));
-      tout = fminf(tout, fmaxf(ta, tb));
-    }
-  }
-  r.tin = tin;
-  r.tout = tout;
-  return hit && tin < tout;
-}
-
-// Transfer function lookup and one Alg. 2 update in transmittance form
-// (Tr = 1 - alpha_dst): w = (1 - T) Tr, C += w C_src, Tr *= T.
-__device__ __forceinline__ void composite(const float4 *tfb, const float4 *tfd, float v, float seg,
-                                          const RenderParams &prm, float &C0, float &C1, float &C2, float &Tr) {
-  const float x = fminf(fmaxf(fmaf(v, prm.tf_scale, prm.tf_bias), 0.f), 255.f);
-  const int q = min((int)x, 254);
-  const float fr = x - (float)q;
-  const float4 e0 = tfb[q], de = tfd[q];
-  const float sa = fmaf(fr, de.w, e0.w);
-  const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (seg * prm.inv_xi));
-  const float w = fmaf(-Tr, T, Tr);
-  C0 = fmaf(w, fmaf(fr, de.x, e0.x), C0);
-  C1 = fmaf(w, fmaf(fr, de.y, e0.y), C1);
-  C2 = fmaf(w, fmaf(fr, de.z, e0.z), C2);
-  Tr *= T;
-}
-
-// Alg. 2 with C_src multiplied by the shading intensity sh (Sec. 4.1).
-__device__ __forceinline__ void composite_shaded(const float4 *tfb, const float4 *tfd, float v, float seg, float sh,
-                                                 const RenderParams &prm, float &C0, float &C1, float &C2,
-                                                 float &Tr) {
-  const float x = fminf(fmaxf(fmaf(v, prm.tf_scale, prm.tf_bias), 0.f), 255.f);
-  const int q = min((int)x, 254);
-  const float fr = x - (float)q;
-  const float4 e0 = tfb[q], de = tfd[q];
-  const float sa = fmaf(fr, de.w, e0.w);
-  const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (seg * prm.inv_xi));
-  const float w = fmaf(-Tr, T, Tr) * sh;
-  C0 = fmaf(w, fmaf(fr, de.x, e0.x), C0);
-  C1 = fmaf(w, fmaf(fr, de.y, e0.y), C1);
-  C2 = fmaf(w, fmaf(fr, de.z, e0.z), C2);
-  Tr *= T;
-}
-
-// ---- packed two-lane FP32 (fma.rn.f32x2 and friends; lane "lo" first) ----
-typedef unsigned long long f2;
-
-__device__ __forceinline__ f2 f2_pack(float lo, float hi) {
-  f2 d;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(lo), "f"(hi));
-  return d;
-}
-__device__ __forceinline__ void f2_unpack(f2 a, float &lo, float &hi) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(a));
-}
-__device__ __forceinline__ f2 f2_mul(f2 a, f2 b) {
-  f2 d;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(d) : "l"(a), "l"(b));
-  return d;
-}
-__device__ __forceinline__ f2 f2_fma(f2 a, f2 b, f2 c) {
-  f2 d;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(d) : "l"(a), "l"(b), "l"(c));
-  return d;
-}
-// 256-bit read-only load (32-byte aligned address)
-__device__ __forceinline__ void ld256(const void *p, f2 &a, f2 &b, f2 &c, f2 &d) {
-  asm("ld.global.nc.v4.b64 {%0, %1, %2, %3}, [%4];" : "=l"(a), "=l"(b), "=l"(c), "=l"(d) : "l"(p));
-}
-__device__ __forceinline__ float4 f2x2_to_float4(f2 a, f2 b) {
-  float4 r;
-  f2_unpack(a, r.x, r.y);
-  f2_unpack(b, r.z, r.w);
-  return r;
-}
-
-// Element record: two 256-bit loads.
-__device__ __forceinline__ void load_record(const ElemRec *er, float4 &ra, float4 &rb, float4 &rc, float4 &rd) {
-  f2 w0, w1, w2, w3, w4, w5, w6, w7;
-  ld256(er, w0, w1, w2, w3);
-  ld256(reinterpret_cast<const char *>(er) + 32, w4, w5, w6, w7);
-  ra = f2x2_to_float4(w0, w1);
-  rb = f2x2_to_float4(w2, w3);
-  rc = f2x2_to_float4(w4, w5);
-  rd = f2x2_to_float4(w6, w7);
-}
-
-// 16-bit storage: two values of one 32-bit word -> FP32 pair (lo = low half).
-template <int STORE>
-__device__ __forceinline__ float h_to_f(unsigned h) {
-  if constexpr (STORE == LRVOL_STORE_F16) return __half2float(__ushort_as_half((unsigned short)h));
-  return __uint_as_float(h << 16);
-}
-template <int STORE>
-__device__ __forceinline__ f2 word_to_f2(unsigned w) {
-  if constexpr (STORE == LRVOL_STORE_BF16) {
-    return ((f2)(w & 0xffff0000u) << 32) | (f2)(w << 16);
-  } else {
-    return f2_pack(h_to_f<STORE>(w & 0xffffu), h_to_f<STORE>(w >> 16));
-  }
-}
-
-// A pixel's ray interval cut by its trimming interval (Sec. 4.1): no hit
-// hides the pixel; only back faces (the eye inside the mesh) keep
-// [t_in, t_back]; only front faces keep [t_front, t_out].
-__device__ __forceinline__ bool trim_cut(float2 tr, float &tin, float &tout) {
-  const float inf = __int_as_float(0x7f800000);
-  if (tr.x == inf && tr.y == 0.f) return false;
-  if (tr.x != inf && tr.x > tin) tin = tr.x;
-  if (tr.y != 0.f && tr.y < tout) tout = tr.y;
-  return tin < tout;
-}
-
-// One element's block in registers and its evaluation at monomials bx, by, bz.
-//   FIELD 0: scalar volume; 1: |v| of a 3-vector; 2: one component of a
-//   3-vector, read from the plain per-component copy.
-//   STORE: LRVOL_STORE_F32, or F16/BF16 values converted to FP32 when the
-//   element is entered, with the value of component c = o_c + s_c * contraction.
-template <int P, int FIELD, int STORE>
-struct Block {
-  static constexpr int N = P + 1;
-  static constexpr int NB = N * N * N;
-  static constexpr bool ROWPAIR = FIELD == 0 && P == 3;   // scalar tricubic: packed row pairs
-  static constexpr bool SCALAR_GENERIC = FIELD == 0 && P != 3;
-  static constexpr bool PAIRS = FIELD == 1;                // components 0 and 1 packed
-  static constexpr bool COMP2 = FIELD == 1 || FIELD == 2;  // one component as plain floats
-  static constexpr bool F32 = STORE == LRVOL_STORE_F32;
-  static constexpr int SGF = ((N * N + 1) / 2) * 2 * N;    // scalar generic: slots used (<= stride)
-  static constexpr int PAIRF = (2 * NB + 7) & ~7;          // slots of the component pair block
-  static constexpr int C2F = (NB + 7) & ~7;                // slots of one plain component
-
-  f2 rp[ROWPAIR ? 8 : 1][4];                 // row pairs (2m, 2m+1), value i
-  float sg[SCALAR_GENERIC ? ((SGF + 7) & ~7) : 1];
-  f2 cp[PAIRS ? PAIRF / 2 : 1];              // (c0, c1) per q
-  float c2[COMP2 ? C2F : 1];
-  float oa, sa, ob, sb, oc, sc;              // affine map of 16-bit storage (component a/b/c)
-
-  __device__ __forceinline__ void load(const unsigned char *eb, int comp) {
-    if constexpr (F32) {
-      const float *fb = reinterpret_cast<const float *>(eb);
-      if constexpr (ROWPAIR) {
-#pragma unroll
-        for (int m = 0; m < 8; ++m) ld256(fb + 8 * m, rp[m][0], rp[m][1], rp[m][2], rp[m][3]);
-      }
-      if constexpr (SCALAR_GENERIC) {
-        const float4 *b4 = reinterpret_cast<const float4 *>(fb);
-#pragma unroll
-        for (int q = 0; q < (SGF + 3) / 4; ++q) {
-          const float4 v = __ldg(b4 + q);
-          sg[4 * q] = v.x;
-          sg[4 * q + 1] = v.y;
-          sg[4 * q + 2] = v.z;
-          sg[4 * q + 3] = v.w;
-        }
-      }
-      if constexpr (PAIRS) {
-#pragma unroll
-        for (int q = 0; q < PAIRF / 8; ++q) ld256(fb + 8 * q, cp[4 * q], cp[4 * q + 1], cp[4 * q + 2], cp[4 * q + 3]);
-      }
-      if constexpr (COMP2) {
-        const float4 *b4 = reinterpret_cast<const float4 *>(FIELD == 1 ? fb + PAIRF : fb + comp * C2F);
-#pragma unroll
-        for (int q = 0; q < C2F / 4; ++q) {
-          const float4 v = __ldg(b4 + q);
-          c2[4 * q] = v.x;
-          c2[4 * q + 1] = v.y;
-          c2[4 * q + 2] = v.z;
-          c2[4 * q + 3] = v.w;
-        }
-      }
-    } else {
-      const float4 *hdr = reinterpret_cast<const float4 *>(eb);
-      const float4 h0 = __ldg(hdr), h1 = __ldg(hdr + 1);   // o0 o1 o2 s0 | s1 s2 - -
-      const uint4 *d = reinterpret_cast<const uint4 *>(eb + kHeaderBytes);   // 8 slots per chunk
-      if constexpr (ROWPAIR) {
-        oa = h0.x;
-        sa = h0.w;
-#pragma unroll
-        for (int m = 0; m < 8; ++m) {   // chunk m holds words 4m+i = (row 2m, row 2m+1) value i
-          const uint4 w = __ldg(d + m);
-          rp[m][0] = word_to_f2<STORE>(w.x);
-          rp[m][1] = word_to_f2<STORE>(w.y);
-          rp[m][2] = word_to_f2<STORE>(w.z);
-          rp[m][3] = word_to_f2<STORE>(w.w);
-        }
-      }
-      if constexpr (SCALAR_GENERIC) {
-        oa = h0.x;
-        sa = h0.w;
-#pragma unroll
-        for (int q = 0; q < (SGF + 7) / 8; ++q) {
-          const uint4 w = __ldg(d + q);
-          const unsigned ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            sg[8 * q + 2 * t] = h_to_f<STORE>(ws[t] & 0xffffu);
-            sg[8 * q + 2 * t + 1] = h_to_f<STORE>(ws[t] >> 16);
-          }
-        }
-      }
-      if constexpr (PAIRS) {
-        oa = h0.x;
-        ob = h0.y;
-        sa = h0.w;
-        sb = h1.x;
-#pragma unroll
-        for (int q = 0; q < PAIRF / 8; ++q) {
-          const uint4 w = __ldg(d + q);
-          cp[4 * q] = word_to_f2<STORE>(w.x);
-          cp[4 * q + 1] = word_to_f2<STORE>(w.y);
-          cp[4 * q + 2] = word_to_f2<STORE>(w.z);
-          cp[4 * q + 3] = word_to_f2<STORE>(w.w);
-        }
-      }
-      if constexpr (COMP2) {
-        if constexpr (FIELD == 1) {
-          oc = h0.z;
-          sc = h1.y;
-        } else {
-          oc = comp == 0 ? h0.x : (comp == 1 ? h0.y : h0.z);
-          sc = comp == 0 ? h0.w : (comp == 1 ? h1.x : h1.y);
-        }
-        const uint4 *dc = d + (FIELD == 1 ? PAIRF : comp * C2F) / 8;
-#pragma unroll
-        for (int q = 0; q < C2F / 8; ++q) {
-          const uint4 w = __ldg(dc + q);
-          const unsigned ws[4] = {w.x, w.y, w.z, w.w};
-#pragma unroll
-          for (int t = 0; t < 4; ++t) {
-            c2[8 * q + 2 * t] = h_to_f<STORE>(ws[t] & 0xffffu);
-            c2[8 * q + 2 * t + 1] = h_to_f<STORE>(ws[t] >> 16);
-          }
-        }
-      }
-    }
-  }
-
-  // Scalar blocks: value and derivatives in local coordinates (d/du, d/dv, d/dw)
-  // at monomials b* and their derivatives d*, reusing the partial sums of the value.
-  __device__ __forceinline__ float eval_grad(const float *bx, const float *by, const float *bz, const float *dx,
-                                             const float *dy, const float *dz, float &gu, float &gv,
-                                             float &gw) const {
-    static_assert(FIELD == 0, "gradients of scalar blocks only");
-    if constexpr (ROWPAIR) {
-      const f2 X0 = f2_pack(bx[0], bx[0]), X1 = f2_pack(bx[1], bx[1]);
-      const f2 X2 = f2_pack(bx[2], bx[2]), X3 = f2_pack(bx[3], bx[3]);
-      const f2 D0 = f2_pack(dx[0], dx[0]), D1 = f2_pack(dx[1], dx[1]);
-      const f2 D2 = f2_pack(dx[2], dx[2]), D3 = f2_pack(dx[3], dx[3]);
-      const f2 Y01 = f2_pack(by[0], by[1]), Y23 = f2_pack(by[2], by[3]);
-      const f2 E01 = f2_pack(dy[0], dy[1]), E23 = f2_pack(dy[2], dy[3]);
-      f2 F = 0, FX = 0, FY = 0, FZ = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const f2 *a = rp[2 * k], *b = rp[2 * k + 1];
-        const f2 S0 = f2_fma(a[3], X3, f2_fma(a[2], X2, f2_fma(a[1], X1, f2_mul(a[0], X0))));
-        const f2 S1 = f2_fma(b[3], X3, f2_fma(b[2], X2, f2_fma(b[1], X1, f2_mul(b[0], X0))));
-        const f2 R0 = f2_fma(a[3], D3, f2_fma(a[2], D2, f2_fma(a[1], D1, f2_mul(a[0], D0))));
-        const f2 R1 = f2_fma(b[3], D3, f2_fma(b[2], D2, f2_fma(b[1], D1, f2_mul(b[0], D0))));
-        const f2 T = f2_fma(S1, Y23, f2_mul(S0, Y01));
-        const f2 TX = f2_fma(R1, Y23, f2_mul(R0, Y01));
-        const f2 TY = f2_fma(S1, E23, f2_mul(S0, E01));
-        const f2 Z = f2_pack(bz[k], bz[k]), DZ = f2_pack(dz[k], dz[k]);
-        F = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, F);
-        FX = k == 0 ? f2_mul(TX, Z) : f2_fma(TX, Z, FX);
-        FY = k == 0 ? f2_mul(TY, Z) : f2_fma(TY, Z, FY);
-        FZ = k == 0 ? f2_mul(T, DZ) : f2_fma(T, DZ, FZ);
-      }
-      float lo, hi;
-      f2_unpack(FX, lo, hi);
-      gu = F32 ? lo + hi : sa * (lo + hi);
-      f2_unpack(FY, lo, hi);
-      gv = F32 ? lo + hi : sa * (lo + hi);
-      f2_unpack(FZ, lo, hi);
-      gw = F32 ? lo + hi : sa * (lo + hi);
-      f2_unpack(F, lo, hi);
-      return F32 ? lo + hi : fmaf(sa, lo + hi, oa);
-    } else {
-      float f = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        float t = 0.f, tx = 0.f, ty = 0.f;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const int r = k * N + j;
-          float sx = 0.f, rx = 0.f;
-#pragma unroll
-          for (int i = 0; i < N; ++i) {
-            const float c = sg[(r >> 1) * 2 * N + 2 * i + (r & 1)];
-            sx = fmaf(c, bx[i], sx);
-            rx = fmaf(c, dx[i], rx);
-          }
-          t = fmaf(sx, by[j], t);
-          tx = fmaf(rx, by[j], tx);
-          ty = fmaf(sx, dy[j], ty);
-        }
-        f = fmaf(t, bz[k], f);
-        fx = fmaf(tx, bz[k], fx);
-        fy = fmaf(ty, bz[k], fy);
-        fz = fmaf(t, dz[k], fz);
-      }
-      gu = F32 ? fx : sa * fx;
-      gv = F32 ? fy : sa * fy;
-      gw = F32 ? fz : sa * fz;
-      return F32 ? f : fmaf(sa, f, oa);
-    }
-  }
-
-  __device__ __forceinline__ float eval(const float *bx, const float *by, const float *bz) const {
-    if constexpr (ROWPAIR) {
-      // rows r = k*4 + j; pair m = 2k + (j >> 1) holds (row 2m, row 2m+1)
-      const f2 X0 = f2_pack(bx[0], bx[0]), X1 = f2_pack(bx[1], bx[1]);
-      const f2 X2 = f2_pack(bx[2], bx[2]), X3 = f2_pack(bx[3], bx[3]);
-      const f2 Y01 = f2_pack(by[0], by[1]), Y23 = f2_pack(by[2], by[3]);
-      f2 F = 0;
-#pragma unroll
-      for (int k = 0; k < 4; ++k) {
-        const f2 *a = rp[2 * k], *b = rp[2 * k + 1];
-        const f2 S0 = f2_fma(a[3], X3, f2_fma(a[2], X2, f2_fma(a[1], X1, f2_mul(a[0], X0))));
-        const f2 S1 = f2_fma(b[3], X3, f2_fma(b[2], X2, f2_fma(b[1], X1, f2_mul(b[0], X0))));
-        const f2 T = f2_fma(S1, Y23, f2_mul(S0, Y01));   // (t_k over j even, t_k over j odd)
-        const f2 Z = f2_pack(bz[k], bz[k]);
-        F = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, F);
-      }
-      float lo, hi;
-      f2_unpack(F, lo, hi);
-      return F32 ? lo + hi : fmaf(sa, lo + hi, oa);
-    } else if constexpr (SCALAR_GENERIC) {
-      float f = 0.f;
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        float t = 0.f;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const int r = k * N + j;
-          float sx = 0.f;
-#pragma unroll
-          for (int i = 0; i < N; ++i) sx = fmaf(sg[(r >> 1) * 2 * N + 2 * i + (r & 1)], bx[i], sx);
-          t = fmaf(sx, by[j], t);
-        }
-        f = fmaf(t, bz[k], f);
-      }
-      return F32 ? f : fmaf(sa, f, oa);
-    } else {
-      float v0, v1, v2;
-      components(bx, by, bz, v0, v1, v2);
-      if constexpr (FIELD == 1) return sqrtf(fmaf(v0, v0, fmaf(v1, v1, v2 * v2)));
-      return v2;
-    }
-  }
-
-  // Vector blocks: the components as evaluated (FIELD 1: all three; FIELD 2:
-  // the chosen component in v2).
-  __device__ __forceinline__ void components(const float *bx, const float *by, const float *bz, float &v0,
-                                             float &v1, float &v2) const {
-    v0 = 0.f;
-    v1 = 0.f;
-    v2 = 0.f;
-    if constexpr (PAIRS) {
-      f2 X[N], Y[N];
-#pragma unroll
-      for (int i = 0; i < N; ++i) {
-        X[i] = f2_pack(bx[i], bx[i]);
-        Y[i] = f2_pack(by[i], by[i]);
-      }
-      f2 V = 0;
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        f2 T = 0;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          const f2 *c = &cp[(k * N + j) * N];
-          f2 S = f2_mul(c[0], X[0]);
-#pragma unroll
-          for (int i = 1; i < N; ++i) S = f2_fma(c[i], X[i], S);
-          T = j == 0 ? f2_mul(S, Y[0]) : f2_fma(S, Y[j], T);
-        }
-        const f2 Z = f2_pack(bz[k], bz[k]);
-        V = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, V);
-      }
-      f2_unpack(V, v0, v1);
-      if constexpr (!F32) {
-        v0 = fmaf(sa, v0, oa);
-        v1 = fmaf(sb, v1, ob);
-      }
-    }
-    if constexpr (COMP2) {
-#pragma unroll
-      for (int k = 0; k < N; ++k) {
-        float t = 0.f;
-#pragma unroll
-        for (int j = 0; j < N; ++j) {
-          float sx = 0.f;
-#pragma unroll
-          for (int i = 0; i < N; ++i) sx = fmaf(c2[(k * N + j) * N + i], bx[i], sx);
-          t = fmaf(sx, by[j], t);
-        }
-        v2 = fmaf(t, bz[k], v2);
-      }
-      if constexpr (!F32) v2 = fmaf(sc, v2, oc);
-    }
-  }
-};
-
-// One CTA of 4 warps renders a 16x8-pixel tile (each warp an 8x4 patch), so
-// the warps sharing an SM's L1 march through neighbouring elements; one lane
-// traces one ray.  The element-change branch (look-up and block loads) is kept
-// minimal: a warp runs it whenever any of its lanes changes element, which
-// happens almost every iteration.
-//
-// In the sample loop the Alg. 2 update of sample k is issued together with
-// the evaluation of sample k+1 (they are independent), so the scheduler can
-// overlap their latencies; a ray that terminates after sample k discards the
-// already evaluated sample k+1.
-//
-// FIELD 3 renders a scalar volume with gradient shading (Sec. 4.1): each
-// sample also evaluates the block's gradient, and C_src is scaled by
-// I = max(0.4, |l . g| / max(|g|, eps)).
-template <int P, int FIELD, int STORE>
-__global__ void __launch_bounds__(128, (FIELD == 3 && P == 3) ? 3 : 4) k_render(const __grid_constant__ RenderParams prm) {
-  constexpr int N = P + 1;
-  constexpr bool SHADE = FIELD == 3;
-  constexpr int BF = SHADE ? 0 : FIELD;
-  __shared__ float4 tfb[256], tfd[256];
-  for (int q = threadIdx.x; q < 256; q += blockDim.x) {
-    const float4 e0 = prm.tf[q], e1 = prm.tf[q < 255 ? q + 1 : 255];
-    tfb[q] = e0;
-    tfd[q] = make_float4(e1.x - e0.x, e1.y - e0.y, e1.z - e0.z, e1.w - e0.w);
-  }
-  __syncthreads();
-
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int i = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-  const int j = prm.row_begin + blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
-  unsigned nsamp = 0, nlook = 0, nhit = 0;
-  const float inf = __int_as_float(0x7f800000);
-
-  Ray ray;
-  if (i < prm.width && j < prm.row_end) {
-    float C0 = 0.f, C1 = 0.f, C2 = 0.f, Tr = 1.f;
-    if (make_ray(prm.ray, i, j, ray) &&
-        (prm.trim == nullptr || trim_cut(__ldg(prm.trim + (int64_t)j * prm.width + i), ray.tin, ray.tout))) {
-      ++nhit;
-      const float tr_stop = 1.f - prm.alpha_stop;
-      float4 ra = make_float4(0.f, 0.f, 0.f, 0.f), rb = ra, rc = ra, rd = ra;
-      float dsv = 0.f;       // step inside the current element (Eq. 4, or Eq. 4 x learned multiplier)
-      Block<P, BF, STORE> blk;
-      float t = ray.tin;
-      int k = 0;
-      bool pend = false;     // a sample evaluated but not yet composited
-      float pv = 0.f, pseg = 0.f, psh = 1.f;
-      float lx = 0.f, ly = 0.f, lz = 0.f;   // towards the light (shading)
-      if constexpr (SHADE) {
-        lx = prm.light_set ? prm.light[0] : -ray.d[0];
-        ly = prm.light_set ? prm.light[1] : -ray.d[1];
-        lz = prm.light_set ? prm.light[2] : -ray.d[2];
-      }
-      for (;;) {
-        if (!(t < ray.tout)) {
-          if (pend) {
-            if constexpr (SHADE)
-              composite_shaded(tfb, tfd, pv, pseg, psh, prm, C0, C1, C2, Tr);
-            else
-              composite(tfb, tfd, pv, pseg, prm, C0, C1, C2, Tr);
-            ++nsamp;
-          }
-          break;
-        }
-        const float px = fminf(fmaxf(__fmaf_rn(t, ray.d[0], ray.o[0]), 0.f), 1.f);
-        const float py = fminf(fmaxf(__fmaf_rn(t, ray.d[1], ray.o[1]), 0.f), 1.f);
-        const float pz = fminf(fmaxf(__fmaf_rn(t, ray.d[2], ray.o[2]), 0.f), 1.f);
-        const bool inside = px >= ra.x && py >= ra.y && pz >= ra.z && px < rb.x && py < rb.y && pz < rb.z;
-        if (!inside) {
-          const uint32_t cur = forest_lookup(prm.forest, px, py, pz, prm.status);
-          if (cur == kNone || (int64_t)cur >= prm.n_elem) {
-            set_status(prm.status, kStatusBounds);
-            break;
-          }
-          ++nlook;
-          load_record(prm.elem + cur, ra, rb, rc, rd);
-          dsv = prm.mode == LRVOL_STEP_LEARNED ? __fmul_rn(ra.w, __ldg(prm.mult + cur)) : ra.w;
-          if constexpr (BF == 2)
-            blk.load(prm.bezc + (int64_t)cur * prm.elemc_bytes, prm.comp);
-          else
-            blk.load(prm.bez + (int64_t)cur * prm.elem_bytes, 0);
-        }
-        float tn = prm.mode == LRVOL_STEP_FIXED ? __fmaf_rn((float)(k + 1), prm.h, ray.tin) : __fadd_rn(t, dsv);
-        if (!(tn > t)) tn = nextafterf(t, inf);
-        const float seg = __fsub_rn(fminf(tn, ray.tout), t);
-        // evaluate sample k ...
-        float bx[N], by[N], bz[N];
-        const float ux = local_u(px, ra.x, rc.x, rd.x);
-        const float uy = local_u(py, ra.y, rc.y, rd.y);
-        const float uz = local_u(pz, ra.z, rc.z, rd.z);
-        monomials<P>(ux, bx);
-        monomials<P>(uy, by);
-        monomials<P>(uz, bz);
-        float v, sh = 1.f;
-        if constexpr (SHADE) {
-          float dx[N], dy[N], dz[N], gu, gv, gw;
-          dmonomials<P>(ux, dx);
-          dmonomials<P>(uy, dy);
-          dmonomials<P>(uz, dz);
-          v = blk.eval_grad(bx, by, bz, dx, dy, dz, gu, gv, gw);
-          const float gx = gu * rd.x, gy = gv * rd.y, gz = gw * rd.z;   // world gradient: d/dx = iw d/du
-          const float gl = fmaf(gx, lx, fmaf(gy, ly, gz * lz));
-          const float gn = fmaxf(sqrtf(fmaf(gx, gx, fmaf(gy, gy, gz * gz))), prm.grad_eps);
-          sh = fmaxf(0.4f, fabsf(gl) / gn);
-        } else {
-          v = blk.eval(bx, by, bz);
-        }
-        // ... while compositing sample k-1
-        if (pend) {
-          if constexpr (SHADE)
-            composite_shaded(tfb, tfd, pv, pseg, psh, prm, C0, C1, C2, Tr);
-          else
-            composite(tfb, tfd, pv, pseg, prm, C0, C1, C2, Tr);
-          ++nsamp;
-          if (Tr <= tr_stop) break;
-        }
-        pend = true;
-        pv = v;
-        psh = sh;
-        pseg = seg;
-        t = tn;
-        if (++k >= kMaxSamplesPerRay) {
-          set_status(prm.status, kStatusTimeout);
-          break;
-        }
-      }
-    }
-    reinterpret_cast<float4 *>(prm.out)[(int64_t)j * prm.width + i] = make_float4(C0, C1, C2, 1.f - Tr);
-  }
-  // per-warp counters
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) {
-    nsamp += __shfl_down_sync(0xffffffffu, nsamp, o);
-    nlook += __shfl_down_sync(0xffffffffu, nlook, o);
-    nhit += __shfl_down_sync(0xffffffffu, nhit, o);
-  }
-  if (lane == 0) {
-    atomicAdd(prm.counters + kCntSamples, (unsigned long long)nsamp);
-    atomicAdd(prm.counters + kCntLookups, (unsigned long long)nlook);
-    atomicAdd(prm.counters + kCntRays, (unsigned long long)nhit);
-  }
-}
 
 }  // namespace
 
@@ -1117,46 +423,6 @@ cudaError_t launch_eval_grad(const lrvol_s *v, const float *pts, int64_t n, floa
   return cudaGetLastError();
 }
 
-template <int P, int FIELD, int STORE>
-cudaError_t launch_render_t(const RenderParams &prm, cudaStream_t s) {
-  const dim3 grid((unsigned)((prm.width + 15) / 16), (unsigned)((prm.row_end - prm.row_begin + 7) / 8));
-  k_render<P, FIELD, STORE><<<grid, 128, 0, s>>>(prm);
-  return cudaGetLastError();
-}
-
-template <int STORE>
-cudaError_t launch_render_s(const RenderParams &prm, int degree, int f, cudaStream_t s) {
-  if (f == 3) {  // scalar with gradient shading
-    switch (degree) {
-      case 1: return launch_render_t<1, 3, STORE>(prm, s);
-      case 2: return launch_render_t<2, 3, STORE>(prm, s);
-      case 3: return launch_render_t<3, 3, STORE>(prm, s);
-      default: return cudaErrorInvalidValue;
-    }
-  }
-  switch (degree * 3 + f) {
-    case 3: return launch_render_t<1, 0, STORE>(prm, s);
-    case 4: return launch_render_t<1, 1, STORE>(prm, s);
-    case 5: return launch_render_t<1, 2, STORE>(prm, s);
-    case 6: return launch_render_t<2, 0, STORE>(prm, s);
-    case 7: return launch_render_t<2, 1, STORE>(prm, s);
-    case 8: return launch_render_t<2, 2, STORE>(prm, s);
-    case 9: return launch_render_t<3, 0, STORE>(prm, s);
-    case 10: return launch_render_t<3, 1, STORE>(prm, s);
-    case 11: return launch_render_t<3, 2, STORE>(prm, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_render(const RenderParams &prm, int degree, int field, int storage, cudaStream_t s) {
-  const int f = field == kFieldShaded ? 3 : (field == LRVOL_FIELD_MAGNITUDE ? 1 : (field == LRVOL_FIELD_COMPONENT ? 2 : 0));
-  switch (storage) {
-    case LRVOL_STORE_F32: return launch_render_s<LRVOL_STORE_F32>(prm, degree, f, s);
-    case LRVOL_STORE_F16: return launch_render_s<LRVOL_STORE_F16>(prm, degree, f, s);
-    case LRVOL_STORE_BF16: return launch_render_s<LRVOL_STORE_BF16>(prm, degree, f, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
 
 // ----------------------------------------------------------------------------
 // Learned step sizes: features, BF16 tensor-core inference, FP32 training,
@@ -2630,70 +1896,6 @@ cudaError_t launch_streamline_error(const double *ref, const int32_t *rc, int rm
                                                              reinterpret_cast<const SLSample *>(app), ac, amax, n,
                                                              sums);
   return cudaGetLastError();
-}
-
-// ----------------------------------------------------------------------------
-// Scratch for lrvol_render_noalloc.  The render kernel needs a little global
-// memory beyond its inputs and outputs: three statistics counters and a status
-// word.  lrvol_render takes them from the handle; lrvol_render_noalloc takes
-// them from this file-scope array, so that the call itself allocates nothing.
-// Every GPU that loads the library holds these 256 bytes until the process
-// exits.  Host code must not pass the symbol itself to a kernel (on the host it
-// names a stand-in, not device memory): its device address is looked up once
-// per device below.
-// ----------------------------------------------------------------------------
-}  // namespace lrvol
-
-static __device__ __align__(256) unsigned long long g_render_scratch[lrvol::kStaticScratchWords];
-
-namespace lrvol {
-
-namespace {
-constexpr int kMaxDevices = 256;
-std::mutex g_scratch_mutex;
-unsigned long long *g_scratch_ptr[kMaxDevices] = {};
-}  // namespace
-
-// Device address of g_render_scratch on the current device; resolved on the
-// first call for that device, with that device current.
-cudaError_t static_scratch(unsigned long long **out) {
-  int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_scratch_mutex);
-  if (!g_scratch_ptr[dev]) {
-    void *ptr = nullptr;
-    e = cudaGetSymbolAddress(&ptr, g_render_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_ptr[dev] = static_cast<unsigned long long *>(ptr);
-  }
-  *out = g_scratch_ptr[dev];
-  return cudaSuccess;
-}
-
-// Same kernel as launch_render, with the counters and the status word in the
-// static scratch (cleared on the stream before the launch).
-cudaError_t launch_render_static(RenderParams prm, int degree, int field, int storage, cudaStream_t s,
-                                 unsigned long long *counters_out) {
-  unsigned long long *scratch = nullptr;
-  cudaError_t e = static_scratch(&scratch);
-  if (e != cudaSuccess) return e;
-  e = cudaMemsetAsync(scratch, 0, sizeof(unsigned long long) * kStaticScratchWords, s);
-  if (e != cudaSuccess) return e;
-  prm.counters = scratch;
-  prm.status = reinterpret_cast<uint32_t *>(scratch + kNumCounters);
-  e = launch_render(prm, degree, field, storage, s);
-  if (e != cudaSuccess) return e;
-  if (counters_out) {
-    // samples, lookups, rays hit, then the status word widened to 64 bits
-    e = cudaMemcpyAsync(counters_out, scratch + kCntSamples, sizeof(unsigned long long) * 3,
-                        cudaMemcpyDeviceToDevice, s);
-    if (e != cudaSuccess) return e;
-    e = cudaMemcpyAsync(counters_out + 3, scratch + kNumCounters, sizeof(unsigned long long),
-                        cudaMemcpyDeviceToDevice, s);
-  }
-  return e;
 }
 
 }  // namespace lrvol

@@ -26,9 +26,12 @@ enum { kCntSamples = 0, kCntLookups = 1, kCntRays = 2, kCntQueue = 3, kNumCounte
 
 // Static scratch of lrvol_render_noalloc: kNumCounters counters, then the
 // status word (in a 64-bit slot); 32 words = 256 bytes per device.  One call
-// needs kNumCounters + 1 words, whatever the image size.
+// uses kNumCounters + 1 words (72 bytes), whatever the image size.
 constexpr int kStaticScratchWords = 32;
+constexpr int kStaticScratchBytesPerCall = (kNumCounters + 1) * 8;
 static_assert(kNumCounters + 1 <= kStaticScratchWords, "static scratch too small for one render");
+static_assert(kStaticScratchBytesPerCall == 72 && kStaticScratchWords * 8 == 256,
+              "lrvol.h states 72 of 256 bytes per lrvol_render_noalloc call");
 constexpr int kMaxImageSide = 32768;  // largest width or height a render accepts
 
 // Element record, 4 x float4 = 64 bytes:
@@ -123,6 +126,13 @@ struct RenderParams {
   float grad_eps;         // shading: gradients below this count as none (1e-3 (vmax - vmin))
   unsigned long long *counters;
   uint32_t *status;
+  // lrvol_render_trace only (null / 0 in every product launch)
+  const int32_t *trace_pix;  // trace_n (i, j) pixel pairs
+  int64_t trace_n;
+  int trace_max;             // records kept per pixel
+  float4 *trace_rec;         // trace_n x trace_max (t, element id bits, value, segment)
+  int32_t *trace_count;      // per pixel: samples composited
+  float4 *trace_rgba;        // per pixel: the composited RGBA
   float4 tf[256];
 };
 
@@ -177,6 +187,7 @@ cudaError_t launch_lookup(const lrvol_s *v, const float *pts, int64_t n, uint32_
 cudaError_t launch_eval_grad(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s);
 cudaError_t launch_eval(const lrvol_s *v, const float *pts, int64_t n, float *out, cudaStream_t s);
 cudaError_t launch_render(const RenderParams &prm, int degree, int field, int storage, cudaStream_t s);
+cudaError_t launch_render_trace(const RenderParams &prm, int degree, int field, int storage, cudaStream_t s);
 cudaError_t launch_render_static(RenderParams prm, int degree, int field, int storage, cudaStream_t s,
                                  unsigned long long *counters_out);
 

@@ -25,7 +25,8 @@ NONE = 0xFFFFFFFF
 
 EXPORTED = ["lrvol_create", "lrvol_build_accel", "lrvol_build_accel_split", "lrvol_to_bezier", "lrvol_render",
             "lrvol_lookup", "lrvol_eval", "lrvol_eval_grad", "lrvol_get_bezier", "lrvol_stats",
-            "lrvol_status_string", "lrvol_last_error", "lrvol_destroy", "lrvol_render_noalloc", "lrvol_features",
+            "lrvol_status_string", "lrvol_last_error", "lrvol_destroy", "lrvol_render_noalloc",
+            "lrvol_render_trace", "lrvol_features",
             "lrvol_mlp_pack", "lrvol_mlp_infer", "lrvol_mlp_check", "lrvol_mlp_infer_timeout_test",
             "lrvol_mlp_scratch_floats", "lrvol_mlp_grad", "lrvol_mlp_train_step", "lrvol_labels",
             "lrvol_arena_create", "lrvol_arena_alloc", "lrvol_arena_free", "lrvol_arena_used",
@@ -124,6 +125,9 @@ def load(path: str = LIB_PATH):
         L.lrvol_to_bezier.argtypes = [vp, i32, vp]
         L.lrvol_render.restype = ctypes.c_int
         L.lrvol_render.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step), vp, vp]
+        L.lrvol_render_trace.restype = ctypes.c_int
+        L.lrvol_render_trace.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
+                                         vp, i64, i32, vp, vp, vp, vp]
         L.lrvol_render_noalloc.restype = ctypes.c_int
         L.lrvol_render_noalloc.argtypes = [vp, ctypes.POINTER(Camera), ctypes.POINTER(TF), ctypes.POINTER(Step),
                                            vp, vp, vp]
@@ -345,6 +349,27 @@ class Volume:
         _check(load().lrvol_render(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), ptr,
                                    _stream_ptr(stream)), "lrvol_render")
         return out
+
+    def render_trace(self, cam, tf, step, pixels, max_samples: int, stream=None):
+        """The render kernel's own samples for a pixel list (lrvol_render_trace).
+        pixels: (n, 2) int32 CUDA tensor of (i, j).  Returns (trace (n, max, 4)
+        float32: t, element id bits, value, segment; count (n,) int32;
+        rgba (n, 4) float32), all CUDA tensors."""
+        import torch
+        c = cam if isinstance(cam, Camera) else make_camera(cam)
+        t = tf if isinstance(tf, TF) else make_tf(tf)
+        s = step if isinstance(step, Step) else make_step(step)
+        if pixels.dim() != 2 or pixels.shape[1] != 2:
+            raise ValueError("pixels: expected n x 2 int32")
+        n = pixels.shape[0]
+        pp = _dev(pixels, torch.int32, 2 * n, "pixels", exact=True)
+        trace = torch.empty((n, max_samples, 4), dtype=torch.float32, device="cuda")
+        count = torch.empty(n, dtype=torch.int32, device="cuda")
+        rgba = torch.empty((n, 4), dtype=torch.float32, device="cuda")
+        _check(load().lrvol_render_trace(self._h, ctypes.byref(c), ctypes.byref(t), ctypes.byref(s), pp, n,
+                                         int(max_samples), trace.data_ptr(), count.data_ptr(), rgba.data_ptr(),
+                                         _stream_ptr(stream)), "lrvol_render_trace")
+        return trace, count, rgba
 
     def lookup(self, pts, out=None, stream=None):
         import torch

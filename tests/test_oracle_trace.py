@@ -211,3 +211,28 @@ def test_trace_matches_render_and_counts(cfg1, cfg1_oracle):
     tr2, cnt2, _, _ = cfg1_oracle.render_trace(cams[1], tf, step, pix, 400)
     np.testing.assert_array_equal(cnt, cnt2)
     np.testing.assert_array_equal(tr, tr2[:, :8])
+
+
+def test_coefficient_hull_bounds_the_blocks():
+    """The incidence hull used to scale per-sample tolerances contains every
+    Bernstein coefficient of the element (convex combination), and equals the
+    min / max of the coefficients found by a numpy support test."""
+    for vol in (V.load_config(1),
+                V.refined_ball((2, 2, 2), (3, 3, 3), centres=((0.3, 0.6, 0.45),), radii=(0.4, 0.2), ncomp=3,
+                               seed=4)):
+        O = Oracle(vol)
+        el = np.arange(0, vol.n_elem, max(1, vol.n_elem // 300))
+        hull = O.coefficient_hull(el)
+        B = O.bezier_blocks(el).reshape(len(el), vol.ncomp, -1)
+        scale = np.abs(vol.coef).max()
+        assert np.all(B.min(axis=2) >= hull[:, :, 0] - 1e-12 * scale)
+        assert np.all(B.max(axis=2) <= hull[:, :, 1] + 1e-12 * scale)
+        p = [int(x) for x in vol.deg]
+        kx, ky = vol.knots[:, :p[0] + 2], vol.knots[:, p[0] + 2:p[0] + p[1] + 4]
+        kz = vol.knots[:, p[0] + p[1] + 4:]
+        for r, e in enumerate(el[:40]):
+            b = vol.elem_box[e]
+            sup = ((kx[:, 0] <= b[0]) & (b[3] <= kx[:, -1]) & (ky[:, 0] <= b[1]) & (b[4] <= ky[:, -1]) &
+                   (kz[:, 0] <= b[2]) & (b[5] <= kz[:, -1]))
+            np.testing.assert_array_equal(hull[r, :, 0], vol.coef[sup].min(axis=0))
+            np.testing.assert_array_equal(hull[r, :, 1], vol.coef[sup].max(axis=0))
