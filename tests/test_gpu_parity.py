@@ -354,12 +354,13 @@ def _sample_pixels(cam, n, seed):
 @pytest.mark.slow
 def test_render_cfg2_full_size_sampled():
     """The benchmark configuration (1920x1080, Eq. 4, alpha_stop 0.99, 64^3 forest)
-    on sampled pixels, each recomputed by the oracle."""
+    on 1024 sampled pixels, each recomputed by the oracle (sample and look-up
+    counts of such pixels: test_gpu_trace)."""
     vol = V.load_config(2)
     tf, cam = V.config2_render()
     tf = _f32_tf(tf)
     step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
-    pix = _sample_pixels(cam, 48, 3)
+    pix = _sample_pixels(cam, 1024, 3)
     img, ref, st, ost = _render_pair(vol, Oracle(vol), cam, tf, step, blocks=(64, 64, 64), pixels=pix)
     assert _rmse(img, ref) <= RMSE_TOL
     assert st["samples"] > 0 and st["rays_hit"] > 0
@@ -379,7 +380,7 @@ def test_render_cfg3_full_size_sampled(field):
     else:
         tf.vmin, tf.vmax = -0.5, 1.5
         step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, field="component", component=0)
-    pix = _sample_pixels(cam, 40, 4)
+    pix = _sample_pixels(cam, 1024, 4)
     img, ref, st, ost = _render_pair(vol, Oracle(vol), cam, tf, step, blocks=(64, 64, 64), pixels=pix)
     assert _rmse(img, ref) <= RMSE_TOL
     assert np.abs(ref[:, 3]).max() > 0.05              # the sampled rays see the field

@@ -1,6 +1,8 @@
 """The frame server on the GPU: every frame in a mixed, overlapping batch is
 identical (bit for bit, with the same sample counts) to the same request
-rendered alone by lrvol_render; admission respects the arena and FIFO order;
+rendered alone by lrvol_render, and sampled pixels of served frames of every
+volume and mode (FP32 Eq. 4, FP16 |v|, fixed steps, learned steps) match the
+FP64 oracle (RMSE <= 1e-4); admission respects the arena and FIFO order;
 frames really overlap on the device; host copies and server-side learned
 steps give the same images as the plain calls."""
 import numpy as np
@@ -8,6 +10,7 @@ import pytest
 
 torch = pytest.importorskip("torch")
 
+from oracle.oracle import Oracle
 from paper_1707_01170_gb300 import learned as LS
 from paper_1707_01170_gb300 import lrvol as lv
 from paper_1707_01170_gb300 import serve
@@ -24,12 +27,42 @@ def _gpu():
     lv.load()
 
 
+RMSE_TOL = 1e-4
+
+
+def _rmse(a, b):
+    return float(np.sqrt(np.mean((np.asarray(a, np.float64) - np.asarray(b, np.float64)) ** 2)))
+
+
+def _oracle_pixels(vol, cam, tf, step, img, n, seed):
+    """n seeded pixels of a served image and the oracle's values there (the TF
+    rounded to FP32 as the library stores it; learned multipliers from the host)."""
+    rng = np.random.default_rng(seed)
+    pix = np.stack([rng.integers(0, cam.width, n), rng.integers(0, cam.height, n)], axis=1).astype(np.int32)
+    tf32 = V.TransferFunction(table=np.asarray(tf.table, np.float32).astype(np.float64), vmin=tf.vmin, vmax=tf.vmax)
+    if step.mode == "learned":
+        step = V.StepParams(**{**step.__dict__, "mult": step.mult.cpu().numpy()})
+    ref, _ = Oracle(vol).render(cam, tf32, step, pixels=pix)
+    got = img.cpu().numpy()[pix[:, 1], pix[:, 0]]
+    return got, ref
+
+
+_VOLS = {}
+
+
+def _resident_volumes():
+    if not _VOLS:
+        _VOLS["v"] = [V.load_config(1),
+                      V.refined_ball((2, 2, 2), (3, 3, 3), centres=((0.3, 0.6, 0.45),), radii=(0.4, 0.2), ncomp=3,
+                                     seed=4),
+                      V.tensor_product((1, 1, 1), (5, 3, 4), seed=2)]
+    return _VOLS["v"]
+
+
 @pytest.fixture(scope="module")
 def resident():
     """Three resident volumes of different kinds, with TF and step each."""
-    v1 = V.load_config(1)
-    vec = V.refined_ball((2, 2, 2), (3, 3, 3), centres=((0.3, 0.6, 0.45),), radii=(0.4, 0.2), ncomp=3, seed=4)
-    tp = V.tensor_product((1, 1, 1), (5, 3, 4), seed=2)
+    v1, vec, tp = _resident_volumes()
     gvs = [lv.Volume(v1).build_accel((32, 32, 32)).to_bezier(),
            lv.Volume(vec).build_accel((16, 16, 16)).to_bezier(lv.STORE_F16),
            lv.Volume(tp).build_accel((8, 8, 8)).to_bezier()]
@@ -66,9 +99,49 @@ def test_mixed_batch_identical_to_alone(resident):
     # frames overlapped on the device: some pair of [start, end] intervals intersects
     iv = sorted((d["dev_start_ms"], d["dev_end_ms"]) for d in infos)
     assert any(iv[k + 1][0] < iv[k][1] for k in range(len(iv) - 1))
+    # served frames against the FP64 oracle: one frame per volume (FP32 Eq. 4,
+    # FP16 |v|, fixed step), 300 sampled pixels each
+    vols = _resident_volumes()
+    for v in range(3):
+        r, t = next((r, t) for r, t in zip(reqs, tickets) if r.volume == v)
+        got, ref = _oracle_pixels(vols[v], r.camera, tfs[v], steps[v], srv.image(t), 300, 40 + v)
+        assert _rmse(got, ref) <= RMSE_TOL, f"volume {v}"
+        assert np.abs(ref[:, 3]).max() > 0.01
     for t in tickets:
         srv.release(t)
     assert srv.stats()["arena_used"] == 0
+    srv.close()
+
+
+def test_served_learned_frames_against_oracle(resident):
+    """Learned-step requests (caller-supplied per-element multipliers) served
+    in a mix with plain ones: each equals the same request alone, and sampled
+    pixels match the oracle marching with the same multipliers."""
+    gvs, tfs, steps = resident
+    vols = _resident_volumes()
+    rng = np.random.default_rng(3)
+    cand = np.array([1, 1.5, 2, 3, 4, 6, 8], np.float32)
+    lsteps = [V.StepParams(mode="learned", xi=1 / 256, alpha_stop=0.99,
+                           mult=torch.from_numpy(rng.choice(cand, vols[0].n_elem)).cuda()),
+              V.StepParams(mode="learned", xi=1 / 128, field="magnitude",
+                           mult=torch.from_numpy(rng.choice(cand, vols[1].n_elem)).cuda())]
+    reqs = serve.request_stream(12, 12, 1000.0, 2, sizes=SMALL)
+    srv = lv.Server(slots=4, arena_bytes=64 << 20)
+    tickets = []
+    for k, r in enumerate(reqs):
+        tickets.append(srv.submit(gvs[r.volume], r.camera, tfs[r.volume], lsteps[r.volume]))
+        if k % 3 == 0:                                   # plain frames in the same mix
+            srv.submit(gvs[r.volume], r.camera, tfs[r.volume], steps[r.volume])
+    srv.drain()
+    checked = set()
+    for r, t in zip(reqs, tickets):
+        img = srv.image(t)
+        assert torch.equal(img, gvs[r.volume].render(r.camera, tfs[r.volume], lsteps[r.volume]))
+        if r.volume not in checked:
+            got, ref = _oracle_pixels(vols[r.volume], r.camera, tfs[r.volume], lsteps[r.volume], img, 300, 50)
+            assert _rmse(got, ref) <= RMSE_TOL, f"volume {r.volume}"
+            checked.add(r.volume)
+    assert checked == {0, 1}
     srv.close()
 
 
@@ -179,10 +252,17 @@ def test_full_size_mix_identical_to_alone():
     tickets = [srv.submit(gvs[r.volume], r.camera, tfs[r.volume], steps[r.volume]) for r in reqs]
     srv.drain()
     assert srv.stats()["max_running"] >= 2
+    checked = set()
     for r, t in zip(reqs, tickets):
         alone = gvs[r.volume].render(r.camera, tfs[r.volume], steps[r.volume])
-        assert torch.equal(srv.image(t), alone)
+        img = srv.image(t)
+        assert torch.equal(img, alone)
+        if r.volume not in checked:                     # one frame per volume against the oracle
+            got, ref = _oracle_pixels(vols[r.volume], r.camera, tfs[r.volume], steps[r.volume], img, 256, 60)
+            assert _rmse(got, ref) <= RMSE_TOL, f"volume {r.volume}"
+            checked.add(r.volume)
         srv.release(t)
+    assert checked == {0, 1, 2}
     srv.close()
     for g in gvs:
         g.close()
