@@ -87,6 +87,14 @@ WORKLOADS = {
 }
 
 
+def bench_config(workload: str, storage: str, ws: int) -> dict:
+    """The workload description both arms print (the reference arm runs the
+    same frame on the host)."""
+    return {"workload": WORKLOADS[workload] + f", forest {BLOCKS[0]}^3", "block_storage": storage,
+            "l2": "flushed between frames (512 MB write, outside the timed events)",
+            "parallelism": f"replicas x{ws}"}
+
+
 def flop_per_sample_shaded(p: int) -> int:
     """Gradient-shaded scalar sample: the scalar sample, plus the gradient
     contraction 2*((p+1)^3 + 2(p+1)^2 + 3(p+1)) reusing the value's partial
@@ -283,9 +291,9 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": val, "unit": "Gsamples/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload] + "; each step = 96 seeded pixels of the frame"},
+            "config": bench_config(args.workload, args.storage, args.gpus),
             "cpu_baseline": {"value": val, "unit": "Gsamples/s", "cores": orc.threads, "kind": "oracle",
-                             "sample": "96 seeded pixels per step"},
+                             "sample": "96 seeded pixels of the same frame per step (FP64 oracle)"},
             "e2e": {"value": val, "unit": "Gsamples/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
     return 0
@@ -341,7 +349,8 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
     rmse = lambda a, b: float(torch.sqrt(torch.mean((a.double() - b.double()) ** 2)))
     res = {"storage": storage, "fine_reference": "fixed step 1/2048, FP32 blocks, same alpha_stop",
            "gpu_launches_per_frame": 3, "frames_timed": steps,
-           "model": {"train_s": train_s, "rows": rows, "loss": losses[-1][1], "tau": model.cfg.tau,
+           "model": {"train_s": train_s, "rows": rows, "loss": losses[-1][1], "losses": losses,
+                     "train_info": getattr(model, "train_info", {}), "tau": model.cfg.tau,
                      "margin": model.cfg.margin, "ymax": model.cfg.ymax, "steps": model.cfg.steps,
                      "recipe": ("loaded from " + model_path) if model_path else
                      "32 seeded 320x180 cameras on each of configs 1 and 2"},
@@ -372,6 +381,8 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
         samples, lookups = lst["samples"], lst["lookups"]
         ms_feat, ms_net, ms_render = _timed_frames([feat_fn, net_fn, render_fn], steps, flush, stream)
         ms_mult = ms_feat + ms_net
+        if (w, h) == (WIDTH, HEIGHT):
+            res["ablation"] = LS.ablation(gq, ccam, ctf, step, model, fine, stream=stream)
         res["by_resolution"][f"{w}x{h}"] = {
             "ms_per_frame": ms_mult + ms_render, "ms_multipliers": ms_mult, "ms_features": ms_feat,
             "ms_network": ms_net, "ms_render": ms_render,
@@ -394,6 +405,70 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
     gq.close()
     res["_model"] = model
     return res
+
+
+def learned_summary(res: dict) -> dict:
+    """The headline comparison in a few hundred characters: per resolution the
+    learned + reduced-precision frame against the plain FP32 Eq. 4 frame
+    (ms/frame, RMSE against the fine-step reference, speed-up), and the
+    ablation against a constant multiplier and a per-element rule."""
+    r3 = lambda x: None if x is None else float(f"{x:.4g}")
+    out = {"storage": res["storage"]}
+    for k, v in res["by_resolution"].items():
+        out[k] = {"ms": r3(v["ms_per_frame"]), "rmse": r3(v["rmse_vs_fine"]),
+                  "plain_f32_ms": r3(v["plain_f32_ms_per_frame"]), "plain_f32_rmse": r3(v["plain_f32_rmse_vs_fine"]),
+                  "speedup": r3(v["speedup_vs_plain_f32"]),
+                  "samples_frac": r3(v["samples_per_frame"] / v["plain_f32_samples_per_frame"])}
+    ab = res.get("ablation")
+    if ab:
+        pick = lambda b: None if b is None else [b["param"], r3(b["samples_frac"]), r3(b["rmse"])]
+        out["ablation_1080p"] = {
+            "network": [r3(ab["network"]["samples_frac"]), r3(ab["network"]["rmse"])],
+            "empty_rule": [r3(ab["rule_empty_8x_else_1x"]["samples_frac"]), r3(ab["rule_empty_8x_else_1x"]["rmse"])],
+            "best_constant": pick(ab["best_constant_at_network_rmse"]),
+            "best_rule": pick(ab["best_rule_at_network_rmse"])}
+    out["network_us"] = r3(res["network"]["us_per_frame"])
+    return out
+
+
+def serving_summary(sv: dict) -> dict:
+    """p50 / p99 frame latency (ms) per mode and arrival rate."""
+    out = {}
+    for r in sv["runs"]:
+        key = "plain" if r["mode"].startswith("FP32") else "learned"
+        out.setdefault(key, {})[f"{r['rate_per_s']:g}/s"] = [float(f"{r['p50_ms']:.3g}"), float(f"{r['p99_ms']:.3g}")]
+    return out
+
+
+def vector_leg(flush, stream, frames: int):
+    """Config 3 (the wind-flow 3-vector volume) at 1920x1080 with Eq. 4 steps:
+    |v| and v_x with FP32, FP16 and BF16 blocks (per-block offset and scale,
+    FP32 accumulation).  Per run: ms/frame (L2 flushed between frames),
+    Gsamples/s, and the image's RMSE against the FP32-block image (the error
+    of each storage against the FP64 oracle is in the GPU tests)."""
+    import torch
+    from paper_1707_01170_gb300 import lrvol as lv
+    out = {}
+    for name, field in (("cfg3mag", "|v|"), ("cfg3x", "v_x")):
+        vol, tf, cam, step = _workload(name)
+        ccam, ctf, cstep = lv.make_camera(cam), lv.make_tf(tf), lv.make_step(step)
+        ref = None
+        for storage, code in (("f32", lv.STORE_F32), ("f16", lv.STORE_F16), ("bf16", lv.STORE_BF16)):
+            gv = lv.Volume(vol).build_accel(BLOCKS, stream=stream).to_bezier(code, stream=stream)
+            img = torch.empty((HEIGHT, WIDTH, 4), dtype=torch.float32, device="cuda")
+            for _ in range(3):
+                gv.render(ccam, ctf, cstep, out=img, stream=stream)
+            torch.cuda.synchronize()
+            n = gv.stats()["samples"]
+            ms = _timed_frames([lambda: gv.render(ccam, ctf, cstep, out=img, stream=stream)], frames, flush,
+                               stream)[0]
+            if ref is None:
+                ref = img.clone()
+            rm = float(torch.sqrt(torch.mean((img.double() - ref.double()) ** 2)))
+            out[f"{field} {storage}"] = {"ms": float(f"{ms:.4g}"), "gsamples_per_s": float(f"{n / ms / 1e6:.4g}"),
+                                         "rmse_vs_f32": float(f"{rm:.3g}")}
+            gv.close()
+    return out
 
 
 SL_RUNS = (("RK2", "heuristic", 1.0, 0.0), ("RK4", "heuristic", 1.0, 0.0), ("RKF5", "heuristic", 1.0, 0.0),
@@ -714,6 +789,8 @@ def run_ours(args):
 
     forest = forest_leg(stream) if (args.forest_sweep and ws == 1) else None
 
+    vector = vector_leg(flush, stream, max(3, min(args.steps, 30))) if (args.vector and ws == 1) else None
+
     serving = None
     if args.serve != "off" and ws == 1:
         modes = ["plain", "learned"] if args.serve == "both" else [args.serve]
@@ -792,31 +869,36 @@ def run_ours(args):
     line = {"metric": METRIC, "value": value, "unit": "Gsamples/s", "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload] + f", forest {BLOCKS[0]}^3",
-                       "block_storage": args.storage,
-                       "l2": "flushed between frames (512 MB write, outside the timed events)",
-                       "samples_per_frame": samples_per_frame, "rays_hit": st["rays_hit"],
-                       "lookups_per_frame": st["lookups"], "parallelism": f"replicas x{ws}"},
+            "config": bench_config(args.workload, args.storage, ws),
+            "frame": {"samples": samples_per_frame, "rays_hit": st["rays_hit"], "lookups": st["lookups"]},
             "wall_s": wall, "gpu_launches": args.steps,
             "roofline": roof, "e2e": e2e, "clocks": clk_summary,
             "setup": {"create_s": t1 - t0, "build_accel_s": t2 - t1, "to_bezier_s": t3 - t2,
                       "forest_depth": [st["depth_min"], st["depth_max"], st["depth_mean"], st["depth_var"]],
                       "n_nodes": st["n_nodes"], "incidence_entries": st["incidence_entries"]}}
+    # details first; the driver keeps the end of the line, so the headline
+    # comparison (learned_step) comes last and short
     if learned is not None:
         learned.pop("_model", None)
-        line["learned_step"] = learned
-    if shading is not None:
-        line["shading"] = shading
+        line["learned_step_detail"] = learned
+    if serving is not None:
+        line["serving_detail"] = serving
     if sl is not None:
         line["streamlines"] = sl
     if forest is not None:
         line["forest_sweep"] = forest
     if trimming is not None:
         line["trimming"] = trimming
-    if serving is not None:
-        line["serving"] = serving
+    if shading is not None:
+        line["shading"] = shading
     if not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline(vol, tf, cam, step, samples_per_frame)
+    if serving is not None:
+        line["serving"] = serving_summary(serving)
+    if vector is not None:
+        line["vector"] = vector
+    if learned is not None:
+        line["learned_step"] = learned_summary(learned)
     print(json.dumps(line))
     gv.close()
     if dist:
@@ -844,6 +926,8 @@ def main():
                     help="also time the frame for 1^3 .. 256^3 trees (the paper's look-up comparison)")
     ap.add_argument("--no-streamlines", dest="streamlines", action="store_false",
                     help="skip the streamline runs on config 3")
+    ap.add_argument("--no-vector", dest="vector", action="store_false",
+                    help="skip the config 3 |v| and v_x frames (FP32, FP16, BF16 blocks)")
     ap.add_argument("--sl-seeds", type=int, default=65536,
                     help="seeds of the streamline runs (a smaller rake makes a small profiling case)")
     args = ap.parse_args()

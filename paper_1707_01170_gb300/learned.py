@@ -74,6 +74,7 @@ class StepModel:
         self.cfg = cfg
         self.params = torch.as_tensor(np.asarray(params, dtype=np.float32)).cuda().contiguous()
         self._packed = None
+        self.train_info = {}
 
     @property
     def packed(self):
@@ -156,7 +157,7 @@ def train(X, target, cfg: TrainConfig, log_every: int = 0):
         # cosine decay from lr to lr_final
         lr = cfg.lr_final + 0.5 * (cfg.lr - cfg.lr_final) * (1 + np.cos(np.pi * (it - 1) / max(1, cfg.steps - 1)))
         lv.mlp_train_step(X[idx].contiguous(), target[idx].contiguous(), params, m, v, it, lr, scratch, loss)
-        if log_every and (it % log_every == 0 or it == cfg.steps):
+        if log_every and (it == 1 or it % log_every == 0 or it == cfg.steps):
             losses.append((it, float(loss.item())))
     if not losses:
         losses.append((cfg.steps, float(loss.item())))
@@ -178,6 +179,14 @@ def fit(volumes, step, cfg: TrainConfig | None = None, cams_per_volume: int = 32
         ts.append(t)
     X, t = torch.cat(Xs), torch.cat(ts)
     model, losses = train(X, t, cfg, log_every=log_every)
+    # what a loss near 0.25 means: half the variance of the targets is the
+    # loss of the best constant prediction; the labels' own spread (one
+    # element, several visits and cameras) puts a floor under any predictor
+    model.train_info = {"rows": int(X.shape[0]), "loss_first": losses[0][1], "loss_final": losses[-1][1],
+                        "loss_of_best_constant": float(0.5 * torch.var(t, unbiased=False)),
+                        "label_histogram": torch.bincount(
+                            torch.searchsorted(torch.log2(torch.tensor(cfg.cand, device="cuda")), t),
+                            minlength=len(cfg.cand)).tolist()}
     return model, losses, int(X.shape[0])
 
 
@@ -186,3 +195,75 @@ def training_cameras(seed: int, count: int, width: int, height: int):
     from .synth.volumes import orbit_camera
     st = Stream(seed, 4 * count + 16)
     return [orbit_camera(st, width, height) for _ in range(count)]
+
+
+# feature column of the largest TF opacity over the element's value range (lrvol.h)
+FEAT_ALPHA_MAX = 6
+
+
+def rule_multipliers(feat, theta: float, big: float, small: float):
+    """A one-line per-element rule on the features the network sees: the
+    multiplier `big` where the largest TF opacity over the element's value
+    range is at most theta (the element is (nearly) empty for this TF), else
+    `small`.  A baseline for the network, not used by the renderer."""
+    import torch
+    return torch.where(feat[:, FEAT_ALPHA_MAX] <= theta, big, small).to(torch.float32).contiguous()
+
+
+def ablation(gvol, cam, tf, step, model, fine, target: float = 1e-3, stream=None):
+    """Samples (as a fraction of Eq. 4's) and image RMSE against the fine-step
+    reference `fine` for: Eq. 4; every constant multiplier of the candidate
+    set; the empty-element rule (8x where the TF's largest opacity over the
+    element's range is 0, else 1x) and its tuned family (threshold theta,
+    multiplier c elsewhere); and the trained network.  For each family the
+    best member is the one with the fewest samples at RMSE <= target, and,
+    separately, at RMSE <= the network's own RMSE."""
+    import torch
+    from .synth.volumes import StepParams
+
+    def run(mult):
+        s = StepParams(mode="learned", xi=step.xi, alpha_stop=step.alpha_stop, field=step.field,
+                       component=step.component, mult=mult)
+        img = gvol.render(cam, tf, s, stream=stream)
+        n = gvol.stats()["samples"]
+        return n, float(torch.sqrt(torch.mean((img.double() - fine.double()) ** 2)))
+
+    heur = gvol.render(cam, tf, step, stream=stream)
+    n0 = gvol.stats()["samples"]
+    e0 = float(torch.sqrt(torch.mean((heur.double() - fine.double()) ** 2)))
+    feat = lv.features(gvol, cam, tf, step, stream=stream)
+    nel = feat.shape[0]
+    rows = {"eq4": (1.0, e0)}
+    consts = {}
+    for c in model.cfg.cand:
+        n, e = run(torch.full((nel,), float(c), dtype=torch.float32, device="cuda"))
+        consts[c] = (n / n0, e)
+    rules = {}
+    for theta in (0.0, 1e-3, 3e-3, 1e-2):
+        for c in model.cfg.cand[:4]:
+            n, e = run(rule_multipliers(feat, theta, float(max(model.cfg.cand)), float(c)))
+            rules[(theta, c)] = (n / n0, e)
+    n, e = run(model.multipliers(gvol, cam, tf, step, stream=stream))
+    rows["network"] = (n / n0, e)
+    rows["rule_empty_8x_else_1x"] = rules[(0.0, model.cfg.cand[0])]
+
+    def best(table, bar):
+        ok = [(v[0], k, v[1]) for k, v in table.items() if v[1] <= bar]
+        if not ok:
+            return None
+        f, k, e = min(ok)
+        return {"param": k, "samples_frac": f, "rmse": e}
+
+    e_net = rows["network"][1]
+    return {
+        "target_rmse": target, "eq4_samples": n0, "eq4_rmse": e0,
+        "network": {"samples_frac": rows["network"][0], "rmse": e_net},
+        "rule_empty_8x_else_1x": {"samples_frac": rows["rule_empty_8x_else_1x"][0],
+                                  "rmse": rows["rule_empty_8x_else_1x"][1]},
+        "best_constant_at_target": best(consts, target),
+        "best_constant_at_network_rmse": best(consts, e_net),
+        "best_rule_at_target": best(rules, target),
+        "best_rule_at_network_rmse": best(rules, e_net),
+        "constants": {str(k): {"samples_frac": v[0], "rmse": v[1]} for k, v in consts.items()},
+        "rules": {f"theta={k[0]:g},else={k[1]:g}": {"samples_frac": v[0], "rmse": v[1]} for k, v in rules.items()},
+    }

@@ -334,6 +334,33 @@ def test_trained_step_gain(trained, k, capsys):
         assert s_l <= 0.9 * s_h
 
 
+@pytest.mark.parametrize("k", [1, 2])
+def test_network_beats_constant_and_rule(trained, k, capsys):
+    """What the network learns beyond a rule: on a held-out view, the trained
+    network against (a) the best constant multiplier of the candidate set and
+    (b) per-element rules on the features it already computes (8x where the
+    TF's largest opacity over the element's value range is at most theta,
+    else a constant), each taken at its fewest samples with an image at least
+    as close to the fine-step reference as the network's."""
+    model, losses, gvs, tfs, step = trained
+    gv, tf = gvs[k], tfs[k]
+    cam = V.orbit_camera(Stream(4242 + k), 480, 270)
+    fine = gv.render(cam, tf, V.StepParams(mode="fixed", h=1 / 2048, xi=1 / 256, alpha_stop=0.99))
+    ab = LS.ablation(gv, cam, tf, step, model, fine)
+    with capsys.disabled():
+        print(f"\n[ablation, config {k}] Eq. 4 RMSE {ab['eq4_rmse']:.2e}; network "
+              f"{ab['network']['samples_frac']:.3f} of Eq. 4 samples at RMSE {ab['network']['rmse']:.2e}; "
+              f"empty-element rule {ab['rule_empty_8x_else_1x']}; best constant at the network's RMSE "
+              f"{ab['best_constant_at_network_rmse']}; best rule at the network's RMSE "
+              f"{ab['best_rule_at_network_rmse']}; train info {model.train_info}")
+    net = ab["network"]["samples_frac"]
+    for key in ("best_constant_at_network_rmse", "best_rule_at_network_rmse"):
+        other = ab[key]
+        assert other is None or net < other["samples_frac"], (key, other, net)
+    r = ab["rule_empty_8x_else_1x"]
+    assert r["rmse"] > ab["network"]["rmse"] or net < r["samples_frac"]
+
+
 def test_step_model_save_load(trained, tmp_path):
     model = trained[0]
     path = str(tmp_path / "step.bin")

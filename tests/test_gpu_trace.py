@@ -19,8 +19,9 @@ the same from oracle.c's march.  Bars:
                                transmittance (GPU) and FP64 opacity (oracle)
                                then decide differently; the shorter march
                                must end within 1e-4 of alpha_stop;
-  pixels                       RMSE <= 1e-4 against the oracle, and bit for
-                               bit equal to lrvol_render's image.
+  pixels                       RMSE <= 1e-4 against the oracle (5e-4 FP16,
+                               4e-3 BF16 blocks, as in test_gpu_precision),
+                               and bit for bit equal to lrvol_render's image.
 Covered: degrees 1-3; scalar, |v| and component fields; FP32, FP16 and BF16
 blocks; fixed, Eq. 4 and learned steps; gradient shading; config 1, a
 non-dyadic 3-vector volume, and >= 1000 hitting pixels of the full-size
@@ -40,7 +41,9 @@ from paper_1707_01170_gb300.synth import volumes as V
 pytestmark = pytest.mark.gpu
 
 VAL_TOL = 1e-5
-RMSE_TOL = 1e-4
+# image bars of test_gpu_precision: 1e-4 for FP32 blocks; 16-bit blocks add
+# their storage error (up to s u per sample) to every composited sample
+RMSE_TOL = {"f32": 1e-4, "f16": 5e-4, "bf16": 4e-3}
 U = {"f32": 0.0, "f16": 2.0 ** -11, "bf16": 2.0 ** -8}
 STORE = {"f32": lv.STORE_F32, "f16": lv.STORE_F16, "bf16": lv.STORE_BF16}
 CANDIDATES = np.array([1, 1.5, 2, 3, 4, 6, 8], np.float32)
@@ -139,7 +142,7 @@ def compare_traces(O, tf, step, storage, gpu, orc, exact_blocks=True):
     worst = int(np.argmax(err - tol))
     assert np.all(err <= tol), f"value {g[worst, 2]} vs {o[worst, 2]} (tol {tol[worst]:.3e}), element {elems[worst]}"
     rmse = float(np.sqrt(np.mean((grgba.astype(np.float64) - orgba) ** 2)))
-    assert rmse <= RMSE_TOL, rmse
+    assert rmse <= RMSE_TOL[storage], rmse
     return int(n.sum()), float((err / np.maximum(tol, 1e-30)).max())
 
 
