@@ -351,7 +351,8 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
            "gpu_launches_per_frame": 3, "frames_timed": steps,
            "model": {"train_s": train_s, "rows": rows, "loss": losses[-1][1], "losses": losses,
                      "train_info": getattr(model, "train_info", {}), "tau": model.cfg.tau,
-                     "margin": model.cfg.margin, "ymax": model.cfg.ymax, "steps": model.cfg.steps,
+                     "margin": model.cfg.margin, "ymin": model.cfg.ymin, "ymax": model.cfg.ymax,
+                     "candidates": list(model.cfg.cand), "steps": model.cfg.steps,
                      "recipe": ("loaded from " + model_path) if model_path else
                      "32 seeded 320x180 cameras on each of configs 1 and 2"},
            "by_resolution": {}}
@@ -369,7 +370,8 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
                                      steps, flush, stream)[0]
             samples_plain = gv32.stats()["samples"]
         feat_fn = lambda: lv.features(gq, ccam, ctf, step, out=feat, stream=stream)
-        net_fn = lambda: lv.mlp_infer(feat, model.packed, model.cfg.ymax, out=mult, stream=stream)
+        net_fn = lambda: lv.mlp_infer(feat, model.packed, model.cfg.ymax, out=mult, stream=stream,
+                                      ymin=model.cfg.ymin)
         render_fn = lambda: gq.render(ccam, ctf, lstep, out=out, stream=stream)
         for _ in range(3):
             feat_fn()
@@ -677,7 +679,7 @@ def serving_leg(model, modes, plan=SERVE_PLAN, slots: int = 8, arena_gb: int = 4
             srv = lv.Server(slots=slots, arena_bytes=arena_gb << 30)
             srv.set_priority_pixels(1 << 20)
             if mode != "plain":
-                srv.set_step_model(model.packed, model.cfg.ymax)
+                srv.set_step_model(model.packed, model.cfg.ymax, model.cfg.ymin)
             reqs = serve.request_stream(1707011700 + 5000 + int(rate), n, rate, 3)
             torch.cuda.synchronize()
             recs = serve.run_stream(srv, gvs, tfs, steps, reqs)

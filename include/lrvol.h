@@ -66,7 +66,12 @@ enum { LRVOL_SHADE_NONE = 0, LRVOL_SHADE_GRADIENT = 1 };
  *   ortho: o_c = fmaf(a, R_c, fmaf(b, U_c, E_c)); d = F
  *   slab test against [0,1]^3 from t = 0 gives [t_in, t_out); a miss writes 0.
  * Rows [row_begin, row_end) are rendered (both 0: all rows); other rows of
- * the output are left untouched.  This is the screen-space sharding hook. */
+ * the output are left untouched.  With band_count = n > 1 those rows are cut
+ * into bands of LRVOL_BAND_ROWS rows (the last one may be shorter) and only
+ * the bands b with b mod n == band_index are rendered (0 <= band_index < n),
+ * so n ranks with band_index 0..n-1 interleave their bands over the frame.
+ * These are the screen-space sharding hooks (Sec. 4's rays are independent). */
+#define LRVOL_BAND_ROWS 8
 typedef struct {
   int32_t projection; /* LRVOL_ORTHO | LRVOL_PERSP */
   int32_t width, height;
@@ -74,6 +79,7 @@ typedef struct {
   double fovy;   /* persp: full vertical field of view, radians */
   double extent; /* ortho: full height of the view window, world units */
   int32_t row_begin, row_end;
+  int32_t band_count, band_index; /* interleaved bands (0 or 1: every band) */
 } lrvol_camera;
 
 /* Transfer function: 256 RGBA entries spanning [vmin, vmax]; value v maps to
@@ -251,9 +257,10 @@ int lrvol_render_noalloc(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *t
 
 /* ---------------------------------------------------------------------------
  * Learned step sizes.  The paper's Eq. 4 step is multiplied per element by
- * m = 2^clamp(y, 0, ymax), y the output of a small network run once per
+ * m = 2^clamp(y, ymin, ymax), y the output of a small network run once per
  * element and frame on 16 block-local features; LRVOL_STEP_LEARNED renders
- * with these multipliers.  Network: 16 -> 64 -> 64 -> 64 -> 1, ReLU on the
+ * with these multipliers (ymin < 0 lets the network refine below Eq. 4 where
+ * Eq. 4 is too coarse for the transfer function, ymax > 0 lets it stretch).  Network: 16 -> 64 -> 64 -> 64 -> 1, ReLU on the
  * hidden layers.  FP32 master parameters (LRVOL_MLP_PARAMS floats) are laid
  * out W1[16][64], b1[64], W2[64][64], b2[64], W3[64][64], b3[64], W4[64], b4
  * (W[in][out], row major).  The paper has no learned component; Eq. 4 stays
@@ -291,17 +298,18 @@ int lrvol_features(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, con
 int lrvol_mlp_pack(const float *params_dev, uint16_t *packed_dev, void *stream);
 
 /* Network forward for n feature rows (device, n x 16); writes out_dev[n] =
- * 2^clamp(y, 0, ymax).  The three hidden layers run on the 5th-generation
+ * 2^clamp(y, ymin, ymax).  The three hidden layers run on the 5th-generation
  * tensor cores (tcgen05.mma kind::f16, BF16 operands, FP32 accumulators in
  * tensor memory, 128 rows per tile); the features and hidden activations are
  * rounded to BF16 as MMA operands, biases are added in FP32, and the 64 -> 1
  * output layer is an FP32 dot product of the BF16 activations and BF16 w4.
- * ymax in [0, 8]; packed_dev 16-byte aligned (it is read in 16-byte words).
+ * ymin in [-8, 0], ymax in [0, 8]; packed_dev 16-byte aligned (it is read in
+ * 16-byte words).
  * The kernel's waits for the tensor cores are bounded: if one runs out (not
  * expected), the rows of the tiles it leaves get multiplier 1 (the Eq. 4
  * step) and the library's network status records it for lrvol_mlp_check. */
-int lrvol_mlp_infer(const float *feat_dev, int64_t n, const uint16_t *packed_dev, float ymax, float *out_dev,
-                    void *stream);
+int lrvol_mlp_infer(const float *feat_dev, int64_t n, const uint16_t *packed_dev, float ymin, float ymax,
+                    float *out_dev, void *stream);
 
 /* Synchronises the device and reports the network status of every
  * lrvol_mlp_infer since the last check: LRVOL_OK, or LRVOL_ERR_TIMEOUT if a
@@ -312,8 +320,8 @@ int lrvol_mlp_check(void);
  * every tile's bounded wait runs out (after at most 0.1 s per wait) and
  * out_dev[0..n) becomes 1; lrvol_mlp_check then reports LRVOL_ERR_TIMEOUT.
  * n in 1 .. 2^20. */
-int lrvol_mlp_infer_timeout_test(const float *feat_dev, int64_t n, const uint16_t *packed_dev, float ymax,
-                                 float *out_dev, void *stream);
+int lrvol_mlp_infer_timeout_test(const float *feat_dev, int64_t n, const uint16_t *packed_dev, float ymin,
+                                 float ymax, float *out_dev, void *stream);
 
 /* FP32 training step of the network on a batch (device): loss = mean over
  * rows of (y - target)^2 / 2.  lrvol_mlp_grad writes the gradient
@@ -342,9 +350,10 @@ int lrvol_mlp_train_step(const float *x_dev, const float *target_dev, int64_t n,
  * becomes min(label_dev[e], the largest i such that candidates 1..i all have
  * error <= tau), so the caller initialises label_dev (n_elem int32) to
  * n_cand.  Needs to_bezier with LRVOL_STORE_F32 and build_accel.  cand_dev:
- * 1..8 increasing multipliers on the device (read back during the call),
- * cand[0] = 1 (always accepted).  A ray stops when its reference
- * transmittance is <= 1 - step->alpha_stop. */
+ * 1..16 increasing multipliers on the device (read back during the call);
+ * cand[0], the smallest, is always accepted (1 keeps every step at least the
+ * Eq. 4 step; a value below 1 lets labels ask for finer steps than Eq. 4).
+ * A ray stops when its reference transmittance is <= 1 - step->alpha_stop. */
 int lrvol_labels(lrvol_t vol, const lrvol_camera *cam, const lrvol_tf *tf, const lrvol_step *step, double h_fine,
                  double tau, const float *cand_dev, int32_t n_cand, int32_t *label_dev, void *stream);
 
@@ -538,8 +547,9 @@ int lrvol_server_create(int32_t slots, int64_t arena_bytes, lrvol_server_t *out)
  * mult == NULL: the server then runs lrvol_features and lrvol_mlp_infer for
  * the request's volume and camera before its render, on the same stream, with
  * the features and multipliers in the arena.  packed_dev (LRVOL_MLP_PACKED
- * uint16, 16-byte aligned) stays caller-owned and must outlive the server. */
-int lrvol_server_set_step_model(lrvol_server_t s, const uint16_t *packed_dev, float ymax);
+ * uint16, 16-byte aligned) stays caller-owned and must outlive the server;
+ * ymin and ymax as for lrvol_mlp_infer. */
+int lrvol_server_set_step_model(lrvol_server_t s, const uint16_t *packed_dev, float ymin, float ymax);
 /* Stream priority tiers by frame size: frames of at most max_pixels pixels
  * run at the device's greatest stream priority, frames of at most
  * 4 * max_pixels at a middle one, larger frames at the least, so the block

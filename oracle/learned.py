@@ -54,8 +54,9 @@ def forward(p, X, emulate_bf16: bool = False):
     return h @ r(w["W4"]) + f32(w["b4"])[0]
 
 
-def multipliers(p, X, ymax: float, emulate_bf16: bool = True):
-    return 2.0 ** np.clip(forward(p, X, emulate_bf16), 0.0, ymax)
+def multipliers(p, X, ymax: float, emulate_bf16: bool = True, ymin: float = 0.0):
+    """Step multipliers 2^clamp(y, ymin, ymax) of the network output y."""
+    return 2.0 ** np.clip(forward(p, X, emulate_bf16), ymin, ymax)
 
 
 def loss_and_grad(p, X, t):

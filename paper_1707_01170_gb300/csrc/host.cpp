@@ -369,6 +369,12 @@ int prepare_render(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *tf
   int r0 = cam->row_begin, r1 = cam->row_end;
   if (r0 == 0 && r1 == 0) r1 = cam->height;
   if (r0 < 0 || r1 > cam->height || r0 > r1) return fail(LRVOL_ERR_ARG, "bad row range");
+  const int nb = cam->band_count < 1 ? 1 : cam->band_count;
+  if (cam->band_count < 0 || cam->band_index < 0 || cam->band_index >= nb)
+    return fail(LRVOL_ERR_ARG, "bad interleaved band (need 0 <= band_index < band_count)");
+  // rows of this call's first band to the end: none when band_index is past the last band
+  const int n_bands = (r1 - r0 + LRVOL_BAND_ROWS - 1) / LRVOL_BAND_ROWS;
+  if (cam->band_index >= n_bands) r1 = r0;
   if (step->mode != LRVOL_STEP_FIXED && step->mode != LRVOL_STEP_HEURISTIC && step->mode != LRVOL_STEP_LEARNED)
     return fail(LRVOL_ERR_ARG, "bad step mode");
   if (step->mode == LRVOL_STEP_LEARNED && !step->mult) return fail(LRVOL_ERR_ARG, "learned steps need multipliers");
@@ -403,6 +409,8 @@ int prepare_render(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *tf
   prm->height = cam->height;
   prm->row_begin = r0;
   prm->row_end = r1;
+  prm->band_count = nb;
+  prm->band_index = r1 > r0 ? cam->band_index : 0;
   camera_consts(cam, &prm->ray);
   prm->mode = step->mode;
   prm->mult = step->mult;
@@ -706,25 +714,29 @@ int lrvol_mlp_pack(const float *params, uint16_t *packed, void *stream) {
   return LRVOL_OK;
 }
 
-int lrvol_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out, void *stream) {
+int lrvol_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymin, float ymax, float *out,
+                    void *stream) {
   if (n < 0 || (n > 0 && (!x || !packed || !out))) return fail(LRVOL_ERR_ARG, "bad arguments");
   if (!(ymax >= 0.f && ymax <= 8.f)) return fail(LRVOL_ERR_ARG, "ymax must be in [0, 8]");
+  if (!(ymin >= -8.f && ymin <= 0.f)) return fail(LRVOL_ERR_ARG, "ymin must be in [-8, 0]");
   if (n == 0) return LRVOL_OK;
   if (reinterpret_cast<uintptr_t>(packed) & 15) return fail(LRVOL_ERR_ARG, "packed weights must be 16-byte aligned");
   uint32_t *status = mlp_status_word();
   if (!status) return fail(LRVOL_ERR_CUDA, "network status word unavailable");
-  CU(launch_mlp_infer(x, n, packed, ymax, out, status, (cudaStream_t)stream), "mlp infer kernel");
+  CU(launch_mlp_infer(x, n, packed, ymin, ymax, out, status, (cudaStream_t)stream), "mlp infer kernel");
   return LRVOL_OK;
 }
 
-int lrvol_mlp_infer_timeout_test(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
-                                 void *stream) {
+int lrvol_mlp_infer_timeout_test(const float *x, int64_t n, const uint16_t *packed, float ymin, float ymax,
+                                 float *out, void *stream) {
   if (n < 1 || n > ((int64_t)1 << 20) || !x || !packed || !out) return fail(LRVOL_ERR_ARG, "bad arguments");
   if (!(ymax >= 0.f && ymax <= 8.f)) return fail(LRVOL_ERR_ARG, "ymax must be in [0, 8]");
+  if (!(ymin >= -8.f && ymin <= 0.f)) return fail(LRVOL_ERR_ARG, "ymin must be in [-8, 0]");
   if (reinterpret_cast<uintptr_t>(packed) & 15) return fail(LRVOL_ERR_ARG, "packed weights must be 16-byte aligned");
   uint32_t *status = mlp_status_word();
   if (!status) return fail(LRVOL_ERR_CUDA, "network status word unavailable");
-  CU(launch_mlp_infer(x, n, packed, ymax, out, status, (cudaStream_t)stream, true), "mlp infer kernel (timeout test)");
+  CU(launch_mlp_infer(x, n, packed, ymin, ymax, out, status, (cudaStream_t)stream, true),
+     "mlp infer kernel (timeout test)");
   return LRVOL_OK;
 }
 
@@ -768,13 +780,14 @@ int lrvol_labels(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   if (v->nc != 1 || v->storage != LRVOL_STORE_F32) return fail(LRVOL_ERR_UNSUPPORTED, "labels need a scalar FP32 volume");
   if (v->p[0] != v->p[1] || v->p[0] != v->p[2] || v->p[0] > 3)
     return fail(LRVOL_ERR_UNSUPPORTED, "labels need equal degrees 1..3");
-  if (n_cand < 1 || n_cand > 8 || !(h_fine > 0) || !(tau >= 0)) return fail(LRVOL_ERR_ARG, "bad label arguments");
+  if (n_cand < 1 || n_cand > 16 || !(h_fine > 0) || !(tau >= 0)) return fail(LRVOL_ERR_ARG, "bad label arguments");
   if (cam->width < 1 || cam->height < 1 || cam->width > 32768 || cam->height > 32768)
     return fail(LRVOL_ERR_ARG, "bad image size");
   if (!(step->xi > 0) || !(tf->vmax > tf->vmin)) return fail(LRVOL_ERR_ARG, "xi and vmax - vmin must be > 0");
-  float hc[8];
+  float hc[16];
+  static_assert(sizeof(hc) / sizeof(hc[0]) >= 16, "room for the largest candidate list");
   CU(cudaMemcpy(hc, cand, sizeof(float) * n_cand, cudaMemcpyDeviceToHost), "read candidates");
-  if (hc[0] != 1.f) return fail(LRVOL_ERR_ARG, "cand[0] must be 1");
+  if (!(hc[0] > 0.f)) return fail(LRVOL_ERR_ARG, "candidates must be positive");
   for (int q = 1; q < n_cand; ++q)
     if (!(hc[q] > hc[q - 1])) return fail(LRVOL_ERR_ARG, "candidates must increase");
   RenderParams prm;
@@ -788,6 +801,8 @@ int lrvol_labels(lrvol_t v, const lrvol_camera *cam, const lrvol_tf *tf, const l
   prm.height = cam->height;
   prm.row_begin = 0;
   prm.row_end = cam->height;
+  prm.band_count = 1;
+  prm.band_index = 0;
   camera_consts(cam, &prm.ray);
   prm.mode = LRVOL_STEP_HEURISTIC;
   prm.inv_xi = (float)(1.0 / step->xi);

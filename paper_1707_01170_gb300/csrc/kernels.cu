@@ -649,7 +649,8 @@ constexpr int kTcSmemBytes = 2 * kTcW4 + kTcGroups * 2 * (int)kTcM * kHid;   // 
 // kStatusTimeout.  no_mma (a diagnostic of that path) issues no MMAs and no
 // commits, so every pipeline's first wait runs out.
 __global__ void __launch_bounds__(128 * kTcGroups, 4) k_mlp_infer(const float *__restrict__ x, int64_t n,
-                                                               const uint16_t *__restrict__ packed, float ymax,
+                                                               const uint16_t *__restrict__ packed, float ymin,
+                                                               float ymax,
                                                                float *__restrict__ out, uint32_t *__restrict__ status,
                                                                bool no_mma) {
   extern __shared__ __align__(1024) unsigned char tc_smem[];
@@ -746,7 +747,7 @@ __global__ void __launch_bounds__(128 * kTcGroups, 4) k_mlp_infer(const float *_
       }
     }
     if (!ok) break;
-    if (row < n) out[row] = exp2f(fminf(fmaxf(y, 0.f), ymax));
+    if (row < n) out[row] = exp2f(fminf(fmaxf(y, ymin), ymax));
   }
   if (!ok) {
     if (gt == 0) set_status(status, kStatusTimeout);
@@ -973,7 +974,7 @@ uint32_t *mlp_status_word() {
   return cudaGetSymbolAddress(&p, g_mlp_status) == cudaSuccess ? static_cast<uint32_t *>(p) : nullptr;
 }
 
-cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
+cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymin, float ymax, float *out,
                              uint32_t *status, cudaStream_t s, bool no_mma) {
   static int sms = 0;
   if (sms == 0) {
@@ -992,8 +993,8 @@ cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, 
   // tensor memory (128 columns each) never exceeds the SM's 512 columns.
   const int64_t tiles = (n + kTcM - 1) / kTcM;
   const int64_t blocks = std::min<int64_t>((tiles + kTcGroups - 1) / kTcGroups, 4 * (int64_t)sms);
-  k_mlp_infer<<<(unsigned)std::max<int64_t>(blocks, 1), 128 * kTcGroups, kTcSmemBytes, s>>>(x, n, packed, ymax, out,
-                                                                                           status, no_mma);
+  k_mlp_infer<<<(unsigned)std::max<int64_t>(blocks, 1), 128 * kTcGroups, kTcSmemBytes, s>>>(x, n, packed, ymin, ymax,
+                                                                                           out, status, no_mma);
   return cudaGetLastError();
 }
 

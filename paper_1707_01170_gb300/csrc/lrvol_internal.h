@@ -115,6 +115,7 @@ struct RenderParams {
   ForestView forest;
   float *out;
   int width, height, row_begin, row_end;
+  int band_count, band_index;  // interleaved LRVOL_BAND_ROWS-row bands (count >= 1)
   RayConsts ray;
   int mode;               // LRVOL_STEP_*
   const float *mult;      // LEARNED: per-element step multipliers
@@ -295,7 +296,7 @@ int prepare_features(const lrvol_s *v, const lrvol_camera *cam, const lrvol_tf *
 cudaError_t launch_mlp_pack(const float *params, uint16_t *packed, cudaStream_t s);
 // status: device word that records LRVOL_ERR_TIMEOUT-class failures (kStatusTimeout) of the kernel's bounded waits
 // no_mma: diagnostic of the timeout path (no MMAs issued, every wait runs out)
-cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymax, float *out,
+cudaError_t launch_mlp_infer(const float *x, int64_t n, const uint16_t *packed, float ymin, float ymax, float *out,
                              uint32_t *status, cudaStream_t s, bool no_mma = false);
 // the library's status word for lrvol_mlp_infer calls (device address)
 uint32_t *mlp_status_word();

@@ -12,6 +12,8 @@
 
 #include "device_common.cuh"
 
+static_assert(LRVOL_BAND_ROWS == 8, "a CTA renders 8 rows: one interleaved band");
+
 namespace lrvol {
 namespace {
 
@@ -66,7 +68,7 @@ __global__ void __launch_bounds__(128, (FIELD == 3 && P == 3) ? 3 : 4) k_render(
     }
   } else {
     i = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    j = prm.row_begin + blockIdx.y * 8 + (warp >> 1) * 4 + (lane >> 3);
+    j = prm.row_begin + (blockIdx.y * prm.band_count + prm.band_index) * 8 + (warp >> 1) * 4 + (lane >> 3);
     active = i < prm.width && j < prm.row_end;
   }
   unsigned nsamp = 0, nlook = 0, nhit = 0;
@@ -196,7 +198,10 @@ cudaError_t launch_render_t(const RenderParams &prm, cudaStream_t s) {
   if constexpr (TRACE) {
     k_render<P, FIELD, STORE, true><<<(unsigned)((prm.trace_n + 127) / 128), 128, 0, s>>>(prm);
   } else {
-    const dim3 grid((unsigned)((prm.width + 15) / 16), (unsigned)((prm.row_end - prm.row_begin + 7) / 8));
+    // this call's bands: band_index, band_index + band_count, ... of the 8-row bands
+    const int n_bands = (prm.row_end - prm.row_begin + 7) / 8;
+    const int mine = (n_bands - prm.band_index + prm.band_count - 1) / prm.band_count;
+    const dim3 grid((unsigned)((prm.width + 15) / 16), (unsigned)mine);
     k_render<P, FIELD, STORE, false><<<grid, 128, 0, s>>>(prm);
   }
   return cudaGetLastError();

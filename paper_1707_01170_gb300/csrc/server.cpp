@@ -141,7 +141,7 @@ struct lrvol_server_s {
   int running = 0, max_running = 0;
   int running_tier[kTiers] = {0, 0, 0};
   const uint16_t *packed = nullptr;
-  float ymax = 0.f;
+  float ymin = 0.f, ymax = 0.f;
   int64_t priority_pixels = 0;  // tier 0 up to this many pixels, tier 1 up to 4 times as many, else tier 2
   int large_cap = 0;            // most frames of the last tier in flight (0: slots - max(1, slots/4))
 };
@@ -182,8 +182,8 @@ int launch_request(lrvol_server_s *s, Request &r, int k) {
     int rc = prepare_features(r.vol, &r.cam, &r.tf, &step, &fp);
     if (rc) return rc;
     CU(launch_features(fp, feat, st), "server: features kernel");
-    CU(launch_mlp_infer(feat, r.vol->n_elem, s->packed, s->ymax, mult, reinterpret_cast<uint32_t *>(sl.d_scratch + 64),
-                        st),
+    CU(launch_mlp_infer(feat, r.vol->n_elem, s->packed, s->ymin, s->ymax, mult,
+                        reinterpret_cast<uint32_t *>(sl.d_scratch + 64), st),
        "server: network kernel");
     step.mult = mult;
   }
@@ -369,11 +369,13 @@ int lrvol_server_create(int32_t slots, int64_t arena_bytes, lrvol_server_t *out)
   return LRVOL_OK;
 }
 
-int lrvol_server_set_step_model(lrvol_server_t s, const uint16_t *packed_dev, float ymax) {
+int lrvol_server_set_step_model(lrvol_server_t s, const uint16_t *packed_dev, float ymin, float ymax) {
   if (!s || !packed_dev) return fail(LRVOL_ERR_ARG, "null pointer");
   if (reinterpret_cast<uintptr_t>(packed_dev) & 15) return fail(LRVOL_ERR_ARG, "packed weights must be 16-byte aligned");
   if (!(ymax >= 0.f && ymax <= 8.f)) return fail(LRVOL_ERR_ARG, "ymax must be in [0, 8]");
+  if (!(ymin >= -8.f && ymin <= 0.f)) return fail(LRVOL_ERR_ARG, "ymin must be in [-8, 0]");
   s->packed = packed_dev;
+  s->ymin = ymin;
   s->ymax = ymax;
   return LRVOL_OK;
 }

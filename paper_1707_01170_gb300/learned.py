@@ -1,7 +1,7 @@
 """Learned step sizes: training on the GPU and per-frame multipliers.
 
 The Eq. 4 step ds(e) of element e is multiplied by m_e = 2^clamp(y_e - margin,
-0, ymax), with y_e the output of the 16-64-64-64-1 network declared in
+ymin, ymax), with y_e the output of the 16-64-64-64-1 network declared in
 lrvol.h, run on the block-local features of e for the frame's camera and
 transfer function.  Eq. 4 stays the fallback (every m_e = 1).
 
@@ -25,8 +25,11 @@ from . import lrvol as lv
 from .synth.lrgen import Stream
 
 CAND = (1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0)
+# candidates of the refining recipe: also steps below Eq. 4 (m >= 1/2), for
+# volumes and transfer functions where Eq. 4 itself is too coarse
+CAND_REFINE = (0.5, 0.75, 1.0, 1.5, 2.0, 3.0, 4.0, 6.0, 8.0)
 MAGIC = b"LRVOLMLP"
-FORMAT_VERSION = 1
+FORMAT_VERSION = 2
 
 # parameter layout of lrvol.h: W1[16][64], b1, W2[64][64], b2, W3[64][64], b3, W4[64], b4
 _IN, _HID = lv.MLP_IN, lv.MLP_HIDDEN
@@ -45,7 +48,16 @@ class TrainConfig:
     lr_final: float = 1e-4
     margin: float = 0.25         # subtracted from y at inference (conservative bias)
     ymax: float = 3.0            # log2 of the largest multiplier
+    ymin: float = 0.0            # log2 of the smallest multiplier (< 0: steps below Eq. 4)
     extra: dict = field(default_factory=dict)
+
+
+def refine_config(**kw) -> TrainConfig:
+    """The refining recipe: candidates from 1/2 to 8 and multipliers clamped
+    to [2^-1, 2^3], so the network can also ask for steps finer than Eq. 4
+    where the Eq. 4 step misses the error bar.  The default recipe (steps at
+    least Eq. 4's) is faster where Eq. 4 already meets it."""
+    return TrainConfig(cand=CAND_REFINE, ymin=-1.0, **kw)
 
 
 def init_params(seed: int) -> np.ndarray:
@@ -90,12 +102,12 @@ class StepModel:
     def multipliers(self, gvol, cam, tf, step, feat=None, out=None, stream=None):
         """Per-element step multipliers for one frame (float32 CUDA tensor, n_elem)."""
         feat = lv.features(gvol, cam, tf, step, out=feat, stream=stream)
-        return lv.mlp_infer(feat, self.packed, self.cfg.ymax, out=out, stream=stream)
+        return lv.mlp_infer(feat, self.packed, self.cfg.ymax, out=out, stream=stream, ymin=self.cfg.ymin)
 
     def save(self, path: str) -> None:
         c = self.cfg
-        head = struct.pack("<8sIIdddddI", MAGIC, FORMAT_VERSION, lv.MLP_PARAMS, c.h_fine, c.tau, c.margin, c.ymax,
-                           float(c.seed), len(c.cand))
+        head = struct.pack("<8sIIddddddI", MAGIC, FORMAT_VERSION, lv.MLP_PARAMS, c.h_fine, c.tau, c.margin, c.ymin,
+                           c.ymax, float(c.seed), len(c.cand))
         with open(path, "wb") as f:
             f.write(head)
             f.write(np.asarray(c.cand, dtype="<f4").tobytes())
@@ -105,15 +117,15 @@ class StepModel:
     def load(cls, path: str) -> "StepModel":
         with open(path, "rb") as f:
             data = f.read()
-        fmt = "<8sIIdddddI"
+        fmt = "<8sIIddddddI"
         n0 = struct.calcsize(fmt)
-        magic, ver, npar, h_fine, tau, margin, ymax, seed, ncand = struct.unpack(fmt, data[:n0])
+        magic, ver, npar, h_fine, tau, margin, ymin, ymax, seed, ncand = struct.unpack(fmt, data[:n0])
         if magic != MAGIC or ver != FORMAT_VERSION or npar != lv.MLP_PARAMS:
             raise ValueError(f"{path}: not a step model of format {FORMAT_VERSION} with {lv.MLP_PARAMS} parameters")
         cand = np.frombuffer(data, dtype="<f4", count=ncand, offset=n0)
         params = np.frombuffer(data, dtype="<f4", count=npar, offset=n0 + 4 * ncand)
         cfg = TrainConfig(seed=int(seed), h_fine=h_fine, tau=tau, cand=tuple(float(x) for x in cand), margin=margin,
-                          ymax=ymax)
+                          ymin=ymin, ymax=ymax)
         return cls(params.copy(), cfg)
 
 

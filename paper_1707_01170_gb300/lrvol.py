@@ -39,6 +39,7 @@ REQ_QUEUED, REQ_RUNNING, REQ_DONE, REQ_FAILED = 0, 1, 2, 3
 SL_METHODS = ["RK1", "RK2", "RK3", "RK4", "RK38", "RKF5", "HE", "BS", "RKF45"]
 SL_RULES = ["fixed", "heuristic", "adaptive"]
 MLP_IN, MLP_HIDDEN, MLP_PARAMS, MLP_PACKED = 16, 64, 9473, 10120
+BAND_ROWS = 8
 
 
 class LrvolError(RuntimeError):
@@ -51,7 +52,8 @@ class Camera(ctypes.Structure):
     _fields_ = [("projection", ctypes.c_int32), ("width", ctypes.c_int32), ("height", ctypes.c_int32),
                 ("eye", ctypes.c_double * 3), ("target", ctypes.c_double * 3), ("up", ctypes.c_double * 3),
                 ("fovy", ctypes.c_double), ("extent", ctypes.c_double),
-                ("row_begin", ctypes.c_int32), ("row_end", ctypes.c_int32)]
+                ("row_begin", ctypes.c_int32), ("row_end", ctypes.c_int32),
+                ("band_count", ctypes.c_int32), ("band_index", ctypes.c_int32)]
 
 
 class TF(ctypes.Structure):
@@ -152,11 +154,11 @@ def load(path: str = LIB_PATH):
         L.lrvol_mlp_pack.restype = ctypes.c_int
         L.lrvol_mlp_pack.argtypes = [vp, vp, vp]
         L.lrvol_mlp_infer.restype = ctypes.c_int
-        L.lrvol_mlp_infer.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
+        L.lrvol_mlp_infer.argtypes = [vp, i64, vp, ctypes.c_float, ctypes.c_float, vp, vp]
         L.lrvol_mlp_check.restype = ctypes.c_int
         L.lrvol_mlp_check.argtypes = []
         L.lrvol_mlp_infer_timeout_test.restype = ctypes.c_int
-        L.lrvol_mlp_infer_timeout_test.argtypes = [vp, i64, vp, ctypes.c_float, vp, vp]
+        L.lrvol_mlp_infer_timeout_test.argtypes = [vp, i64, vp, ctypes.c_float, ctypes.c_float, vp, vp]
         L.lrvol_mlp_scratch_floats.restype = i64
         L.lrvol_mlp_scratch_floats.argtypes = [i64]
         L.lrvol_mlp_grad.restype = ctypes.c_int
@@ -190,7 +192,7 @@ def load(path: str = LIB_PATH):
         L.lrvol_server_create.restype = ctypes.c_int
         L.lrvol_server_create.argtypes = [i32, i64, ctypes.POINTER(vp)]
         L.lrvol_server_set_step_model.restype = ctypes.c_int
-        L.lrvol_server_set_step_model.argtypes = [vp, vp, ctypes.c_float]
+        L.lrvol_server_set_step_model.argtypes = [vp, vp, ctypes.c_float, ctypes.c_float]
         L.lrvol_server_set_priority_pixels.restype = ctypes.c_int
         L.lrvol_server_set_priority_pixels.argtypes = [vp, i64]
         L.lrvol_server_set_large_cap.restype = ctypes.c_int
@@ -244,8 +246,9 @@ def _stream_ptr(stream) -> int | None:
     return getattr(stream, "cuda_stream", stream)
 
 
-def make_camera(cam, row_begin: int = 0, row_end: int = 0) -> Camera:
-    """From any object with projection ('ortho'|'persp'), width, height, eye, target, up, fovy, extent."""
+def make_camera(cam, row_begin: int = 0, row_end: int = 0, band_count: int = 0, band_index: int = 0) -> Camera:
+    """From any object with projection ('ortho'|'persp'), width, height, eye, target, up, fovy, extent;
+    optionally a row range and an interleaved band (every band_count-th 8-row band from band_index)."""
     c = Camera()
     c.projection = PERSP if cam.projection == "persp" else ORTHO
     c.width, c.height = int(cam.width), int(cam.height)
@@ -254,6 +257,7 @@ def make_camera(cam, row_begin: int = 0, row_end: int = 0) -> Camera:
     c.up = (ctypes.c_double * 3)(*[float(v) for v in cam.up])
     c.fovy, c.extent = float(cam.fovy), float(cam.extent)
     c.row_begin, c.row_end = int(row_begin), int(row_end)
+    c.band_count, c.band_index = int(band_count), int(band_index)
     return c
 
 
@@ -337,10 +341,11 @@ class Volume:
         _check(load().lrvol_to_bezier(self._h, int(storage), _stream_ptr(stream)), "lrvol_to_bezier")
         return self
 
-    def render(self, cam, tf, step, out=None, stream=None, row_begin: int = 0, row_end: int = 0):
+    def render(self, cam, tf, step, out=None, stream=None, row_begin: int = 0, row_end: int = 0,
+               band_count: int = 0, band_index: int = 0):
         """Render into a (H, W, 4) float32 CUDA tensor (allocated if out is None)."""
         import torch
-        c = cam if isinstance(cam, Camera) else make_camera(cam, row_begin, row_end)
+        c = cam if isinstance(cam, Camera) else make_camera(cam, row_begin, row_end, band_count, band_index)
         t = tf if isinstance(tf, TF) else make_tf(tf)
         s = step if isinstance(step, Step) else make_step(step)
         if out is None:
@@ -460,26 +465,27 @@ def mlp_pack(params, out=None, stream=None):
     return out
 
 
-def mlp_infer(x, packed, ymax: float, out=None, stream=None):
-    """Multipliers 2^clamp(y, 0, ymax) for feature rows x (n x 16); hidden layers on the tcgen05 tensor cores."""
+def mlp_infer(x, packed, ymax: float, out=None, stream=None, ymin: float = 0.0):
+    """Multipliers 2^clamp(y, ymin, ymax) for feature rows x (n x 16); hidden layers on the tcgen05 tensor cores."""
     import torch
     n = x.shape[0]
     if out is None:
         out = torch.empty(n, dtype=torch.float32, device="cuda")
     _check(load().lrvol_mlp_infer(_dev(x, torch.float32, n * MLP_IN, "features"), n,
-                                  _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymax),
+                                  _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymin), float(ymax),
                                   _dev(out, torch.float32, n, "multipliers out"), _stream_ptr(stream)), "lrvol_mlp_infer")
     return out
 
 
-def mlp_infer_timeout_test(x, packed, ymax: float, out=None, stream=None):
+def mlp_infer_timeout_test(x, packed, ymax: float, out=None, stream=None, ymin: float = 0.0):
     """Diagnostic: the network kernel with no MMAs issued, so its bounded waits run out."""
     import torch
     n = x.shape[0]
     if out is None:
         out = torch.empty(n, dtype=torch.float32, device="cuda")
     _check(load().lrvol_mlp_infer_timeout_test(_dev(x, torch.float32, n * MLP_IN, "features"), n,
-                                               _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymax),
+                                               _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymin),
+                                               float(ymax),
                                                _dev(out, torch.float32, n, "multipliers out"), _stream_ptr(stream)),
            "lrvol_mlp_infer_timeout_test")
     return out
@@ -587,11 +593,11 @@ class Server:
         self._h = h
         self._keep = {}   # ticket -> (camera, host buffer) kept alive while the request exists
 
-    def set_step_model(self, packed, ymax: float) -> None:
+    def set_step_model(self, packed, ymax: float, ymin: float = 0.0) -> None:
         self._model = packed
         import torch
-        _check(load().lrvol_server_set_step_model(self._h, _dev(packed, torch.int16, MLP_PACKED, "packed"), float(ymax)),
-               "lrvol_server_set_step_model")
+        _check(load().lrvol_server_set_step_model(self._h, _dev(packed, torch.int16, MLP_PACKED, "packed"),
+                                                  float(ymin), float(ymax)), "lrvol_server_set_step_model")
 
     def set_priority_pixels(self, max_pixels: int) -> None:
         _check(load().lrvol_server_set_priority_pixels(self._h, int(max_pixels)), "lrvol_server_set_priority_pixels")

@@ -111,7 +111,7 @@ def test_binding_constants_match_header(tmp_path):
              "ERR_STATE": "LRVOL_ERR_STATE", "ERR_BOUNDS": "LRVOL_ERR_BOUNDS", "ERR_TIMEOUT": "LRVOL_ERR_TIMEOUT",
              "ERR_UNSUPPORTED": "LRVOL_ERR_UNSUPPORTED", "ORTHO": "LRVOL_ORTHO", "PERSP": "LRVOL_PERSP",
              "MLP_IN": "LRVOL_MLP_IN", "MLP_HIDDEN": "LRVOL_MLP_HIDDEN", "MLP_PARAMS": "LRVOL_MLP_PARAMS",
-             "MLP_PACKED": "LRVOL_MLP_PACKED"}
+             "MLP_PACKED": "LRVOL_MLP_PACKED", "BAND_ROWS": "LRVOL_BAND_ROWS"}
     for group in ("STEP_FIXED STEP_HEURISTIC STEP_LEARNED", "FIELD_SCALAR FIELD_MAGNITUDE FIELD_COMPONENT",
                   "STORE_F32 STORE_F16 STORE_BF16", "SHADE_NONE SHADE_GRADIENT", "SPLIT_BALANCED SPLIT_MIDPOINT",
                   "REQ_QUEUED REQ_RUNNING REQ_DONE REQ_FAILED"):

@@ -411,17 +411,29 @@ def test_render_one_pixel_and_extreme_aspect(vols, oracles):
         assert _rmse(img, ref) <= RMSE_TOL
 
 
-def test_render_shards_reassemble(vols):
-    """Screen-space shards (row ranges of 3 ranks, rendered here in turn) give
-    the full frame bitwise."""
-    from paper_1707_01170_gb300.shard import render_shard
+@pytest.mark.parametrize("interleaved", [True, False])
+@pytest.mark.parametrize("world", [2, 3, 8])
+def test_render_shards_reassemble(vols, interleaved, world):
+    """Screen-space shards of `world` ranks (interleaved 8-row bands, or
+    contiguous row blocks), rendered here in turn, give the full frame
+    bitwise; each shard writes only its own rows."""
+    from paper_1707_01170_gb300.shard import render_shard, rows_of
     tf, cams = V.config1_render()
     cam = V.orbit_camera(V.Stream(9), 70, 53)
     step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99)
     gv = lv.Volume(vols["cfg1"]).build_accel((16, 16, 16)).to_bezier()
     full = gv.render(cam, tf, step)
     out = torch.full_like(full, -1.0)
-    for r in range(3):
-        render_shard(gv, cam, tf, step, out, world=3, rank=r)
+    for r in range(world):
+        one = torch.full_like(full, -1.0)
+        render_shard(gv, cam, tf, step, one, world=world, rank=r, interleaved=interleaved)
+        mine = torch.zeros(cam.height, dtype=torch.bool, device="cuda")
+        for a, b in rows_of(cam.height, world, r, interleaved):
+            mine[a:b] = True
+        assert bool(torch.all(one[~mine] == -1.0))
+        out[mine] = one[mine]
     assert torch.equal(out, full)
+    with pytest.raises(lv.LrvolError) as ei:
+        gv.render(cam, tf, step, band_count=2, band_index=2)
+    assert ei.value.status == lv.ERR_ARG
     gv.close()

@@ -180,7 +180,7 @@ def test_server_learned_steps_match_manual(resident, cfg1):
     gvs, tfs, steps = resident
     model = LS.StepModel(LS.init_params(5), LS.TrainConfig(margin=-1.5))
     srv = lv.Server(slots=3, arena_bytes=64 << 20)
-    srv.set_step_model(model.packed, model.cfg.ymax)
+    srv.set_step_model(model.packed, model.cfg.ymax, model.cfg.ymin)
     cams = [serve.orbit_view(0, k, 1, 160, 90) for k in range(5)]
     lstep = V.StepParams(mode="learned", xi=1 / 256, alpha_stop=0.99)
     tickets = [srv.submit(gvs[0], c, tfs[0], lstep) for c in cams]

@@ -209,6 +209,10 @@ def test_multipliers_clamp_the_exponent():
     for b4, ymax, want in ((-1.5, 3.0, 1.0), (1.5, 3.0, 2 ** 1.5), (5.0, 3.0, 8.0), (0.0, 0.0, 1.0)):
         p[-1] = b4
         np.testing.assert_allclose(OL.multipliers(p, X, ymax), [want], rtol=1e-15)
+    # a lower clamp below zero lets the multiplier refine below Eq. 4
+    for b4, ymin, want in ((-1.5, -2.0, 2 ** -1.5), (-3.0, -2.0, 0.25), (0.5, -1.0, 2 ** 0.5)):
+        p[-1] = b4
+        np.testing.assert_allclose(OL.multipliers(p, X, 3.0, ymin=ymin), [want], rtol=1e-15)
 
 
 def test_hand_pin_catches_planted_forward_mistakes():
