@@ -233,19 +233,29 @@ def cpu_baseline(vol, tf, cam, step, samples_per_frame=None, target_s: float = 1
     return out
 
 
+RENDER_SOURCES = ("render.cu", "device_common.cuh", "lrvol_internal.h")
+
+
+def render_source_hash(root: str | None = None) -> str:
+    """sha256 (16 hex digits) of the files that define k_render."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in RENDER_SOURCES:
+        h.update(open(os.path.join(root or ROOT, "paper_1707_01170_gb300", "csrc", name), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def profiled_counters():
     """DRAM and L2 bytes per k_render launch from the committed ncu summary,
-    if the kernel source is unchanged since that capture; else None."""
-    import hashlib
+    if the render kernel's source is unchanged since that capture; else None."""
     try:
         prof = open(os.path.join(ROOT, "profiles", "k_render_cfg2_1080p.md")).read()
-        src = open(os.path.join(ROOT, "paper_1707_01170_gb300", "csrc", "kernels.cu"), "rb").read()
+        sha = render_source_hash()
     except OSError:
         return None
-    sha = hashlib.sha256(src).hexdigest()[:16]
     fields = dict(ln.strip().split(": ", 1) for ln in prof.splitlines() if ln.strip().startswith(
-        ("kernels_cu_sha256_16:", "traffic_bytes_per_launch:", "l2_bytes_per_launch:")))
-    if fields.get("kernels_cu_sha256_16") != sha:
+        ("render_source_sha256_16:", "traffic_bytes_per_launch:", "l2_bytes_per_launch:")))
+    if fields.get("render_source_sha256_16") != sha:
         return None
     return {"traffic": int(fields["traffic_bytes_per_launch"]), "l2": int(fields.get("l2_bytes_per_launch", 0)) or None}
 

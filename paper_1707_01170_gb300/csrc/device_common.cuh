@@ -23,10 +23,14 @@ __device__ __forceinline__ void set_status(uint32_t *status, uint32_t code) { at
 // look-up (Alg. 1)
 // ----------------------------------------------------------------------------
 
+// Element holding the FP32 point (x, y, z), each coordinate in [0, 1] (every
+// caller clamps or checks first): head word of its block, then the tree walk.
 __device__ __forceinline__ uint32_t forest_lookup(const ForestView &f, float x, float y, float z, uint32_t *status) {
-  const int bx = min((int)(x * f.fbx), f.bx - 1);
-  const int by = min((int)(y * f.fby), f.by - 1);
-  const int bz = min((int)(z * f.fbz), f.bz - 1);
+  // block index floor(p * blocks) (0 <= p <= 1, blocks <= 1024) as 2^23 + floor
+  // by a round-down add, without a float-int conversion
+  const int bx = min(__float_as_int(__fadd_rd(x * f.fbx, 8388608.f)) - 0x4b000000, f.bx - 1);
+  const int by = min(__float_as_int(__fadd_rd(y * f.fby, 8388608.f)) - 0x4b000000, f.by - 1);
+  const int bz = min(__float_as_int(__fadd_rd(z * f.fbz, 8388608.f)) - 0x4b000000, f.bz - 1);
   uint32_t w = __ldg(f.head + ((int64_t)bz * f.by + by) * f.bx + bx);
   for (int depth = 0; !(w & kLeaf); ++depth) {
     if ((int64_t)w >= f.n_nodes || depth >= kMaxDepth) {
@@ -176,8 +180,11 @@ __device__ __forceinline__ bool make_ray(const RayConsts &K, int i, int j, Ray &
 __device__ __forceinline__ void composite(const float4 *tfb, const float4 *tfd, float v, float seg,
                                           const RenderParams &prm, float &C0, float &C1, float &C2, float &Tr) {
   const float x = fminf(fmaxf(fmaf(v, prm.tf_scale, prm.tf_bias), 0.f), 255.f);
-  const int q = min((int)x, 254);
-  const float fr = x - (float)q;
+  // floor(x) without a float-int conversion (those issue on the narrow XU
+  // pipe): adding 2^23 rounding down leaves 2^23 + floor(x) exactly
+  const float r = __fadd_rd(x, 8388608.f);
+  const int q = min(__float_as_int(r) - 0x4b000000, 254);
+  const float fr = x - fminf(__fsub_rn(r, 8388608.f), 254.f);
   const float4 e0 = tfb[q], de = tfd[q];
   const float sa = fmaf(fr, de.w, e0.w);
   const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (seg * prm.inv_xi));
@@ -193,8 +200,11 @@ __device__ __forceinline__ void composite_shaded(const float4 *tfb, const float4
                                                  const RenderParams &prm, float &C0, float &C1, float &C2,
                                                  float &Tr) {
   const float x = fminf(fmaxf(fmaf(v, prm.tf_scale, prm.tf_bias), 0.f), 255.f);
-  const int q = min((int)x, 254);
-  const float fr = x - (float)q;
+  // floor(x) without a float-int conversion (those issue on the narrow XU
+  // pipe): adding 2^23 rounding down leaves 2^23 + floor(x) exactly
+  const float r = __fadd_rd(x, 8388608.f);
+  const int q = min(__float_as_int(r) - 0x4b000000, 254);
+  const float fr = x - fminf(__fsub_rn(r, 8388608.f), 254.f);
   const float4 e0 = tfb[q], de = tfd[q];
   const float sa = fmaf(fr, de.w, e0.w);
   const float T = ex2_approx(lg2_approx(fmaxf(1.f - sa, 0.f)) * (seg * prm.inv_xi));

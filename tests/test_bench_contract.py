@@ -36,20 +36,21 @@ def _bench_module():
 
 def test_traffic_record_is_used_only_for_the_captured_source(tmp_path, monkeypatch):
     """The roofline's ncu traffic comes from the committed k_render summary
-    only while kernels.cu still has the hash that summary records."""
-    import hashlib
+    only while the render kernel's sources still have the hash that summary
+    records."""
     b = _bench_module()
     (tmp_path / "profiles").mkdir()
     src = tmp_path / "paper_1707_01170_gb300" / "csrc"
     src.mkdir(parents=True)
-    (src / "kernels.cu").write_bytes(b"// kernel source A\n")
-    sha = hashlib.sha256(b"// kernel source A\n").hexdigest()[:16]
+    for name in b.RENDER_SOURCES:
+        (src / name).write_bytes(b"// source A of " + name.encode() + b"\n")
+    sha = b.render_source_hash(str(tmp_path))
     (tmp_path / "profiles" / "k_render_cfg2_1080p.md").write_text(
-        "# summary\n\n    kernels_cu_sha256_16: %s\n" % sha
+        "# summary\n\n    render_source_sha256_16: %s\n" % sha
         + "    traffic_bytes_per_launch: 123\n    l2_bytes_per_launch: 456\n")
     monkeypatch.setattr(b, "ROOT", str(tmp_path))
     assert b.profiled_counters() == {"traffic": 123, "l2": 456}
-    (src / "kernels.cu").write_bytes(b"// kernel source B\n")
+    (src / "device_common.cuh").write_bytes(b"// source B\n")
     assert b.profiled_counters() is None
 
 
