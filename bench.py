@@ -455,9 +455,9 @@ def serving_summary(sv: dict) -> dict:
 def vector_leg(flush, stream, frames: int):
     """Config 3 (the wind-flow 3-vector volume) at 1920x1080 with Eq. 4 steps:
     |v| and v_x with FP32, FP16 and BF16 blocks (per-block offset and scale,
-    FP32 accumulation).  Per run: ms/frame (L2 flushed between frames),
-    Gsamples/s, and the image's RMSE against the FP32-block image (the error
-    of each storage against the FP64 oracle is in the GPU tests)."""
+    FP32 accumulation).  Per run [ms/frame (L2 flushed between frames),
+    Gsamples/s, the image's RMSE against the FP32-block image] (the error of
+    each storage against the FP64 oracle is in the GPU tests)."""
     import torch
     from paper_1707_01170_gb300 import lrvol as lv
     out = {}
@@ -477,8 +477,7 @@ def vector_leg(flush, stream, frames: int):
             if ref is None:
                 ref = img.clone()
             rm = float(torch.sqrt(torch.mean((img.double() - ref.double()) ** 2)))
-            out[f"{field} {storage}"] = {"ms": float(f"{ms:.4g}"), "gsamples_per_s": float(f"{n / ms / 1e6:.4g}"),
-                                         "rmse_vs_f32": float(f"{rm:.3g}")}
+            out[f"{field} {storage}"] = [float(f"{ms:.4g}"), float(f"{n / ms / 1e6:.4g}"), float(f"{rm:.3g}")]
             gv.close()
     return out
 
@@ -611,7 +610,10 @@ FOREST_SWEEP = (1, 4, 16, 64, 256)
 OCTREE_SWEEP = (1, 4, 16)   # midpoint (octree-style) trees; at 64^3 cfg2 has no trees at all
 
 
-def forest_leg(stream, frames: int = 20):
+SHORT_SWEEP = (("cfg2", (1, 16, 64)), ("cfg3mag", (4, 16, 64)))
+
+
+def forest_leg(stream, frames: int = 20, plan=None):
     """The paper's look-up comparison (Sec. 4.3 tables) on the synthetic
     volumes: for each forest resolution (trees per axis) and split rule
     (depth-balanced k-d trees; octree-style midpoint trees), the build time
@@ -625,10 +627,15 @@ def forest_leg(stream, frames: int = 20):
     flush = torch.empty(L2_FLUSH_BYTES // 4, dtype=torch.float32, device="cuda")
     out = []
     for name in ("cfg2", "cfg3mag"):
+        if plan is not None and name not in dict(plan):
+            continue
         vol, tf, cam, step = _workload(name)
         ccam, ctf, cstep = lv.make_camera(cam), lv.make_tf(tf), lv.make_step(step)
         img = torch.empty((HEIGHT, WIDTH, 4), dtype=torch.float32, device="cuda")
-        for split, b in [(lv.SPLIT_BALANCED, b) for b in FOREST_SWEEP] + [(lv.SPLIT_MIDPOINT, b) for b in OCTREE_SWEEP]:
+        runs = [(lv.SPLIT_BALANCED, b) for b in FOREST_SWEEP] + [(lv.SPLIT_MIDPOINT, b) for b in OCTREE_SWEEP]
+        if plan is not None:
+            runs = [(lv.SPLIT_BALANCED, b) for b in dict(plan).get(name, ())]
+        for split, b in runs:
             gv = lv.Volume(vol)
             t0 = time.perf_counter()
             try:
@@ -800,6 +807,10 @@ def run_ours(args):
         trimming = trim_leg(gv, vol, tf, cam, step, flush, stream)
 
     forest = forest_leg(stream) if (args.forest_sweep and ws == 1) else None
+    # a short look-up sweep in every default run: the k-d trees the 64^3
+    # benchmark forest leaves out (cfg2 needs none there) at work
+    forest_short = forest_leg(stream, frames=10, plan=SHORT_SWEEP) if (not args.forest_sweep and ws == 1
+                                                                      and args.short_sweep) else None
 
     vector = vector_leg(flush, stream, max(3, min(args.steps, 30))) if (args.vector and ws == 1) else None
 
@@ -907,6 +918,9 @@ def run_ours(args):
         line["cpu_baseline"] = cpu_baseline(vol, tf, cam, step, samples_per_frame)
     if serving is not None:
         line["serving"] = serving_summary(serving)
+    if forest_short is not None:
+        line["forest"] = [[r["workload"], r["trees_per_axis"], float(f"{r['depth']['mean']:.3g}"),
+                           float(f"{r['ms_per_frame']:.4g}")] for r in forest_short if "ms_per_frame" in r]
     if vector is not None:
         line["vector"] = vector
     if learned is not None:
@@ -938,6 +952,8 @@ def main():
                     help="also time the frame for 1^3 .. 256^3 trees (the paper's look-up comparison)")
     ap.add_argument("--no-streamlines", dest="streamlines", action="store_false",
                     help="skip the streamline runs on config 3")
+    ap.add_argument("--no-short-sweep", dest="short_sweep", action="store_false",
+                    help="skip the short look-up sweep (cfg2 at 1, 16, 64 and cfg3 |v| at 4, 16, 64 trees per axis)")
     ap.add_argument("--no-vector", dest="vector", action="store_false",
                     help="skip the config 3 |v| and v_x frames (FP32, FP16, BF16 blocks)")
     ap.add_argument("--sl-seeds", type=int, default=65536,

@@ -16,10 +16,10 @@ def _blocks():
 
 
 def test_readme_has_examples():
-    assert len(_blocks()) >= 4
+    assert len(_blocks()) >= 5
 
 
-@pytest.mark.parametrize("i", range(4))
+@pytest.mark.parametrize("i", range(5))
 def test_readme_example_parses_and_names_exist(i):
     pytest.importorskip("torch")
     from paper_1707_01170_gb300 import learned as LS

@@ -171,6 +171,24 @@ def test_octree_rejects_nondyadic_faces(vols, name):
     gv.close()
 
 
+@pytest.mark.slow
+@pytest.mark.parametrize("blocks", [(64, 64, 64), (4, 4, 4)])
+def test_lookup_bit_exact_cfg3_full_size(blocks):
+    """The vector benchmark volume at full size (388,016 elements, faces at
+    multiples of 1/192, not FP32-exact): element ids of 50,000 probe points,
+    faces and forest-block faces included, equal brute force; with 4^3 blocks
+    the trees are 3 to 18 levels deep."""
+    vol = V.load_config(3)
+    gv = lv.Volume(vol).build_accel(blocks)
+    X = _probe_points(vol, 50_000, seed=91, blocks=blocks)
+    got = gv.lookup(torch.from_numpy(X).cuda()).cpu().numpy().view(np.uint32)
+    want = Oracle(vol).lookup(X)
+    bad = np.nonzero(got != want)[0]
+    assert bad.size == 0, f"{bad.size} mismatches, e.g. {X[bad[:3]]} gpu {got[bad[:3]]} orc {want[bad[:3]]}"
+    assert gv.stats()["depth_max"] >= (6 if blocks[0] == 64 else 12)
+    gv.close()
+
+
 def test_lookup_million_points_cfg1(vols, oracles):
     vol = vols["cfg1"]
     gv = lv.Volume(vol).build_accel((64, 64, 64))
