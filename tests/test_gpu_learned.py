@@ -18,9 +18,9 @@ Bars:
                      ReLU kink (so both sides take the same branch);
   Adam               moments within 4 FP32 ulps of their larger term, the
                      step within 1e-3 relative of the FP64 step;
-  labels             between the oracle's labels at tau*(1 -+ 0.2) (the
+  labels             between the oracle's labels at tau*(1 -+ 0.02) (the
                      decision error <= tau is FP32 on the GPU, FP64 in the
-                     oracle; labels are monotone in tau), and equal for >= 95%
+                     oracle; labels are monotone in tau), and equal for >= 98%
                      of the visited elements.
 """
 import numpy as np
@@ -275,21 +275,26 @@ def test_training_reduces_loss():
 # labels
 # ----------------------------------------------------------------------------
 
-def test_labels_match_oracle(cfg1, cfg1_oracle, cfg1_gpu):
+@pytest.mark.parametrize("cand", [LS.CAND, LS.CAND_REFINE], ids=["default", "refining"])
+def test_labels_match_oracle(cfg1, cfg1_oracle, cfg1_gpu, cand):
     tf, _ = V.config1_render()
     tf = _f32_tf(tf)
     cam = V.seeded_oblique(Stream(55), 12, 10)
     step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=1.0)
-    tau, cand = 2e-4, LS.CAND
+    tau = 2e-4
     got = lv.labels(cfg1_gpu, cam, tf, step, 1 / 2048, tau, cand).cpu().numpy()
     want = cfg1_oracle.labels(cam, tf, step, 1 / 2048, tau, cand)
-    lo = cfg1_oracle.labels(cam, tf, step, 1 / 2048, 0.8 * tau, cand)
-    hi = cfg1_oracle.labels(cam, tf, step, 1 / 2048, 1.2 * tau, cand)
+    # a label is the outcome of comparisons err <= tau, taken on FP32
+    # composites on the GPU and FP64 ones in the oracle; the FP32 error of a
+    # composite difference is a few 1e-7, about 1e-3 of tau, so a 2 % band
+    # of tau bounds every label and all but a few agree exactly
+    lo = cfg1_oracle.labels(cam, tf, step, 1 / 2048, 0.98 * tau, cand)
+    hi = cfg1_oracle.labels(cam, tf, step, 1 / 2048, 1.02 * tau, cand)
     visited = want < len(cand)
     assert np.array_equal(got < len(cand), visited)
     assert visited.sum() > 50
     assert np.all((got >= lo) & (got <= hi))
-    assert np.mean(got[visited] == want[visited]) >= 0.95
+    assert np.mean(got[visited] == want[visited]) >= 0.98
     # the labels discriminate: several classes occur
     assert len(np.unique(want[visited])) >= 3
 
