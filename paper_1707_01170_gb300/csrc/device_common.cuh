@@ -284,11 +284,23 @@ __device__ __forceinline__ bool trim_cut(float2 tr, float &tin, float &tout) {
   return tin < tout;
 }
 
+// Mixed-precision FMA d = a * b + c with FP16 a, b (exact product) and FP32 c, d.
+__device__ __forceinline__ float fma_f16(unsigned short a, unsigned short b, float c) {
+  float d;
+  asm("fma.rn.f32.f16 %0, %1, %2, %3;" : "=f"(d) : "h"(a), "h"(b), "f"(c));
+  return d;
+}
+__device__ __forceinline__ unsigned short f16_bits(float x) { return __half_as_ushort(__float2half_rn(x)); }
+
 // One element's block in registers and its evaluation at monomials bx, by, bz.
 //   FIELD 0: scalar volume; 1: |v| of a 3-vector; 2: one component of a
 //   3-vector, read from the plain per-component copy.
 //   STORE: LRVOL_STORE_F32, or F16/BF16 values converted to FP32 when the
 //   element is entered, with the value of component c = o_c + s_c * contraction.
+//   Scalar tricubic FP16 blocks (MIXED) stay as 16-bit pairs in registers (32
+//   instead of 64), and the first contraction stage multiplies them with the
+//   x monomials rounded to FP16 in mixed-precision FMAs (exact products, FP32
+//   sums); the later stages run in FP32 as for the other storages.
 template <int P, int FIELD, int STORE>
 struct Block {
   static constexpr int N = P + 1;
@@ -302,7 +314,9 @@ struct Block {
   static constexpr int PAIRF = (2 * NB + 7) & ~7;          // slots of the component pair block
   static constexpr int C2F = (NB + 7) & ~7;                // slots of one plain component
 
-  f2 rp[ROWPAIR ? 8 : 1][4];                 // row pairs (2m, 2m+1), value i
+  static constexpr bool MIXED = ROWPAIR && STORE == LRVOL_STORE_F16;
+  f2 rp[ROWPAIR && !MIXED ? 8 : 1][4];       // row pairs (2m, 2m+1), value i
+  unsigned rh[MIXED ? 8 : 1][4];             // MIXED: FP16 words (row 2m, row 2m+1), value i
   float sg[SCALAR_GENERIC ? ((SGF + 7) & ~7) : 1];
   f2 cp[PAIRS ? PAIRF / 2 : 1];              // (c0, c1) per q
   float c2[COMP2 ? C2F : 1];
@@ -351,10 +365,17 @@ struct Block {
 #pragma unroll
         for (int m = 0; m < 8; ++m) {   // chunk m holds words 4m+i = (row 2m, row 2m+1) value i
           const uint4 w = __ldg(d + m);
-          rp[m][0] = word_to_f2<STORE>(w.x);
-          rp[m][1] = word_to_f2<STORE>(w.y);
-          rp[m][2] = word_to_f2<STORE>(w.z);
-          rp[m][3] = word_to_f2<STORE>(w.w);
+          if constexpr (MIXED) {
+            rh[m][0] = w.x;
+            rh[m][1] = w.y;
+            rh[m][2] = w.z;
+            rh[m][3] = w.w;
+          } else {
+            rp[m][0] = word_to_f2<STORE>(w.x);
+            rp[m][1] = word_to_f2<STORE>(w.y);
+            rp[m][2] = word_to_f2<STORE>(w.z);
+            rp[m][3] = word_to_f2<STORE>(w.w);
+          }
         }
       }
       if constexpr (SCALAR_GENERIC) {
@@ -408,13 +429,67 @@ struct Block {
     }
   }
 
+  // MIXED: the x sums of rows 4k .. 4k+3 against FP16 monomials xh, as the
+  // pairs (rows 4k, 4k+1) and (rows 4k+2, 4k+3).
+  __device__ __forceinline__ void row_sums(int k, const unsigned short *xh, f2 &S0, f2 &S1) const {
+    float s[4];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      float se = 0.f, so = 0.f;
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        unsigned short lo, hi;
+        asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(rh[2 * k + h][i]));
+        se = fma_f16(lo, xh[i], se);
+        so = fma_f16(hi, xh[i], so);
+      }
+      s[2 * h] = se;
+      s[2 * h + 1] = so;
+    }
+    S0 = f2_pack(s[0], s[1]);
+    S1 = f2_pack(s[2], s[3]);
+  }
+
   // Scalar blocks: value and derivatives in local coordinates (d/du, d/dv, d/dw)
   // at monomials b* and their derivatives d*, reusing the partial sums of the value.
   __device__ __forceinline__ float eval_grad(const float *bx, const float *by, const float *bz, const float *dx,
                                              const float *dy, const float *dz, float &gu, float &gv,
                                              float &gw) const {
     static_assert(FIELD == 0, "gradients of scalar blocks only");
-    if constexpr (ROWPAIR) {
+    if constexpr (MIXED) {
+      unsigned short xh[4], dh[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) {
+        xh[i] = f16_bits(bx[i]);
+        dh[i] = f16_bits(dx[i]);
+      }
+      const f2 Y01 = f2_pack(by[0], by[1]), Y23 = f2_pack(by[2], by[3]);
+      const f2 E01 = f2_pack(dy[0], dy[1]), E23 = f2_pack(dy[2], dy[3]);
+      f2 F = 0, FX = 0, FY = 0, FZ = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        f2 S0, S1, R0, R1;
+        row_sums(k, xh, S0, S1);
+        row_sums(k, dh, R0, R1);
+        const f2 T = f2_fma(S1, Y23, f2_mul(S0, Y01));
+        const f2 TX = f2_fma(R1, Y23, f2_mul(R0, Y01));
+        const f2 TY = f2_fma(S1, E23, f2_mul(S0, E01));
+        const f2 Z = f2_pack(bz[k], bz[k]), DZ = f2_pack(dz[k], dz[k]);
+        F = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, F);
+        FX = k == 0 ? f2_mul(TX, Z) : f2_fma(TX, Z, FX);
+        FY = k == 0 ? f2_mul(TY, Z) : f2_fma(TY, Z, FY);
+        FZ = k == 0 ? f2_mul(T, DZ) : f2_fma(T, DZ, FZ);
+      }
+      float lo, hi;
+      f2_unpack(FX, lo, hi);
+      gu = sa * (lo + hi);
+      f2_unpack(FY, lo, hi);
+      gv = sa * (lo + hi);
+      f2_unpack(FZ, lo, hi);
+      gw = sa * (lo + hi);
+      f2_unpack(F, lo, hi);
+      return fmaf(sa, lo + hi, oa);
+    } else if constexpr (ROWPAIR) {
       const f2 X0 = f2_pack(bx[0], bx[0]), X1 = f2_pack(bx[1], bx[1]);
       const f2 X2 = f2_pack(bx[2], bx[2]), X3 = f2_pack(bx[3], bx[3]);
       const f2 D0 = f2_pack(dx[0], dx[0]), D1 = f2_pack(dx[1], dx[1]);
@@ -479,7 +554,24 @@ struct Block {
   }
 
   __device__ __forceinline__ float eval(const float *bx, const float *by, const float *bz) const {
-    if constexpr (ROWPAIR) {
+    if constexpr (MIXED) {
+      unsigned short xh[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) xh[i] = f16_bits(bx[i]);
+      const f2 Y01 = f2_pack(by[0], by[1]), Y23 = f2_pack(by[2], by[3]);
+      f2 F = 0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        f2 S0, S1;
+        row_sums(k, xh, S0, S1);
+        const f2 T = f2_fma(S1, Y23, f2_mul(S0, Y01));
+        const f2 Z = f2_pack(bz[k], bz[k]);
+        F = k == 0 ? f2_mul(T, Z) : f2_fma(T, Z, F);
+      }
+      float lo, hi;
+      f2_unpack(F, lo, hi);
+      return fmaf(sa, lo + hi, oa);
+    } else if constexpr (ROWPAIR) {
       // rows r = k*4 + j; pair m = 2k + (j >> 1) holds (row 2m, row 2m+1)
       const f2 X0 = f2_pack(bx[0], bx[0]), X1 = f2_pack(bx[1], bx[1]);
       const f2 X2 = f2_pack(bx[2], bx[2]), X3 = f2_pack(bx[3], bx[3]);

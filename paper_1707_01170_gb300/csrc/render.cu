@@ -37,8 +37,17 @@ namespace {
 // FIELD 3 renders a scalar volume with gradient shading (Sec. 4.1): each
 // sample also evaluates the block's gradient, and C_src is scaled by
 // I = max(0.4, |l . g| / max(|g|, eps)).
+// CTAs per SM the register budget allows: the tricubic FP32/BF16 block takes
+// 64 registers a lane (4 CTAs of 128 threads), 16-bit pairs of an FP16 block
+// 32 (5 CTAs), the shaded variants keep the gradient's partial sums too.
+template <int P, int FIELD, int STORE>
+constexpr int render_min_ctas() {
+  if (P == 3 && STORE == LRVOL_STORE_F16 && (FIELD == 0 || FIELD == 3)) return FIELD == 3 ? 4 : 5;
+  return (FIELD == 3 && P == 3) ? 3 : 4;
+}
+
 template <int P, int FIELD, int STORE, bool TRACE>
-__global__ void __launch_bounds__(128, (FIELD == 3 && P == 3) ? 3 : 4) k_render(const __grid_constant__ RenderParams prm) {
+__global__ void __launch_bounds__(128, (render_min_ctas<P, FIELD, STORE>())) k_render(const __grid_constant__ RenderParams prm) {
   constexpr int N = P + 1;
   constexpr bool SHADE = FIELD == 3;
   constexpr int BF = SHADE ? 0 : FIELD;

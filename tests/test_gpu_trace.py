@@ -13,7 +13,9 @@ the same from oracle.c's march.  Bars:
                                its interpolated block), plus 1.02 s_e u for
                                16-bit blocks (s_e the half range of the
                                element's coefficients, u = 2^-11 FP16, 2^-8
-                               BF16);
+                               BF16), or 2.04 s_e u for tricubic scalar FP16
+                               blocks (the x monomials are rounded to FP16
+                               too, for the mixed-precision FMAs);
   sample counts                equal, except where the ray's opacity sits at
                                the early-termination threshold: FP32
                                transmittance (GPU) and FP64 opacity (oracle)
@@ -80,7 +82,9 @@ def _alg2_alpha(tf, vals, segs, xi):
 
 
 def _bounds(O, elems, field, comp, storage, exact_blocks):
-    """Per element: the coefficient bound c_e and the 16-bit bound s_e u."""
+    """Per element: the coefficient bound c_e and the 16-bit bound: 1.02 s_e u,
+    or 2.04 s_e u for tricubic scalar FP16 blocks, whose render also rounds the
+    x monomials to FP16 for its mixed-precision FMAs."""
     uniq, inv = np.unique(elems, return_inverse=True)
     if exact_blocks:
         B = O.bezier_blocks(uniq).reshape(len(uniq), O.nc, -1)
@@ -96,7 +100,8 @@ def _bounds(O, elems, field, comp, storage, exact_blocks):
     else:
         k = comp if field == "component" else 0
         c, s = amax[:, k], half[:, k]
-    return c[inv], 1.02 * U[storage] * s[inv]
+    mixed = storage == "f16" and int(O.deg[0]) == 3 and field == "scalar"
+    return c[inv], (2.04 if mixed else 1.02) * U[storage] * s[inv]
 
 
 def _runs(elem, count):
@@ -211,15 +216,16 @@ def test_trace_cfg1(cfg1, storage, mode, view, alpha_stop, capsys):
     gv.close()
 
 
-def test_trace_cfg1_shaded(cfg1):
+@pytest.mark.parametrize("storage", ["f32", "f16"])
+def test_trace_cfg1_shaded(cfg1, storage):
     """Gradient shading (Sec. 4.1): same march and values; shaded pixels."""
     vol, O = cfg1
     tf, _ = V.config1_render()
     tf = _f32_tf(tf)
     cam = V.orbit_camera(V.Stream(78), 120, 90)
     step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, shading="gradient")
-    gv = lv.Volume(vol).build_accel((32, 32, 32)).to_bezier()
-    run_case(gv, O, cam, tf, step, "f32", _hitting_pixels(cam, 600, 9), image=gv.render(cam, tf, step))
+    gv = lv.Volume(vol).build_accel((32, 32, 32)).to_bezier(STORE[storage])
+    run_case(gv, O, cam, tf, step, storage, _hitting_pixels(cam, 600, 9), image=gv.render(cam, tf, step))
     gv.close()
 
 
