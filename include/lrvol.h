@@ -180,11 +180,12 @@ int lrvol_build_accel_split(lrvol_t vol, const int32_t blocks[3], int32_t split,
  *   LRVOL_STORE_F16 / LRVOL_STORE_BF16   16-bit values with a per-element,
  *     per-component FP32 offset o = (max+min)/2 and scale s = (max-min)/2:
  *     a sample differs from the FP32-storage value by at most s*u,
- *     u = 2^-11 (FP16) or 2^-8 (BF16); accumulation stays FP32.  For
- *     tricubic scalar FP16 blocks the render keeps the 16-bit values in
- *     registers and multiplies them with the x monomials rounded to FP16
- *     (mixed-precision FMAs, exact products, FP32 sums): its samples differ
- *     from the FP32-storage value by at most 2*s*u (lrvol_eval: s*u).
+ *     u = 2^-11 (FP16) or 2^-8 (BF16); accumulation stays FP32.  With FP16
+ *     blocks the render, the streamline tracer and the tube colouring keep
+ *     the 16-bit values in registers and multiply them with the x monomials
+ *     rounded to FP16 (mixed-precision FMAs, exact products, FP32 sums):
+ *     their values differ from the FP32-storage value by at most 2*s*u
+ *     (lrvol_eval, lrvol_eval_grad: s*u).
  * Errors: LRVOL_ERR_ARG (bad storage), LRVOL_ERR_OOM, LRVOL_ERR_CUDA. */
 int lrvol_to_bezier(lrvol_t vol, int32_t storage, void *stream);
 

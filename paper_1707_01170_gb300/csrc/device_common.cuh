@@ -297,8 +297,8 @@ __device__ __forceinline__ unsigned short f16_bits(float x) { return __half_as_u
 //   3-vector, read from the plain per-component copy.
 //   STORE: LRVOL_STORE_F32, or F16/BF16 values converted to FP32 when the
 //   element is entered, with the value of component c = o_c + s_c * contraction.
-//   Scalar tricubic FP16 blocks (MIXED) stay as 16-bit pairs in registers (32
-//   instead of 64), and the first contraction stage multiplies them with the
+//   FP16 blocks (MIXED) stay as 16-bit pairs in registers (half the registers
+//   of FP32 values), and the first contraction stage multiplies them with the
 //   x monomials rounded to FP16 in mixed-precision FMAs (exact products, FP32
 //   sums); the later stages run in FP32 as for the other storages.
 template <int P, int FIELD, int STORE>
@@ -314,12 +314,22 @@ struct Block {
   static constexpr int PAIRF = (2 * NB + 7) & ~7;          // slots of the component pair block
   static constexpr int C2F = (NB + 7) & ~7;                // slots of one plain component
 
-  static constexpr bool MIXED = ROWPAIR && STORE == LRVOL_STORE_F16;
+  static constexpr bool MIXED = STORE == LRVOL_STORE_F16;
   f2 rp[ROWPAIR && !MIXED ? 8 : 1][4];       // row pairs (2m, 2m+1), value i
-  unsigned rh[MIXED ? 8 : 1][4];             // MIXED: FP16 words (row 2m, row 2m+1), value i
-  float sg[SCALAR_GENERIC ? ((SGF + 7) & ~7) : 1];
-  f2 cp[PAIRS ? PAIRF / 2 : 1];              // (c0, c1) per q
-  float c2[COMP2 ? C2F : 1];
+  unsigned rh[ROWPAIR && MIXED ? 8 : 1][4];  // MIXED: FP16 words (row 2m, row 2m+1), value i
+  float sg[SCALAR_GENERIC && !MIXED ? ((SGF + 7) & ~7) : 1];
+  unsigned sgh[SCALAR_GENERIC && MIXED ? ((SGF + 7) & ~7) / 2 : 1];   // MIXED: slots (2w, 2w+1)
+  f2 cp[PAIRS && !MIXED ? PAIRF / 2 : 1];    // (c0, c1) per q
+  unsigned cph[PAIRS && MIXED ? PAIRF / 2 : 1];   // MIXED: FP16 (c0, c1) per q
+  float c2[COMP2 && !MIXED ? C2F : 1];
+  unsigned c2h[COMP2 && MIXED ? C2F / 2 : 1];     // MIXED: slots (2w, 2w+1)
+
+  // half h (0: low) of a word of FP16 pairs
+  __device__ __forceinline__ static unsigned short half_of(unsigned w, int h) {
+    unsigned short lo, hi;
+    asm("mov.b32 {%0, %1}, %2;" : "=h"(lo), "=h"(hi) : "r"(w));
+    return h ? hi : lo;
+  }
   float oa, sa, ob, sb, oc, sc;              // affine map of 16-bit storage (component a/b/c)
 
   __device__ __forceinline__ void load(const unsigned char *eb, int comp) {
@@ -387,8 +397,12 @@ struct Block {
           const unsigned ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            sg[8 * q + 2 * t] = h_to_f<STORE>(ws[t] & 0xffffu);
-            sg[8 * q + 2 * t + 1] = h_to_f<STORE>(ws[t] >> 16);
+            if constexpr (MIXED) {
+              sgh[4 * q + t] = ws[t];
+            } else {
+              sg[8 * q + 2 * t] = h_to_f<STORE>(ws[t] & 0xffffu);
+              sg[8 * q + 2 * t + 1] = h_to_f<STORE>(ws[t] >> 16);
+            }
           }
         }
       }
@@ -400,10 +414,17 @@ struct Block {
 #pragma unroll
         for (int q = 0; q < PAIRF / 8; ++q) {
           const uint4 w = __ldg(d + q);
-          cp[4 * q] = word_to_f2<STORE>(w.x);
-          cp[4 * q + 1] = word_to_f2<STORE>(w.y);
-          cp[4 * q + 2] = word_to_f2<STORE>(w.z);
-          cp[4 * q + 3] = word_to_f2<STORE>(w.w);
+          if constexpr (MIXED) {
+            cph[4 * q] = w.x;
+            cph[4 * q + 1] = w.y;
+            cph[4 * q + 2] = w.z;
+            cph[4 * q + 3] = w.w;
+          } else {
+            cp[4 * q] = word_to_f2<STORE>(w.x);
+            cp[4 * q + 1] = word_to_f2<STORE>(w.y);
+            cp[4 * q + 2] = word_to_f2<STORE>(w.z);
+            cp[4 * q + 3] = word_to_f2<STORE>(w.w);
+          }
         }
       }
       if constexpr (COMP2) {
@@ -421,8 +442,12 @@ struct Block {
           const unsigned ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
           for (int t = 0; t < 4; ++t) {
-            c2[8 * q + 2 * t] = h_to_f<STORE>(ws[t] & 0xffffu);
-            c2[8 * q + 2 * t + 1] = h_to_f<STORE>(ws[t] >> 16);
+            if constexpr (MIXED) {
+              c2h[4 * q + t] = ws[t];
+            } else {
+              c2[8 * q + 2 * t] = h_to_f<STORE>(ws[t] & 0xffffu);
+              c2[8 * q + 2 * t + 1] = h_to_f<STORE>(ws[t] >> 16);
+            }
           }
         }
       }
@@ -456,7 +481,7 @@ struct Block {
                                              const float *dy, const float *dz, float &gu, float &gv,
                                              float &gw) const {
     static_assert(FIELD == 0, "gradients of scalar blocks only");
-    if constexpr (MIXED) {
+    if constexpr (ROWPAIR && MIXED) {
       unsigned short xh[4], dh[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) {
@@ -523,6 +548,14 @@ struct Block {
       f2_unpack(F, lo, hi);
       return F32 ? lo + hi : fmaf(sa, lo + hi, oa);
     } else {
+      unsigned short xh[N], dh[N];
+      if constexpr (MIXED) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+          xh[i] = f16_bits(bx[i]);
+          dh[i] = f16_bits(dx[i]);
+        }
+      }
       float f = 0.f, fx = 0.f, fy = 0.f, fz = 0.f;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
@@ -533,9 +566,15 @@ struct Block {
           float sx = 0.f, rx = 0.f;
 #pragma unroll
           for (int i = 0; i < N; ++i) {
-            const float c = sg[(r >> 1) * 2 * N + 2 * i + (r & 1)];
-            sx = fmaf(c, bx[i], sx);
-            rx = fmaf(c, dx[i], rx);
+            if constexpr (MIXED) {
+              const unsigned short c = half_of(sgh[(r >> 1) * N + i], r & 1);
+              sx = fma_f16(c, xh[i], sx);
+              rx = fma_f16(c, dh[i], rx);
+            } else {
+              const float c = sg[(r >> 1) * 2 * N + 2 * i + (r & 1)];
+              sx = fmaf(c, bx[i], sx);
+              rx = fmaf(c, dx[i], rx);
+            }
           }
           t = fmaf(sx, by[j], t);
           tx = fmaf(rx, by[j], tx);
@@ -554,7 +593,7 @@ struct Block {
   }
 
   __device__ __forceinline__ float eval(const float *bx, const float *by, const float *bz) const {
-    if constexpr (MIXED) {
+    if constexpr (ROWPAIR && MIXED) {
       unsigned short xh[4];
 #pragma unroll
       for (int i = 0; i < 4; ++i) xh[i] = f16_bits(bx[i]);
@@ -590,6 +629,11 @@ struct Block {
       f2_unpack(F, lo, hi);
       return F32 ? lo + hi : fmaf(sa, lo + hi, oa);
     } else if constexpr (SCALAR_GENERIC) {
+      unsigned short xh[N];
+      if constexpr (MIXED) {
+#pragma unroll
+        for (int i = 0; i < N; ++i) xh[i] = f16_bits(bx[i]);
+      }
       float f = 0.f;
 #pragma unroll
       for (int k = 0; k < N; ++k) {
@@ -599,7 +643,12 @@ struct Block {
           const int r = k * N + j;
           float sx = 0.f;
 #pragma unroll
-          for (int i = 0; i < N; ++i) sx = fmaf(sg[(r >> 1) * 2 * N + 2 * i + (r & 1)], bx[i], sx);
+          for (int i = 0; i < N; ++i) {
+            if constexpr (MIXED)
+              sx = fma_f16(half_of(sgh[(r >> 1) * N + i], r & 1), xh[i], sx);
+            else
+              sx = fmaf(sg[(r >> 1) * 2 * N + 2 * i + (r & 1)], bx[i], sx);
+          }
           t = fmaf(sx, by[j], t);
         }
         f = fmaf(t, bz[k], f);
@@ -620,6 +669,11 @@ struct Block {
     v0 = 0.f;
     v1 = 0.f;
     v2 = 0.f;
+    unsigned short xh[N];
+    if constexpr (MIXED) {
+#pragma unroll
+      for (int i = 0; i < N; ++i) xh[i] = f16_bits(bx[i]);
+    }
     if constexpr (PAIRS) {
       f2 X[N], Y[N];
 #pragma unroll
@@ -633,10 +687,22 @@ struct Block {
         f2 T = 0;
 #pragma unroll
         for (int j = 0; j < N; ++j) {
-          const f2 *c = &cp[(k * N + j) * N];
-          f2 S = f2_mul(c[0], X[0]);
+          f2 S;
+          if constexpr (MIXED) {
+            float s0 = 0.f, s1 = 0.f;
 #pragma unroll
-          for (int i = 1; i < N; ++i) S = f2_fma(c[i], X[i], S);
+            for (int i = 0; i < N; ++i) {
+              const unsigned w = cph[(k * N + j) * N + i];
+              s0 = fma_f16(half_of(w, 0), xh[i], s0);
+              s1 = fma_f16(half_of(w, 1), xh[i], s1);
+            }
+            S = f2_pack(s0, s1);
+          } else {
+            const f2 *c = &cp[(k * N + j) * N];
+            S = f2_mul(c[0], X[0]);
+#pragma unroll
+            for (int i = 1; i < N; ++i) S = f2_fma(c[i], X[i], S);
+          }
           T = j == 0 ? f2_mul(S, Y[0]) : f2_fma(S, Y[j], T);
         }
         const f2 Z = f2_pack(bz[k], bz[k]);
@@ -656,7 +722,13 @@ struct Block {
         for (int j = 0; j < N; ++j) {
           float sx = 0.f;
 #pragma unroll
-          for (int i = 0; i < N; ++i) sx = fmaf(c2[(k * N + j) * N + i], bx[i], sx);
+          for (int i = 0; i < N; ++i) {
+            const int q = (k * N + j) * N + i;
+            if constexpr (MIXED)
+              sx = fma_f16(half_of(c2h[q >> 1], q & 1), xh[i], sx);
+            else
+              sx = fmaf(c2[q], bx[i], sx);
+          }
           t = fmaf(sx, by[j], t);
         }
         v2 = fmaf(t, bz[k], v2);

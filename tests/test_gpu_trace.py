@@ -13,9 +13,9 @@ the same from oracle.c's march.  Bars:
                                its interpolated block), plus 1.02 s_e u for
                                16-bit blocks (s_e the half range of the
                                element's coefficients, u = 2^-11 FP16, 2^-8
-                               BF16), or 2.04 s_e u for tricubic scalar FP16
-                               blocks (the x monomials are rounded to FP16
-                               too, for the mixed-precision FMAs);
+                               BF16), 2.04 s_e u for FP16 blocks (the x
+                               monomials are rounded to FP16 too, for the
+                               mixed-precision FMAs);
   sample counts                equal, except where the ray's opacity sits at
                                the early-termination threshold: FP32
                                transmittance (GPU) and FP64 opacity (oracle)
@@ -82,8 +82,8 @@ def _alg2_alpha(tf, vals, segs, xi):
 
 
 def _bounds(O, elems, field, comp, storage, exact_blocks):
-    """Per element: the coefficient bound c_e and the 16-bit bound: 1.02 s_e u,
-    or 2.04 s_e u for tricubic scalar FP16 blocks, whose render also rounds the
+    """Per element: the coefficient bound c_e and the 16-bit bound: 1.02 s_e u
+    for BF16 blocks, 2.04 s_e u for FP16 blocks, whose render also rounds the
     x monomials to FP16 for its mixed-precision FMAs."""
     uniq, inv = np.unique(elems, return_inverse=True)
     if exact_blocks:
@@ -100,8 +100,7 @@ def _bounds(O, elems, field, comp, storage, exact_blocks):
     else:
         k = comp if field == "component" else 0
         c, s = amax[:, k], half[:, k]
-    mixed = storage == "f16" and int(O.deg[0]) == 3 and field == "scalar"
-    return c[inv], (2.04 if mixed else 1.02) * U[storage] * s[inv]
+    return c[inv], (2.04 if storage == "f16" else 1.02) * U[storage] * s[inv]
 
 
 def _runs(elem, count):
