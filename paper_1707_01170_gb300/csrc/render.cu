@@ -40,15 +40,17 @@ namespace {
 // CTAs per SM the register budget allows: the tricubic FP32/BF16 block takes
 // 64 registers a lane (4 CTAs of 128 threads), 16-bit pairs of an FP16 block
 // 32 (5 CTAs); the triquadratic 3-vector FP16 block (42 registers instead of
-// 83) also fits 5; the shaded variants keep the gradient's partial sums too.
+// 83) also fits 5.  The shaded tricubic kernel keeps the gradient's partial
+// sums too: at 4 CTAs it spills 88 bytes and still beats 3 CTAs without
+// spills by 5 % (measured); forcing 5 CTAs on the FP32 kernels spills
+// inside the sample loop and costs 37-51 %.
 template <int P, int FIELD, int STORE>
 constexpr int render_min_ctas() {
   if (STORE == LRVOL_STORE_F16) {
     if (P == 3 && FIELD == 0) return 5;
-    if (P == 3 && FIELD == 3) return 4;
     if (P == 2 && (FIELD == 1 || FIELD == 2)) return 5;
   }
-  return (FIELD == 3 && P == 3) ? 3 : 4;
+  return 4;
 }
 
 template <int P, int FIELD, int STORE, bool TRACE>
