@@ -17,9 +17,10 @@ static_assert(LRVOL_BAND_ROWS == 8, "a CTA renders 8 rows: one interleaved band"
 namespace lrvol {
 namespace {
 
-// One CTA of 4 warps renders a 16x8-pixel tile (each warp an 8x4 patch), so
-// the warps sharing an SM's L1 march through neighbouring elements; one lane
-// traces one ray.  The element-change branch (look-up and block loads) is kept
+// One CTA of 4 warps renders a 16x8-pixel tile, so the warps sharing an SM's
+// L1 march through neighbouring elements; one lane traces one ray.  A warp
+// covers an 8x4 patch for scalar fields and a 4x8 patch for 3-vector fields
+// (the shapes that measured fastest for each).  The element-change branch (look-up and block loads) is kept
 // minimal: a warp runs it whenever any of its lanes changes element, which
 // happens almost every iteration.
 //
@@ -83,8 +84,13 @@ __global__ void __launch_bounds__(128, (render_min_ctas<P, FIELD, STORE>())) k_r
       active = false;
     }
   } else {
-    i = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
-    j = prm.row_begin + (blockIdx.y * prm.band_count + prm.band_index) * 8 + (warp >> 1) * 4 + (lane >> 3);
+    if constexpr (BF == 1 || BF == 2) {   // 3-vector fields: four 4x8 patches side by side
+      i = blockIdx.x * 16 + warp * 4 + (lane & 3);
+      j = prm.row_begin + (blockIdx.y * prm.band_count + prm.band_index) * 8 + (lane >> 2);
+    } else {                              // scalar fields: 2x2 patches of 8x4
+      i = blockIdx.x * 16 + (warp & 1) * 8 + (lane & 7);
+      j = prm.row_begin + (blockIdx.y * prm.band_count + prm.band_index) * 8 + (warp >> 1) * 4 + (lane >> 3);
+    }
     active = i < prm.width && j < prm.row_end;
   }
   unsigned nsamp = 0, nlook = 0, nhit = 0;
