@@ -455,3 +455,31 @@ def test_render_shards_reassemble(vols, interleaved, world):
         gv.render(cam, tf, step, band_count=2, band_index=2)
     assert ei.value.status == lv.ERR_ARG
     gv.close()
+
+
+@pytest.mark.parametrize("storage", [lv.STORE_F32, lv.STORE_F16])
+@pytest.mark.parametrize("field", ["magnitude", "component"])
+def test_render_shards_reassemble_vector(vols, storage, field):
+    """The same for a 3-vector volume, whose kernels map 4x8-pixel warps
+    (scalar ones 8x4) onto the 8-row bands: 3 interleaved and 2 contiguous
+    shards give the full frame bitwise, on a ragged 70x53 image."""
+    from paper_1707_01170_gb300.shard import render_shard, rows_of
+    tf = V.seeded_tf(V.Stream(31), alpha_max=0.05)
+    tf.vmin, tf.vmax = (0.0, 1.6) if field == "magnitude" else (-0.5, 1.0)
+    cam = V.orbit_camera(V.Stream(10), 70, 53)
+    step = V.StepParams(mode="heuristic", xi=1 / 128, field=field, component=1)
+    gv = lv.Volume(vols["nondyadic_p2_vec"]).build_accel((16, 16, 16)).to_bezier(storage)
+    full = gv.render(cam, tf, step)
+    assert float(full[..., 3].max()) > 0.05
+    for world, interleaved in ((3, True), (2, False)):
+        out = torch.full_like(full, -1.0)
+        for r in range(world):
+            one = torch.full_like(full, -1.0)
+            render_shard(gv, cam, tf, step, one, world=world, rank=r, interleaved=interleaved)
+            mine = torch.zeros(cam.height, dtype=torch.bool, device="cuda")
+            for a, b in rows_of(cam.height, world, r, interleaved):
+                mine[a:b] = True
+            assert bool(torch.all(one[~mine] == -1.0))
+            out[mine] = one[mine]
+        assert torch.equal(out, full), (world, interleaved)
+    gv.close()
