@@ -451,66 +451,115 @@ __device__ __forceinline__ void field_range(const FeatureParams &fp, int64_t e, 
   }
 }
 
+// The TF in shared memory with aggregates over blocks of kTfBlock bins (the
+// largest opacity, the opacity sum, the largest opacity step to the next bin,
+// the RGB range), so that an element's bin range [i0, i1] costs at most
+// 2 (kTfBlock - 1) single bins plus whole blocks instead of up to 256 bins:
+// one element straddling a sharp TF band would otherwise hold its whole warp.
+// Maxima and minima are exact in any order; only the opacity sum is added in
+// another order.
+constexpr int kTfBlock = 16, kTfBlocks = 256 / kTfBlock;
+
 __global__ void k_features(const __grid_constant__ FeatureParams fp, float *__restrict__ out) {
-  // the TF in shared memory: the bin scans below index it per lane
   __shared__ float4 tfs[256];
+  __shared__ float b_amax[kTfBlocks], b_asum[kTfBlocks], b_slope[kTfBlocks];
+  __shared__ float b_cmin[3][kTfBlocks], b_cmax[3][kTfBlocks];
   for (int q = threadIdx.x; q < 256; q += blockDim.x) tfs[q] = fp.tf[q];
+  __syncthreads();
+  if (threadIdx.x < kTfBlocks) {
+    const int q = threadIdx.x;
+    float am = 0.f, as = 0.f, sl = 0.f;
+    float mn[3] = {1e30f, 1e30f, 1e30f}, mx[3] = {-1e30f, -1e30f, -1e30f};
+    for (int i = q * kTfBlock; i < (q + 1) * kTfBlock; ++i) {
+      const float4 t = tfs[i];
+      am = fmaxf(am, t.w);
+      as += t.w;
+      if (i < 255) sl = fmaxf(sl, fabsf(tfs[i + 1].w - t.w));   // the step from bin i to bin i + 1
+      mn[0] = fminf(mn[0], t.x); mx[0] = fmaxf(mx[0], t.x);
+      mn[1] = fminf(mn[1], t.y); mx[1] = fmaxf(mx[1], t.y);
+      mn[2] = fminf(mn[2], t.z); mx[2] = fmaxf(mx[2], t.z);
+    }
+    b_amax[q] = am;
+    b_asum[q] = as;
+    b_slope[q] = sl;
+    for (int c = 0; c < 3; ++c) {
+      b_cmin[c][q] = mn[c];
+      b_cmax[c][q] = mx[c];
+    }
+  }
   __syncthreads();
   const int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (e >= fp.n_elem) return;
-  const double *b = fp.box + 6 * e;
-  float w[3], ctr[3];
-  for (int a = 0; a < 3; ++a) {
-    w[a] = (float)(b[3 + a] - b[a]);
-    ctr[a] = (float)(0.5 * (b[a] + b[3 + a]));
+  {
+    // the box as three 16-byte loads (48 bytes per element, so 16-byte aligned)
+    const double2 *b2 = reinterpret_cast<const double2 *>(fp.box + 6 * e);
+    const double2 q0 = __ldg(b2), q1 = __ldg(b2 + 1), q2 = __ldg(b2 + 2);
+    const double b[6] = {q0.x, q0.y, q1.x, q1.y, q2.x, q2.y};
+    float w[3], ctr[3];
+    for (int a = 0; a < 3; ++a) {
+      w[a] = (float)(b[3 + a] - b[a]);
+      ctr[a] = (float)(0.5 * (b[a] + b[3 + a]));
+    }
+    const float ds = __ldg(&fp.elem[e].a.w);
+    float lo, hi;
+    field_range(fp, e, lo, hi);
+    const float xlo = fmaf(lo, fp.tf_scale, fp.tf_bias) * (1.f / 255.f);
+    const float xhi = fmaf(hi, fp.tf_scale, fp.tf_bias) * (1.f / 255.f);
+    const int i0 = (int)floorf(255.f * fminf(fmaxf(xlo, 0.f), 1.f));
+    const int i1 = min(255, (int)ceilf(255.f * fminf(fmaxf(xhi, 0.f), 1.f)));
+    float amax = 0.f, asum = 0.f, slope = 0.f;
+    float cmin[3] = {1e30f, 1e30f, 1e30f}, cmax[3] = {-1e30f, -1e30f, -1e30f};
+    auto bin = [&](int i) {
+      const float4 t = tfs[i];
+      amax = fmaxf(amax, t.w);
+      asum += t.w;
+      cmin[0] = fminf(cmin[0], t.x); cmax[0] = fmaxf(cmax[0], t.x);
+      cmin[1] = fminf(cmin[1], t.y); cmax[1] = fmaxf(cmax[1], t.y);
+      cmin[2] = fminf(cmin[2], t.z); cmax[2] = fmaxf(cmax[2], t.z);
+    };
+    int i = i0;   // bins i0 .. i1: head to a block boundary, whole blocks, tail
+    for (; i <= i1 && (i % kTfBlock) != 0; ++i) bin(i);
+    for (; i + kTfBlock - 1 <= i1; i += kTfBlock) {
+      const int q = i / kTfBlock;
+      amax = fmaxf(amax, b_amax[q]);
+      asum += b_asum[q];
+      for (int c = 0; c < 3; ++c) {
+        cmin[c] = fminf(cmin[c], b_cmin[c][q]);
+        cmax[c] = fmaxf(cmax[c], b_cmax[c][q]);
+      }
+    }
+    for (; i <= i1; ++i) bin(i);
+    // the largest opacity step between neighbouring bins of the range: steps i -> i + 1 for i0 <= i < i1
+    for (i = i0; i < i1 && (i % kTfBlock) != 0; ++i) slope = fmaxf(slope, fabsf(tfs[i + 1].w - tfs[i].w));
+    for (; i + kTfBlock - 1 < i1; i += kTfBlock) slope = fmaxf(slope, b_slope[i / kTfBlock]);
+    for (; i < i1; ++i) slope = fmaxf(slope, fabsf(tfs[i + 1].w - tfs[i].w));
+    float dir[3];
+    float nn = 0.f;
+    for (int a = 0; a < 3; ++a) {
+      dir[a] = ctr[a] - fp.eye[a];
+      nn = fmaf(dir[a], dir[a], nn);
+    }
+    nn = rsqrtf(fmaxf(nn, 1e-30f));
+    float proj = 0.f;
+    for (int a = 0; a < 3; ++a) {
+      dir[a] *= nn;
+      proj = fmaf(fabsf(dir[a]), w[a], proj);
+    }
+    const float f[kIn] = {log2f(64.f * w[0]), log2f(64.f * w[1]), log2f(64.f * w[2]), xlo,
+                          xhi, xhi - xlo, amax, asum / (float)(i1 - i0 + 1),
+                          255.f * slope, fmaxf(cmax[0] - cmin[0], fmaxf(cmax[1] - cmin[1], cmax[2] - cmin[2])),
+                          dir[0], dir[1],
+                          dir[2], log2f(2048.f * ds), proj / (8.f * ds), log2f(1.f + 255.f * (xhi - xlo))};
+    float *o = out + e * kIn;
+    if ((reinterpret_cast<uintptr_t>(out) & 15) == 0) {   // one 64-byte row, four 16-byte stores
+      float4 *o4 = reinterpret_cast<float4 *>(o);
+#pragma unroll
+      for (int c = 0; c < kIn / 4; ++c) o4[c] = make_float4(f[4 * c], f[4 * c + 1], f[4 * c + 2], f[4 * c + 3]);
+    } else {                                               // a caller's buffer not 16-byte aligned
+#pragma unroll
+      for (int c = 0; c < kIn; ++c) o[c] = f[c];
+    }
   }
-  const float ds = __ldg(&fp.elem[e].a.w);
-  float lo, hi;
-  field_range(fp, e, lo, hi);
-  const float xlo = fmaf(lo, fp.tf_scale, fp.tf_bias) * (1.f / 255.f);
-  const float xhi = fmaf(hi, fp.tf_scale, fp.tf_bias) * (1.f / 255.f);
-  const int i0 = (int)floorf(255.f * fminf(fmaxf(xlo, 0.f), 1.f));
-  const int i1 = min(255, (int)ceilf(255.f * fminf(fmaxf(xhi, 0.f), 1.f)));
-  float amax = 0.f, asum = 0.f, slope = 0.f;
-  float cmin[3] = {1e30f, 1e30f, 1e30f}, cmax[3] = {-1e30f, -1e30f, -1e30f};
-  for (int i = i0; i <= i1; ++i) {
-    const float4 t = tfs[i];
-    amax = fmaxf(amax, t.w);
-    asum += t.w;
-    if (i < i1) slope = fmaxf(slope, fabsf(tfs[i + 1].w - t.w));
-    cmin[0] = fminf(cmin[0], t.x); cmax[0] = fmaxf(cmax[0], t.x);
-    cmin[1] = fminf(cmin[1], t.y); cmax[1] = fmaxf(cmax[1], t.y);
-    cmin[2] = fminf(cmin[2], t.z); cmax[2] = fmaxf(cmax[2], t.z);
-  }
-  float dir[3];
-  float nn = 0.f;
-  for (int a = 0; a < 3; ++a) {
-    dir[a] = ctr[a] - fp.eye[a];
-    nn = fmaf(dir[a], dir[a], nn);
-  }
-  nn = rsqrtf(fmaxf(nn, 1e-30f));
-  float proj = 0.f;
-  for (int a = 0; a < 3; ++a) {
-    dir[a] *= nn;
-    proj = fmaf(fabsf(dir[a]), w[a], proj);
-  }
-  float *o = out + e * kIn;
-  o[0] = log2f(64.f * w[0]);
-  o[1] = log2f(64.f * w[1]);
-  o[2] = log2f(64.f * w[2]);
-  o[3] = xlo;
-  o[4] = xhi;
-  o[5] = xhi - xlo;
-  o[6] = amax;
-  o[7] = asum / (float)(i1 - i0 + 1);
-  o[8] = 255.f * slope;
-  o[9] = fmaxf(cmax[0] - cmin[0], fmaxf(cmax[1] - cmin[1], cmax[2] - cmin[2]));
-  o[10] = dir[0];
-  o[11] = dir[1];
-  o[12] = dir[2];
-  o[13] = log2f(2048.f * ds);
-  o[14] = proj / (8.f * ds);
-  o[15] = log2f(1.f + 255.f * (xhi - xlo));
 }
 
 // ---- the step network on the 5th-generation tensor cores (tcgen05) ----
@@ -958,6 +1007,7 @@ __global__ void __launch_bounds__(128) k_labels(const __grid_constant__ RenderPa
 }  // namespace
 
 cudaError_t launch_features(const FeatureParams &fp, float *out, cudaStream_t s) {
+  if (fp.n_elem == 0) return cudaSuccess;
   k_features<<<(unsigned)((fp.n_elem + 127) / 128), 128, 0, s>>>(fp, out);
   return cudaGetLastError();
 }

@@ -136,6 +136,23 @@ def test_features_match_oracle(cfg1, cfg1_oracle, cfg1_gpu, which):
         gv.close()
 
 
+def test_features_unaligned_output_matches_aligned(cfg1, cfg1_gpu):
+    """An output buffer that is not 16-byte aligned takes the kernel's
+    scalar-store path; its rows equal those written to an aligned buffer,
+    and nothing outside the rows is written."""
+    tf, cams = V.config1_render()
+    step = V.StepParams(mode="heuristic")
+    n = cfg1_gpu.n_elem
+    want = lv.features(cfg1_gpu, cams[1], tf, step)
+    assert want.data_ptr() % 16 == 0
+    buf = torch.full((16 * n + 2,), -7.0, dtype=torch.float32, device="cuda")
+    shifted = buf[1:1 + 16 * n].view(n, 16)
+    assert shifted.data_ptr() % 16 != 0
+    got = lv.features(cfg1_gpu, cams[1], tf, step, out=shifted)
+    assert torch.equal(got, want)
+    assert float(buf[0]) == -7.0 and float(buf[-1]) == -7.0
+
+
 # ----------------------------------------------------------------------------
 # network: BF16 inference, FP32 gradient, Adam
 # ----------------------------------------------------------------------------
