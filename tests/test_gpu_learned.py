@@ -136,6 +136,33 @@ def test_features_match_oracle(cfg1, cfg1_oracle, cfg1_gpu, which):
         gv.close()
 
 
+def test_features_match_oracle_full_size_cfg2():
+    """The benchmark volume (cfg2, 174,000 elements) with its own TF and
+    camera: 3,000 sampled elements against the oracle's features computed
+    from its own Bezier blocks.  Its elements at the shells span up to the
+    whole TF range, so the range scans run through the 16-bin aggregates as
+    well as single bins (checked below)."""
+    vol = V.load_config(2)
+    tf, cam = V.config2_render(vol=vol)
+    tf = _f32_tf(tf)
+    orc = Oracle(vol)
+    gv = lv.Volume(vol).build_accel((64, 64, 64)).to_bezier()
+    got = lv.features(gv, cam, tf, V.StepParams(mode="heuristic")).cpu().numpy()
+    gv.close()
+    rng = np.random.default_rng(17)
+    sel = np.sort(rng.choice(vol.n_elem, 3000, replace=False))
+    want = OL.features(orc, orc.box[sel], cam, tf, "scalar", 0, orc.bezier_blocks(sel))
+    got = got[sel]
+    near = lambda x: (x > 0) & (x < 1) & (np.abs(255 * x - np.round(255 * x)) < 1e-3)
+    edge = near(want[:, 3]) | near(want[:, 4])
+    assert edge.mean() < 0.02
+    width = np.ceil(255 * np.clip(want[:, 4], 0, 1)) - np.floor(255 * np.clip(want[:, 3], 0, 1))
+    assert np.sum(width >= 32) >= 20                      # ranges that cover whole 16-bin blocks
+    cols = [c for c in range(16) if c not in (6, 7, 8, 9)]
+    np.testing.assert_allclose(got[:, cols], want[:, cols], atol=1e-5, rtol=1e-5)
+    np.testing.assert_allclose(got[~edge][:, 6:10], want[~edge][:, 6:10], atol=1e-5, rtol=1e-5)
+
+
 def test_features_unaligned_output_matches_aligned(cfg1, cfg1_gpu):
     """An output buffer that is not 16-byte aligned takes the kernel's
     scalar-store path; its rows equal those written to an aligned buffer,
