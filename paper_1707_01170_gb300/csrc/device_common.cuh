@@ -372,15 +372,25 @@ struct Block {
       if constexpr (ROWPAIR) {
         oa = h0.x;
         sa = h0.w;
+        // chunk m holds words 4m+i = (row 2m, row 2m+1) value i
+        if constexpr (MIXED) {   // chunks m and m + 1 by one 256-bit load (the data start 32-byte aligned)
 #pragma unroll
-        for (int m = 0; m < 8; ++m) {   // chunk m holds words 4m+i = (row 2m, row 2m+1) value i
-          const uint4 w = __ldg(d + m);
-          if constexpr (MIXED) {
-            rh[m][0] = w.x;
-            rh[m][1] = w.y;
-            rh[m][2] = w.z;
-            rh[m][3] = w.w;
-          } else {
+          for (int m = 0; m < 8; m += 2) {
+            f2 a, b, c, e;
+            ld256(d + m, a, b, c, e);
+            rh[m][0] = (unsigned)a;
+            rh[m][1] = (unsigned)(a >> 32);
+            rh[m][2] = (unsigned)b;
+            rh[m][3] = (unsigned)(b >> 32);
+            rh[m + 1][0] = (unsigned)c;
+            rh[m + 1][1] = (unsigned)(c >> 32);
+            rh[m + 1][2] = (unsigned)e;
+            rh[m + 1][3] = (unsigned)(e >> 32);
+          }
+        } else {
+#pragma unroll
+          for (int m = 0; m < 8; ++m) {
+            const uint4 w = __ldg(d + m);
             rp[m][0] = word_to_f2<STORE>(w.x);
             rp[m][1] = word_to_f2<STORE>(w.y);
             rp[m][2] = word_to_f2<STORE>(w.z);
