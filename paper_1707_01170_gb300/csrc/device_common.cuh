@@ -416,13 +416,47 @@ struct Block {
           }
         }
       }
+      constexpr bool V256 = MIXED && (PAIRS || COMP2) && (FIELD == 1 || (C2F / 8) % 2 == 0);
+      if constexpr (V256) {
+        // this field's 16-bit words ((c0, c1) pairs then component 2, or one
+        // component) by 256-bit loads from a 32-byte aligned start, a 128-bit tail
+        constexpr int NP = PAIRS ? PAIRF / 8 : 0, NCH = NP + C2F / 8;
+        const uint4 *src = FIELD == 1 ? d : d + comp * (C2F / 8);
+        unsigned wv[4 * NCH];
+#pragma unroll
+        for (int q = 0; q + 1 < NCH; q += 2) {
+          f2 a, b, c, e;
+          ld256(src + q, a, b, c, e);
+          wv[4 * q] = (unsigned)a;
+          wv[4 * q + 1] = (unsigned)(a >> 32);
+          wv[4 * q + 2] = (unsigned)b;
+          wv[4 * q + 3] = (unsigned)(b >> 32);
+          wv[4 * q + 4] = (unsigned)c;
+          wv[4 * q + 5] = (unsigned)(c >> 32);
+          wv[4 * q + 6] = (unsigned)e;
+          wv[4 * q + 7] = (unsigned)(e >> 32);
+        }
+        if constexpr (NCH % 2 == 1) {
+          const uint4 w = __ldg(src + NCH - 1);
+          wv[4 * NCH - 4] = w.x;
+          wv[4 * NCH - 3] = w.y;
+          wv[4 * NCH - 2] = w.z;
+          wv[4 * NCH - 1] = w.w;
+        }
+        if constexpr (PAIRS) {
+#pragma unroll
+          for (int q = 0; q < 4 * NP; ++q) cph[q] = wv[q];
+        }
+#pragma unroll
+        for (int q = 0; q < C2F / 2; ++q) c2h[q] = wv[4 * NP + q];
+      }
       if constexpr (PAIRS) {
         oa = h0.x;
         ob = h0.y;
         sa = h0.w;
         sb = h1.x;
 #pragma unroll
-        for (int q = 0; q < PAIRF / 8; ++q) {
+        for (int q = 0; q < (V256 ? 0 : PAIRF / 8); ++q) {
           const uint4 w = __ldg(d + q);
           if constexpr (MIXED) {
             cph[4 * q] = w.x;
@@ -447,7 +481,7 @@ struct Block {
         }
         const uint4 *dc = d + (FIELD == 1 ? PAIRF : comp * C2F) / 8;
 #pragma unroll
-        for (int q = 0; q < C2F / 8; ++q) {
+        for (int q = 0; q < (V256 ? 0 : C2F / 8); ++q) {
           const uint4 w = __ldg(dc + q);
           const unsigned ws[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
