@@ -385,6 +385,21 @@ def test_render_cfg2_full_size_sampled():
 
 
 @pytest.mark.slow
+def test_render_cfg2_shaded_full_size_sampled():
+    """The benchmark frame with gradient shading (Sec. 4.1, light at the eye;
+    the FP32 kernel that runs 4 CTAs per SM with spills) on 512 sampled
+    pixels, each recomputed by the oracle with its own FP64 gradients."""
+    vol = V.load_config(2)
+    tf, cam = V.config2_render()
+    tf = _f32_tf(tf)
+    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, shading="gradient")
+    pix = _sample_pixels(cam, 512, 6)
+    img, ref, st, ost = _render_pair(vol, Oracle(vol), cam, tf, step, blocks=(64, 64, 64), pixels=pix)
+    assert _rmse(img, ref) <= RMSE_TOL
+    assert np.abs(ref[:, 3]).max() > 0.05
+
+
+@pytest.mark.slow
 @pytest.mark.parametrize("field", ["magnitude", "component"])
 def test_render_cfg3_full_size_sampled(field):
     """The vector benchmark configurations (388,016 elements, knots not FP32
