@@ -263,6 +263,39 @@ def test_trace_vector_nondyadic(vec, storage, field, comp, mode):
     gv.close()
 
 
+VEC_DEG_CASES = [
+    (1, "f32", "magnitude", 0),
+    (1, "f16", "magnitude", 0),
+    (1, "f16", "component", 1),
+    (1, "bf16", "component", 2),
+    (3, "f32", "component", 0),
+    (3, "f16", "magnitude", 0),
+    (3, "f16", "component", 2),
+    (3, "bf16", "magnitude", 0),
+]
+
+
+@pytest.mark.parametrize("deg,storage,field,comp", VEC_DEG_CASES)
+def test_trace_vector_degrees(deg, storage, field, comp):
+    """3-vector volumes of degree 1 and 3 (the benchmark's vector volume is
+    degree 2): |v| and single components through every block layout, the
+    16-bit ones in both of their load paths (256-bit loads where a
+    component's words start 32-byte aligned, 128-bit loads otherwise)."""
+    vol = V.refined_ball((deg,) * 3, (3, 3, 3), centres=((0.4, 0.55, 0.5),), radii=(0.35, 0.18), ncomp=3,
+                         seed=7 + deg)
+    O = Oracle(vol)
+    tf = _f32_tf(V.seeded_tf(V.Stream(51), alpha_max=0.05))
+    if field == "magnitude":
+        tf.vmin, tf.vmax = 0.0, float(np.linalg.norm(vol.coef, axis=1).max())
+    else:
+        tf.vmin, tf.vmax = float(vol.coef[:, comp].min()), float(vol.coef[:, comp].max())
+    cam = V.orbit_camera(V.Stream(52), 80, 60)
+    step = V.StepParams(mode="heuristic", xi=1 / 128, alpha_stop=0.99, field=field, component=comp)
+    gv = lv.Volume(vol).build_accel((16, 16, 16)).to_bezier(STORE[storage])
+    run_case(gv, O, cam, tf, step, storage, _hitting_pixels(cam, 500, 23), 2048, image=gv.render(cam, tf, step))
+    gv.close()
+
+
 @pytest.mark.parametrize("deg,storage,mode", [(2, "f32", "heuristic"), (2, "f16", "learned"), (1, "f32", "heuristic"),
                                                (1, "bf16", "fixed")])
 def test_trace_scalar_low_degree(deg, storage, mode):
