@@ -312,6 +312,22 @@ def test_trace_scalar_low_degree(deg, storage, mode):
     gv.close()
 
 
+@pytest.mark.parametrize("deg,storage", [(1, "f16"), (1, "bf16"), (2, "f16"), (2, "bf16"), (2, "f32")])
+def test_trace_shaded_low_degree(deg, storage):
+    """Gradient shading on scalar volumes of degree 1 and 2, whose blocks take
+    the generic layout (with 16-bit storage: mixed-precision FMAs for FP16,
+    conversion for BF16) instead of the tricubic row pairs."""
+    vol = V.refined_ball((deg,) * 3, (4, 4, 4), centres=((0.45, 0.5, 0.55),), radii=(0.35, 0.15), seed=6)
+    O = Oracle(vol)
+    tf = _f32_tf(V.seeded_tf(V.Stream(43), alpha_max=0.06))
+    tf.vmin, tf.vmax = float(vol.coef.min()), float(vol.coef.max())
+    cam = V.orbit_camera(V.Stream(44), 90, 64)
+    step = V.StepParams(mode="heuristic", xi=1 / 256, alpha_stop=0.99, shading="gradient", light=(0.3, -0.5, 0.8))
+    gv = lv.Volume(vol).build_accel((16, 16, 16)).to_bezier(STORE[storage])
+    run_case(gv, O, cam, tf, step, storage, _hitting_pixels(cam, 500, 24), 2048, image=gv.render(cam, tf, step))
+    gv.close()
+
+
 def test_trace_edge_cases(cfg1):
     """Pixels that miss, an empty list, a ray longer than max_samples (only
     the first records are kept; the count is the full one), and a pixel
