@@ -215,7 +215,7 @@ def test_trace_cfg1(cfg1, storage, mode, view, alpha_stop, capsys):
     gv.close()
 
 
-@pytest.mark.parametrize("storage", ["f32", "f16"])
+@pytest.mark.parametrize("storage", ["f32", "f16", "bf16"])
 def test_trace_cfg1_shaded(cfg1, storage):
     """Gradient shading (Sec. 4.1): same march and values; shaded pixels."""
     vol, O = cfg1
