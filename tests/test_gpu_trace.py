@@ -265,13 +265,17 @@ def test_trace_vector_nondyadic(vec, storage, field, comp, mode):
 
 VEC_DEG_CASES = [
     (1, "f32", "magnitude", 0),
+    (1, "f32", "component", 2),
     (1, "f16", "magnitude", 0),
     (1, "f16", "component", 1),
+    (1, "bf16", "magnitude", 0),
     (1, "bf16", "component", 2),
+    (3, "f32", "magnitude", 0),
     (3, "f32", "component", 0),
     (3, "f16", "magnitude", 0),
     (3, "f16", "component", 2),
     (3, "bf16", "magnitude", 0),
+    (3, "bf16", "component", 1),
 ]
 
 
@@ -296,8 +300,8 @@ def test_trace_vector_degrees(deg, storage, field, comp):
     gv.close()
 
 
-@pytest.mark.parametrize("deg,storage,mode", [(2, "f32", "heuristic"), (2, "f16", "learned"), (1, "f32", "heuristic"),
-                                               (1, "bf16", "fixed")])
+@pytest.mark.parametrize("deg,storage,mode", [(2, "f32", "heuristic"), (2, "f16", "learned"), (2, "bf16", "heuristic"),
+                                               (1, "f32", "heuristic"), (1, "f16", "fixed"), (1, "bf16", "fixed")])
 def test_trace_scalar_low_degree(deg, storage, mode):
     vol = V.refined_ball((deg,) * 3, (4, 4, 4), centres=((0.45, 0.5, 0.55),), radii=(0.35, 0.15), seed=6)
     O = Oracle(vol)
