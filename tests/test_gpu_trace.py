@@ -316,7 +316,7 @@ def test_trace_scalar_low_degree(deg, storage, mode):
     gv.close()
 
 
-@pytest.mark.parametrize("deg,storage", [(1, "f16"), (1, "bf16"), (2, "f16"), (2, "bf16"), (2, "f32")])
+@pytest.mark.parametrize("deg,storage", [(1, "f32"), (1, "f16"), (1, "bf16"), (2, "f32"), (2, "f16"), (2, "bf16")])
 def test_trace_shaded_low_degree(deg, storage):
     """Gradient shading on scalar volumes of degree 1 and 2, whose blocks take
     the generic layout (with 16-bit storage: mixed-precision FMAs for FP16,
