@@ -96,6 +96,55 @@ def test_stepwise_parity_heuristic(swirl, method):
             assert s[j, n + 1, 3] - s[j, n, 3] == pytest.approx(orc.heuristic_step(int(e)), rel=0, abs=1e-15)
 
 
+STORE = {"f32": lv.STORE_F32, "f16": lv.STORE_F16, "bf16": lv.STORE_BF16}
+# per-evaluation bound of 16-bit blocks, in units of the element's coefficient
+# half range (at most max|c|): FP16 pairs with mixed-precision FMAs 2.04 u,
+# BF16 converted at element entry 1.02 u
+BLOCK_BOUND = {"f32": 0.0, "f16": 2.04 * 2.0 ** -11, "bf16": 1.02 * 2.0 ** -8}
+
+
+@pytest.mark.parametrize("deg,storage", [(1, "f32"), (1, "f16"), (2, "f16"), (2, "bf16"), (3, "f32"), (3, "f16"),
+                                         (3, "bf16")])
+def test_stepwise_parity_degrees_and_storage(deg, storage):
+    """RK4 with Eq. 4 steps on 3-vector volumes of every degree and block
+    storage the tracer instantiates; each GPU step redone by the FP64 oracle
+    with the bar above plus the 16-bit block bound, and the heuristic step
+    exact."""
+    vol = V.refined_ball((deg,) * 3, (4, 4, 4), centres=((0.4, 0.5, 0.55),), radii=(0.35, 0.18), ncomp=3,
+                         seed=13 + deg)
+    vol.coef = (vol.coef - 0.5) * 2.0
+    orc = Oracle(vol)
+    gv = lv.Volume(vol).build_accel((16, 16, 16)).to_bezier(STORE[storage])
+    seeds = np.random.default_rng(3 + deg).uniform(0.2, 0.8, (32, 3))
+    s, c, st = _gpu_lines(gv, seeds, "RK4", "heuristic", 1.0, 0.4)
+    gv.close()
+    cmax = np.abs(vol.coef).max()
+    min_side = float(np.min(vol.elem_box[:, 3:] - vol.elem_box[:, :3]))
+    G = 2 * deg * cmax / min_side
+    xs, hs, nxt = [], [], []
+    for j in range(len(s)):
+        for n in range(int(c[j]) - 1):
+            xs.append(s[j, n, :3])
+            hs.append(s[j, n + 1, 3] - s[j, n, 3])
+            nxt.append(s[j, n + 1, :3])
+    xs, hs, nxt = np.array(xs), np.array(hs), np.array(nxt)
+    assert len(xs) > 300
+    worst = 0.0
+    for h in np.unique(hs):
+        sel = hs == h
+        out, cnt, _ = orc.streamlines(xs[sel], "RK4", "fixed", h, h, max_samples=2)
+        ok = cnt == 2
+        assert ok.mean() > 0.99
+        err = np.abs(out[ok, 1, :3] - nxt[sel][ok])
+        bound = 2 * h * ((1e-5 + BLOCK_BOUND[storage]) * cmax + 1.2e-7 * G) + 1e-12
+        worst = max(worst, float((err / bound).max()))
+    assert worst <= 1.0, worst
+    for j in range(4):
+        for n in range(int(c[j]) - 2):
+            e = orc.eval(s[j, n, :3].astype(np.float32)[None], return_elem=True)[1][0]
+            assert s[j, n + 1, 3] - s[j, n, 3] == pytest.approx(orc.heuristic_step(int(e)), rel=0, abs=1e-15)
+
+
 @pytest.mark.parametrize("method,tol", [("HE", 1e-5), ("BS", 1e-6), ("RKF45", 1e-7)])
 def test_stepwise_parity_adaptive(swirl, method, tol):
     vol, orc, gv = swirl
