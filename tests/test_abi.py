@@ -134,3 +134,21 @@ def test_binding_constants_match_header(tmp_path):
         assert int(got[m]) == i, m                   # the binding passes the list index as the method
     for i, r in enumerate(lv.SL_RULES):
         assert int(got[r]) == i, r
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    """Without the compiled library the binding raises on first use; there is
+    no CPU fallback (a fresh interpreter, so no library is loaded already)."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "from paper_1707_01170_gb300 import lrvol as lv\n"
+            "try:\n"
+            "    lv.load(%r)\n"
+            "except RuntimeError as e:\n"
+            "    print('raised:', e)\n"
+            "else:\n"
+            "    print('loaded')\n") % (ROOT, str(tmp_path / "no_such" / "liblrvol.so"))
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, timeout=120)
+    assert out.returncode == 0, out.stderr
+    assert out.stdout.startswith("raised:") and "not built" in out.stdout
