@@ -392,6 +392,8 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
         lst = gq.stats()
         samples, lookups = lst["samples"], lst["lookups"]
         ms_feat, ms_net, ms_render = _timed_frames([feat_fn, net_fn, render_fn], steps, flush, stream)
+        fps = flop_per_sample(int(vol.deg[0]), "scalar")
+        peak32, peak32_src = plain.get("peak32") or fp32_peak(None)
         ms_mult = ms_feat + ms_net
         if (w, h) == (WIDTH, HEIGHT):
             res["ablation"] = LS.ablation(gq, ccam, ctf, step, model, fine, stream=stream)
@@ -400,7 +402,12 @@ def learned_leg(vol, tf, step, plain, steps: int, storage: str, flush, stream, m
             "ms_network": ms_net, "ms_render": ms_render,
             "samples_per_frame": samples, "lookups_per_frame": lookups, "rmse_vs_fine": rmse(out, fine),
             "plain_f32_ms_per_frame": ms_plain, "plain_f32_samples_per_frame": samples_plain,
-            "plain_f32_rmse_vs_fine": rmse(ref_img, fine), "speedup_vs_plain_f32": ms_plain / (ms_mult + ms_render)}
+            "plain_f32_rmse_vs_fine": rmse(ref_img, fine), "speedup_vs_plain_f32": ms_plain / (ms_mult + ms_render),
+            # the learned render's counted flops (same per-sample count as the plain frame) against the FP32 peak
+            "render_roofline": {"bound": "alu", "achieved": fps * samples / (ms_render * 1e-3) / 1e12,
+                                "peak": peak32, "unit": "TFLOP/s",
+                                "frac": fps * samples / (ms_render * 1e-3) / 1e12 / peak32,
+                                "flop_per_sample": fps, "peak_source": peak32_src}}
         del fine, out
     res.update(res["by_resolution"][f"{WIDTH}x{HEIGHT}"])
     peak, peak_src = measured_bf16_tflops()
@@ -430,7 +437,8 @@ def learned_summary(res: dict) -> dict:
         out[k] = {"ms": r3(v["ms_per_frame"]), "rmse": r3(v["rmse_vs_fine"]),
                   "plain_f32_ms": r3(v["plain_f32_ms_per_frame"]), "plain_f32_rmse": r3(v["plain_f32_rmse_vs_fine"]),
                   "speedup": r3(v["speedup_vs_plain_f32"]),
-                  "samples_frac": r3(v["samples_per_frame"] / v["plain_f32_samples_per_frame"])}
+                  "samples_frac": r3(v["samples_per_frame"] / v["plain_f32_samples_per_frame"]),
+                  "render_frac": r3(v["render_roofline"]["frac"])}
     ab = res.get("ablation")
     if ab:
         pick = lambda b: None if b is None else [b["param"], r3(b["samples_frac"]), r3(b["rmse"])]
@@ -774,7 +782,8 @@ def run_ours(args):
     learned = None
     if args.learned != "off" and ws == 1 and step.field == "scalar":
         if args.storage == "f32":
-            plain = {"gv32": gv, "ms": ms_per_step, "samples": samples_per_frame, "img": out.clone()}
+            plain = {"gv32": gv, "ms": ms_per_step, "samples": samples_per_frame, "img": out.clone(),
+                     "peak32": fp32_peak(clk_summary)}
             learned = learned_leg(vol, tf, step, plain, max(3, min(args.steps, 50)), args.learned, flush, stream,
                                   args.learned_model, args.save_learned_model)
 
